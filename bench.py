@@ -1,0 +1,369 @@
+"""Benchmark: FP64 partial-assembly diffusion apply (GDOF/s) and Jacobi-PCG
+time to 1e-10 relative residual, FP64 vs FP32-inner iterative refinement.
+
+Workload (one GPU): unit-cube hexahedral mesh N^3 (N = 68), vertices
+perturbed by U[-0.15h, 0.15h] (tangentially on the boundary), order p = 4,
+q = 6 Gauss points per direction, per-element lognormal kappa, 20,346,417
+DOFs, x ~ U[-1, 1]. One step = one operator application y = A x (element
+kernel + inverse-map scatter). Inputs (D = 3.26 GB) are far larger than L2,
+so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With torchrun (N > 1) every rank applies the operator of its own
+independent problem (seed offset by rank; no collective in the data path)
+and `value` is the aggregate DOFs/s over all ranks (weak scaling).
+The reference arm (`--impl reference`) times the CPU oracle (assembled CSR
+SpMV, scipy, one core) on a bounded sample of the same workload.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+# FP64 FMA rate of a GB300 SM: 2 DFMA per clock per SM (derived from the
+# nominal 1.25 TFLOP/s; a DFMA microbenchmark on the box measured 1.19 TFLOP/s
+# at ~1.96 GHz). Peak = 152 SMs x 2 DFMA x 2 flop x 2070 MHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def alg_counts(p, q, E, n, kind="diffusion", fp=8):
+    """Algorithmic flops and bytes of one apply (stream D once, read the map
+    once, read x and write y once)."""
+    D1, Q = p + 1, q
+    if kind == "diffusion":
+        flops_e = 2 * (4 * Q * D1 ** 3 + 6 * Q ** 2 * D1 ** 2 + 6 * Q ** 3 * D1) + 15 * Q ** 3
+        bytes_ = 6 * fp * Q ** 3 * E + 4 * D1 ** 3 * E + 2 * fp * n
+    else:
+        flops_e = 4 * (Q * D1 ** 3 + Q ** 2 * D1 ** 2 + Q ** 3 * D1) + Q ** 3
+        bytes_ = fp * Q ** 3 * E + 4 * D1 ** 3 * E + 2 * fp * n
+    return flops_e * E, bytes_
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("k_apply.cu", "k_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1911_09220_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload_key):
+    """dram bytes per launch of the element kernel from a committed ncu
+    summary, if it was taken on the current kernel source."""
+    try:
+        t = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None
+    ent = t.get(workload_key)
+    if not ent or ent.get("kernel_hash") != kernel_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+def make_problem(p, N, seed_offset=0):
+    from fem_inputs import hex_lattice, lognormal, x_uniform
+    c, h = hex_lattice(N, 0.15, seed=10 + p + seed_offset)
+    kappa = lognormal(20 + p + seed_offset, h.shape[0])
+    return c, h, kappa, (lambda n: x_uniform(30 + p + seed_offset, n))
+
+
+def cpu_oracle_spmv(p, N_sample, reps, deadline_s=30.0):
+    """Time the oracle's apply (assembled CSR SpMV, scipy, one thread) on a
+    sub-problem of the same recipe. Returns dict."""
+    from oracle import assemble
+    c, h, kappa, xgen = make_problem(p, N_sample)
+    t0 = time.perf_counter()
+    prob = assemble.Problem(c, h, p, p + 2, kappa=kappa)
+    K = prob.K
+    t_asm = time.perf_counter() - t0
+    x = xgen(prob.ndof)
+    y = K @ x
+    times = []
+    t_start = time.perf_counter()
+    for _ in range(reps):
+        t1 = time.perf_counter()
+        y = K @ x
+        times.append(time.perf_counter() - t1)
+        if time.perf_counter() - t_start > deadline_s:
+            break
+    t = statistics.median(times)
+    return {"ndof": prob.ndof, "E": h.shape[0], "t_spmv": t, "t_assembly": t_asm, "nnz": K.nnz,
+            "gdofs": prob.ndof / t / 1e9, "reps": len(times), "times": times}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p = args.p
+    r = cpu_oracle_spmv(p, args.cpu_n, max(args.steps, 1), deadline_s=60.0)
+    total = sum(r["times"][: args.steps]) if len(r["times"]) >= args.steps else sum(r["times"])
+    value = r["gdofs"]
+    line = {
+        "impl": "reference", "metric": "PA diffusion apply GDOF/s", "value": value, "unit": "GDOF/s",
+        "n_gpus": args.gpus, "steps": len(r["times"]), "warmup": 1, "ms_per_step": r["t_spmv"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"FP64 diffusion y=Ax, p={p}, q={p + 2}, {args.cpu_n}^3 perturbed hex sample "
+                               f"({r['ndof']} DOFs) of the N={args.N} workload", "p": p, "q1d": p + 2,
+                   "ndof": r["ndof"]},
+        "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+                         "sample": f"scipy CSR SpMV of the oracle's assembled matrix, {r['ndof']} DOFs "
+                                   f"(nnz {r['nnz']}), median of {len(r['times'])}; assembly {r['t_assembly']:.1f} s untimed"},
+        "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "total_s": total,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--p", type=int, default=4)
+    ap.add_argument("--N", type=int, default=68)
+    ap.add_argument("--cpu-n", type=int, default=16, help="lattice size of the CPU oracle sample")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--solve-maxit", type=int, default=20000)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1911_09220_gb300 import build as fbuild
+    fbuild.build()
+    import paper_1911_09220_gb300 as F
+
+    p, N = args.p, args.N
+    q = p + 2
+    c, h, kappa, xgen = make_problem(p, N, seed_offset=1000 * rank)
+    t0 = time.perf_counter()
+    mesh = F.Mesh(c, h)
+    space = F.Space(mesh, p)
+    t_space = time.perf_counter() - t0
+    kap = torch.as_tensor(kappa, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    form = F.Form(space, "diffusion", q, coef=kap)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    n, E = space.ndof, space.ne
+    x_host = torch.as_tensor(xgen(n)).pin_memory()
+    x = x_host.to(dev)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    ye = torch.empty((E, (p + 1) ** 3), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        form.apply_element(x, ye)
+        form.scatter(ye, y)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        form.apply_element(x, ye)
+        ev[k][1].record(stream)
+        form.scatter(ye, y)
+        ev[k][2].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    t_total_ms = ev[0][0].elapsed_time(ev[-1][2])
+    t_elem = [a.elapsed_time(b) for a, b, _ in ev]
+    t_scat = [b.elapsed_time(c_) for _, b, c_ in ev]
+    ms_step = t_total_ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * n / (ms_step * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers
+    y_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        xd = x_host.to(dev, non_blocking=True)
+        form.apply(xd, y)
+        y_host.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        xd = x_host.to(dev, non_blocking=True)
+        form.apply(xd, y)
+        y_host.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * n / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": 8 * n,
+           "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_ms}
+
+    flops, bytes_alg = alg_counts(p, q, E, n)
+    t_el = statistics.mean(t_elem) * 1e-3
+    achieved = flops / t_el / 1e12
+    key = f"diffusion_f64_p{p}_N{N}"
+    traffic_full = measured_traffic(key)
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_full,
+            "kernel": "k_diffusion_apply<double,5,6,4> (FP64 element kernel)",
+            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
+            "alg_flops_per_launch": flops, "alg_bytes_per_launch": bytes_alg,
+            "hbm_achieved_gbs": bytes_alg / (t_el + statistics.mean(t_scat) * 1e-3) / 1e9,
+            "hbm_peak_gbs_measured": peaks().get("hbm_gbs"),
+            "element_kernel_ms": statistics.mean(t_elem), "scatter_kernel_ms": statistics.mean(t_scat),
+            "element_share": statistics.mean(t_elem) / (statistics.mean(t_elem) + statistics.mean(t_scat))}
+
+    solve = None
+    if not args.no_solve:
+        solve = {}
+        ess = torch.as_tensor(space.boundary_dofs(), device=dev)
+        form.set_essential(ess)
+        xq = form.qpoint_coords()
+        fq = (3 * np.pi ** 2 * torch.sin(np.pi * xq[..., 0]) * torch.sin(np.pi * xq[..., 1])
+              * torch.sin(np.pi * xq[..., 2])).contiguous()
+        del xq
+        b = torch.empty(n, dtype=torch.float64, device=dev)
+        form.rhs(fq, b)
+        del fq
+        bc = torch.empty_like(b)
+        form.lift_rhs(b, torch.zeros_like(b), bc)
+        sols = {}
+        for prec in ("f64", "mixed"):
+            u = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = form.solve(bc, u, rtol=1e-10, maxit=args.solve_maxit, precision=prec, raise_on_error=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            solve[prec] = {"seconds": dt, "iterations": info["iterations"], "outer": info["outer"],
+                           "converged": info["converged"], "relres": info["relres"]}
+            sols[prec] = u
+        diff = (sols["mixed"] - sols["f64"]).abs().max().item() / sols["f64"].abs().max().item()
+        solve["mixed_vs_f64_maxrel"] = diff
+        solve["speedup_mixed"] = solve["f64"]["seconds"] / solve["mixed"]["seconds"]
+        solve["rtol"] = 1e-10
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        r = cpu_oracle_spmv(p, args.cpu_n, 20, deadline_s=20.0)
+        cpu = {"value": r["gdofs"], "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+               "sample": f"scipy CSR SpMV of the oracle's assembled matrix on a {args.cpu_n}^3-element sample of "
+                         f"the same recipe ({r['ndof']} DOFs, nnz {r['nnz']}), median of {r['reps']}; "
+                         f"assembly {r['t_assembly']:.1f} s not timed", "host_cpus": os.cpu_count()}
+
+    if rank == 0:
+        line = {
+            "metric": "PA diffusion apply GDOF/s", "value": value, "unit": "GDOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"FP64 PA diffusion apply y=Ax, p={p}, q={q}, {N}^3 hex mesh perturbed 0.15h, "
+                                   f"lognormal kappa, {n} DOFs per GPU", "p": p, "q1d": q, "N": N, "ndof": n,
+                       "elements": E, "parallelism": f"replicas x{world} (independent problems)",
+                       "l2": "inputs larger than L2 (D alone 3.26 GB); no flush"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "clocks": clk, "solve": solve,
+            "setup_s": {"space_host": t_space, "form_setup": t_setup},
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

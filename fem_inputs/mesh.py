@@ -101,3 +101,16 @@ def hex_lattice(N, perturb=0.0, seed=1, shuffle=False, shuffle_seed=None,
 def lattice_dofs(N, p):
     """Number of H1 Q_p DOFs on an N^3 lattice: (pN+1)^3."""
     return (p * N + 1) ** 3
+
+
+def submesh(coords, hexes, keep):
+    """Keep the elements listed in `keep` and renumber the vertices they use
+    (in order of first use), e.g. to build meshes whose element count is not
+    a multiple of a kernel's block size."""
+    hexes = np.asarray(hexes, dtype=np.int64)[np.asarray(keep)]
+    used, first = np.unique(hexes.ravel(), return_index=True)
+    order = used[np.argsort(first, kind="stable")]
+    remap = np.full(int(hexes.max()) + 1, -1, dtype=np.int64)
+    remap[order] = np.arange(order.size)
+    return (np.ascontiguousarray(np.asarray(coords)[order]),
+            np.ascontiguousarray(remap[hexes].astype(np.int32)))

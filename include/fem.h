@@ -1,0 +1,219 @@
+/*
+ * fem.h - C ABI of the GB300 (sm_103a) partial-assembly finite-element library.
+ *
+ * The library computes the matrix-free (partially assembled) action y = A x of
+ * the high-order H1 mass and diffusion operators on unstructured hexahedral
+ * Q_p meshes by sum factorization, the assembled diagonal, the load vector,
+ * the Jacobi-preconditioned CG solve built on the action (FP64, or FP32 inner
+ * iterations inside FP64 iterative refinement), batched applies/solves over
+ * many independent problems, and the compliance gradient with respect to a
+ * per-element coefficient.
+ *
+ * The operator follows the decomposition A = P^T G^T B^T D B G P of the paper
+ * (Sec. 4.3 "Operator Decomposition"; P = I on one GPU): G is the element
+ * restriction (L-vector -> E-vector gather, its transpose an atomic-free
+ * scatter-add through an inverse map), B the sum-factorized basis evaluator
+ * (Sec. 4.4, B_ki as a product of 1D factors), D the point-wise quadrature
+ * data stored by the setup phase (Sec. 4.4, "partial assembly operates at the
+ * Q-vector level ... leaves only the D operator to store").
+ *
+ * Conventions (all entry points):
+ *  - Every call returns fem_status; FEM_OK == 0. No call aborts, throws or
+ *    traps on the device. fem_last_error() returns a thread-local message for
+ *    the last failing call of the calling thread.
+ *  - Handles (fem_mesh, fem_space, fem_form, fem_batch) are opaque and owned
+ *    by the library; destroy them with the matching *_destroy call. A space
+ *    must outlive the forms built on it; a mesh must outlive its spaces.
+ *  - Vectors passed as `void*` / `double*` device pointers are caller-owned
+ *    CUDA device memory (e.g. torch tensor data pointers), contiguous, and
+ *    of the dtype named by the call. Host pointers are named `*_host`.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Calls are
+ *    asynchronous on that stream unless documented otherwise.
+ *  - Output vectors must not alias input vectors.
+ *  - L-vector ordering: global DOF numbering of Sec. 3.4 ("Finite Element
+ *    Spaces"): vertices (vertex id), then edges, then faces, then element
+ *    interiors. Edges/faces are numbered by first appearance scanning elements
+ *    in order and, inside an element, the local edge order
+ *    (0,1),(1,2),(3,2),(0,3),(4,5),(5,6),(7,6),(4,7),(0,4),(1,5),(2,6),(3,7)
+ *    and face order z=0,y=0,x=1,y=1,x=0,z=1. Edge DOFs run from the lower to
+ *    the higher global vertex; face DOFs are listed row by row in the frame at
+ *    the face's lowest global vertex, first axis toward the lower-numbered of
+ *    its two face neighbours. Interiors: lexicographic, x fastest.
+ *  - Reference cell [0,1]^3; local hexahedron vertex order: bottom face 0-1-2-3
+ *    counter-clockwise seen from above, top face 4-5-6-7 (VTK order). The map
+ *    is trilinear in the 8 vertices (Sec. 3.1, Eq. mesh_eq_x with vertex
+ *    coordinates). Basis: nodal Lagrange at Gauss-Lobatto points (Sec. 3.3);
+ *    quadrature: q1d-point Gauss-Legendre per direction.
+ */
+#ifndef FEM_H
+#define FEM_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int fem_status;
+enum {
+  FEM_OK = 0,
+  FEM_EINVAL = 1,        /* bad argument, size or mesh connectivity */
+  FEM_ENOMEM = 2,        /* device or host allocation failed */
+  FEM_EINVERTED = 3,     /* setup found det J <= 0 at a quadrature point */
+  FEM_ENOCONV = 4,       /* solver hit maxit before the tolerance */
+  FEM_EBREAKDOWN = 5,    /* CG breakdown: p^T A p <= 0 or a non-finite scalar */
+  FEM_ECUDA = 6,         /* a CUDA runtime call or kernel launch failed */
+  FEM_EUNSUPPORTED = 7   /* (p, q1d) or size outside the compiled set */
+};
+
+enum { FEM_MASS = 0, FEM_DIFFUSION = 1 };       /* bilinear form kind */
+enum { FEM_F64 = 0, FEM_F32 = 1 };              /* vector / compute dtype */
+enum { FEM_SOLVE_F64 = 0, FEM_SOLVE_MIXED = 1 }; /* solve precision */
+
+typedef struct fem_mesh fem_mesh;
+typedef struct fem_space fem_space;
+typedef struct fem_form fem_form;
+typedef struct fem_batch fem_batch;
+
+/* Library version string and thread-local description of the last error. */
+const char* fem_version(void);
+const char* fem_last_error(void);
+
+/* Orders p and 1D quadrature sizes q1d compiled into this build.
+ * fem_supported(p, q1d) returns 1 if the pair has kernels, else 0. */
+int fem_supported(int p, int q1d);
+
+/* ---- mesh (Sec. 3.1 "Conforming Meshes": vertices + element vertex tuples) --
+ * coords_host: [nv][3] float64 vertex coordinates; hex_host: [ne][8] int32
+ * vertex indices in the local order above. Both are copied (host + device);
+ * the caller keeps ownership of its arrays. Errors: FEM_EINVAL if nv or ne is
+ * not positive, an index is out of range, an element repeats a vertex or a
+ * vertex is referenced by no element. */
+fem_status fem_mesh_create(const double* coords_host, int64_t nv,
+                           const int32_t* hex_host, int64_t ne, fem_mesh** out);
+void fem_mesh_destroy(fem_mesh* mesh);
+
+/* ---- H1 space of order p (Sec. 3.4 "Finite Element Spaces") ----------------
+ * Builds the global numbering, the element->DOF table e2l [ne][(p+1)^3]
+ * (lexicographic local order, x fastest), its inverse (CSR, entries sorted by
+ * element then local index: the fixed summation order of the scatter) and the
+ * boundary DOFs (DOFs on faces with exactly one adjacent element). Host-side
+ * setup, synchronous. Errors: FEM_EINVAL (p < 1), FEM_EUNSUPPORTED (p > 8 or
+ * ne (p+1)^3 >= 2^31). */
+fem_status fem_space_create(const fem_mesh* mesh, int p, fem_space** out);
+void fem_space_destroy(fem_space* space);
+fem_status fem_space_info(const fem_space* space, int64_t* ndof, int64_t* nbdr,
+                          int64_t* ne, int* p);
+/* Boundary DOF ids, ascending: out_host [nbdr] int32. */
+fem_status fem_space_boundary_dofs(const fem_space* space, int32_t* out_host);
+/* The element->DOF table: out_host [ne][(p+1)^3] int32. */
+fem_status fem_space_element_dofs(const fem_space* space, int32_t* out_host);
+/* Physical location of every DOF (the trilinear map of its first element at
+ * the GLL node): out [ndof][3] float64 device. Asynchronous on stream. */
+fem_status fem_space_dof_coords(const fem_space* space, double* out, void* stream);
+
+/* ---- partial-assembly setup (Sec. 4.3: setup phase "evaluates and stores D")
+ * kind = FEM_DIFFUSION stores, per element e and quadrature point q,
+ *   D_q = coef_e w_q det J_q J_q^-1 J_q^-T  (6 symmetric components
+ *   00,01,02,11,12,22; the 3D form of the diffusion setup listing of
+ *   Sec. 5.3, which stores alpha W adj(J) adj(J)^T / det J in 2D);
+ * kind = FEM_MASS stores D_q = coef_e w_q det J_q (Sec. 4.4, (D_E)_kk).
+ * coef: device float64 [ne] per-element coefficient, or NULL for 1.
+ * Layout in HBM: [ne][6][q1d^3] (diffusion) or [ne][q1d^3] (mass), float64,
+ * point index lexicographic (x fastest). Synchronises `stream` to read the
+ * det J check. Errors: FEM_EINVERTED if any det J <= 0, FEM_EUNSUPPORTED if
+ * (p, q1d) is not compiled. */
+fem_status fem_form_create(const fem_space* space, int kind, int q1d,
+                           const double* coef, void* stream, fem_form** out);
+void fem_form_destroy(fem_form* form);
+/* Replace the per-element coefficient (recomputes D). */
+fem_status fem_form_set_coef(fem_form* form, const double* coef, void* stream);
+/* Essential DOF list (device int32 [n], any order, no duplicates needed):
+ * defines the constrained operator A_c = (I-E) A (I-E) + E (reading of the
+ * "further modifications" of FormLinearSystem, Sec. 5.1). */
+fem_status fem_form_set_essential(fem_form* form, const int32_t* ess, int64_t n,
+                                  void* stream);
+
+/* ---- operator action (Sec. 4.3 apply phase; Sec. 4.4 sum factorization) ----
+ * y = A x (overwrite; MFEM's AddMultPA adds, this call does not).
+ * dtype FEM_F64: x, y float64, D float64 (the FP64 path).
+ * dtype FEM_F32: x, y float32 with a float32 copy of D made on first use.
+ * constrained != 0 applies A_c (needs fem_form_set_essential).
+ * Runs the element kernel (gather, B/G contractions, D, B^T/G^T) into the
+ * form's E-vector scratch and the inverse-map scatter into y. */
+fem_status fem_apply(const fem_form* form, int dtype, const void* x, void* y,
+                     int constrained, void* stream);
+/* The two halves of fem_apply with a caller-provided E-vector
+ * ye [ne][(p+1)^3] of the same dtype: element kernel, then scatter. */
+fem_status fem_apply_element(const fem_form* form, int dtype, const void* x,
+                             void* ye, void* stream);
+fem_status fem_scatter(const fem_form* form, int dtype, const void* ye, void* y,
+                       void* stream);
+
+/* ---- assembled diagonal (needed for Jacobi: PA has no matrix entries,
+ * Sec. 4.4 and Sec. 5.2) ----------------------------------------------------
+ * diag_i = sum_e sum_q sum_ab D_ab(q) dphi_i/dxhat_a dphi_i/dxhat_b
+ * (diffusion) or sum_e sum_q D(q) phi_i(q)^2 (mass); float64 device [ndof].
+ * constrained != 0 sets diag = 1 on essential DOFs. */
+fem_status fem_assemble_diagonal(const fem_form* form, double* diag,
+                                 int constrained, void* stream);
+
+/* ---- load vector (Sec. 2, b_i = int f phi_i) -------------------------------
+ * fq: device float64 [ne][q1d^3], source values at the form's quadrature
+ * points; b: device float64 [ndof], overwritten with
+ * b_i = sum_e sum_q w_q det J_q fq(e,q) phi_i(q). */
+fem_status fem_rhs(const fem_form* form, const double* fq, double* b, void* stream);
+/* Physical coordinates of the quadrature points: xq device float64
+ * [ne][q1d^3][3]. */
+fem_status fem_qpoint_coords(const fem_form* form, double* xq, void* stream);
+
+/* ---- Jacobi-preconditioned CG (Sec. 5.2, CGSolver with SetRelTol /
+ * SetMaxIter) -----------------------------------------------------------------
+ * Solves A_c x = b for the constrained operator. On entry x holds the initial
+ * guess including the essential values g on essential DOFs; b must already be
+ * the constrained right-hand side (b_ess = g, b_free = b - A g on free DOFs;
+ * fem_lift_rhs builds it). Stops when ||b - A_c x||_2 <= rtol ||b||_2 for the
+ * true residual (recomputed in FP64 at exit; the iteration restarts from x if
+ * the recursive residual drifted). precision FEM_SOLVE_MIXED runs FP32 inner
+ * Jacobi-PCG to inner_rtol on FP32 copies of D, inside FP64 iterative
+ * refinement (FP64 outer residual, norms and updates).
+ * Synchronises `stream`. Errors: FEM_ENOCONV, FEM_EBREAKDOWN. */
+typedef struct {
+  double rtol;          /* relative tolerance, e.g. 1e-10 */
+  int maxit;            /* cap on (inner, for mixed) CG iterations */
+  int precision;        /* FEM_SOLVE_F64 or FEM_SOLVE_MIXED */
+  double inner_rtol;    /* mixed: inner relative tolerance (e.g. 1e-4) */
+  int max_outer;        /* mixed: cap on refinement steps */
+  int check_every;      /* iterations per CUDA-graph launch between host polls */
+  int use_graph;        /* capture check_every iterations in a CUDA graph */
+} fem_solve_opts;
+typedef struct {
+  int iterations;       /* total CG iterations (inner iterations for mixed) */
+  int outer;            /* refinement steps (mixed) or restarts (FP64) */
+  int converged;        /* 1 if the true residual met rtol */
+  double relres;        /* final ||b - A_c x||_2 / ||b||_2, FP64 */
+  double bnorm;         /* ||b||_2 */
+} fem_solve_info;
+void fem_solve_opts_default(fem_solve_opts* opts);
+fem_status fem_solve(const fem_form* form, const double* b, double* x,
+                     const fem_solve_opts* opts, fem_solve_info* info, void* stream);
+/* b_c = (I-E)(b - A g) + E g for the essential values held in g on essential
+ * DOFs (g is read on essential DOFs only). b, g, bc: device float64 [ndof]. */
+fem_status fem_lift_rhs(const fem_form* form, const double* b, const double* g,
+                        double* bc, void* stream);
+
+/* ---- compliance gradient (differentiation; the paper's LiDO application,
+ * Sec. 7, motivates it; no kernel in the paper) ------------------------------
+ * For a diffusion form: g_e = -(1/coef_e) sum_q gradhat(u)^T D_q gradhat(u)
+ * = -u_e^T Khat_e u_e, the derivative of J = b^T u (A u = b, b independent of
+ * the coefficient, self-adjoint so the adjoint state is u) with respect to
+ * coef_e. u: device float64 [ndof] (zero on essential DOFs); g: device
+ * float64 [ne]. */
+fem_status fem_compliance_grad(const fem_form* form, const double* u, double* g,
+                               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEM_H */

@@ -1,0 +1,226 @@
+"""GB300 (sm_103a) partial-assembly finite elements: Python front end.
+
+Thin wrappers over the C ABI of libfem.so (include/fem.h). Tensors are torch
+CUDA tensors (torch supplies device memory and streams); every computation
+runs in the library's kernels on the current torch stream.
+
+    mesh = Mesh(coords, hexes)                  # numpy float64 [nv,3], int32 [ne,8]
+    space = Space(mesh, p)
+    form = Form(space, "diffusion", q1d=p + 2, coef=kappa)   # PA setup (D)
+    form.apply(x, y)                             # y = A x
+    form.diagonal(d); form.rhs(fq, b); form.solve(b, x, rtol=1e-10)
+"""
+
+import ctypes as C
+
+import numpy as np
+
+from . import _binding as B
+from ._binding import FemError, FEM_DIFFUSION, FEM_MASS, FEM_F64, FEM_F32, FEM_SOLVE_F64, FEM_SOLVE_MIXED
+
+__all__ = ["Mesh", "Space", "Form", "FemError", "lib", "supported", "version"]
+
+
+def lib():
+    return B.lib()
+
+
+def version():
+    return B.lib().fem_version().decode()
+
+
+def supported(p, q1d):
+    return bool(B.lib().fem_supported(int(p), int(q1d)))
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float64:
+        return FEM_F64
+    if t.dtype == torch.float32:
+        return FEM_F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+class Mesh:
+    """Unstructured hexahedral mesh: vertex coordinates and 8-vertex tuples
+    in VTK order (Sec. 3.1, conforming meshes)."""
+
+    def __init__(self, coords, hexes):
+        L = B.lib()
+        self.coords = np.ascontiguousarray(coords, dtype=np.float64)
+        self.hexes = np.ascontiguousarray(hexes, dtype=np.int32)
+        if self.coords.ndim != 2 or self.coords.shape[1] != 3 or self.hexes.ndim != 2 or self.hexes.shape[1] != 8:
+            raise ValueError("coords must be [nv,3] and hexes [ne,8]")
+        h = C.c_void_p()
+        B.check(L.fem_mesh_create(self.coords.ctypes.data, self.coords.shape[0], self.hexes.ctypes.data,
+                                  self.hexes.shape[0], C.byref(h)))
+        self._h = h
+        self.nv, self.ne = self.coords.shape[0], self.hexes.shape[0]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and B._lib is not None:
+            B._lib.fem_mesh_destroy(self._h)
+            self._h = None
+
+
+class Space:
+    """H1 space of order p (GLL nodal basis) with the global numbering of
+    Sec. 3.4 and the element restriction G and its inverse."""
+
+    def __init__(self, mesh, p):
+        L = B.lib()
+        self.mesh = mesh
+        h = C.c_void_p()
+        B.check(L.fem_space_create(mesh._h, int(p), C.byref(h)))
+        self._h = h
+        ndof, nbdr, ne = C.c_int64(), C.c_int64(), C.c_int64()
+        pp = C.c_int()
+        B.check(L.fem_space_info(h, C.byref(ndof), C.byref(nbdr), C.byref(ne), C.byref(pp)))
+        self.ndof, self.nbdr, self.ne, self.p = ndof.value, nbdr.value, ne.value, pp.value
+
+    def boundary_dofs(self):
+        out = np.empty(self.nbdr, dtype=np.int32)
+        B.check(B.lib().fem_space_boundary_dofs(self._h, out.ctypes.data))
+        return out
+
+    def element_dofs(self):
+        out = np.empty((self.ne, (self.p + 1) ** 3), dtype=np.int32)
+        B.check(B.lib().fem_space_element_dofs(self._h, out.ctypes.data))
+        return out
+
+    def dof_coords(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.ndof, 3), dtype=torch.float64, device="cuda")
+        B.check(B.lib().fem_space_dof_coords(self._h, _ptr(out, torch.float64, "out"), _stream(stream)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None) and B._lib is not None:
+            B._lib.fem_space_destroy(self._h)
+            self._h = None
+
+
+class Form:
+    """Partially assembled mass or diffusion form (Sec. 4.3-4.4): setup stores
+    D at the quadrature points; apply runs G, B, D, B^T, G^T on the fly."""
+
+    def __init__(self, space, kind="diffusion", q1d=None, coef=None, stream=None):
+        import torch
+        L = B.lib()
+        self.space = space
+        self.kind = {"diffusion": FEM_DIFFUSION, "mass": FEM_MASS}[kind] if isinstance(kind, str) else int(kind)
+        self.q1d = int(q1d) if q1d is not None else space.p + 2
+        self.nq = self.q1d ** 3
+        self._coef = None if coef is None else coef.contiguous()
+        h = C.c_void_p()
+        B.check(L.fem_form_create(space._h, self.kind, self.q1d, _ptr(self._coef, torch.float64, "coef"),
+                                  _stream(stream), C.byref(h)))
+        self._h = h
+        self.ess = None
+
+    # ---- configuration
+    def set_coef(self, coef, stream=None):
+        import torch
+        self._coef = coef.contiguous()
+        B.check(B.lib().fem_form_set_coef(self._h, _ptr(self._coef, torch.float64, "coef"), _stream(stream)))
+
+    def set_essential(self, ess, stream=None):
+        import torch
+        if not isinstance(ess, torch.Tensor):
+            ess = torch.as_tensor(np.asarray(ess, dtype=np.int32), device="cuda")
+        self.ess = ess.to(torch.int32).contiguous()
+        B.check(B.lib().fem_form_set_essential(self._h, _ptr(self.ess, torch.int32, "ess") if self.ess.numel() else None,
+                                               self.ess.numel(), _stream(stream)))
+
+    # ---- operator
+    def apply(self, x, y, constrained=False, stream=None):
+        if x.dtype != y.dtype:
+            raise TypeError("x and y must have the same dtype")
+        B.check(B.lib().fem_apply(self._h, _dtype_code(x), _ptr(x, name="x"), _ptr(y, name="y"),
+                                  int(bool(constrained)), _stream(stream)))
+        return y
+
+    def apply_element(self, x, ye, stream=None):
+        B.check(B.lib().fem_apply_element(self._h, _dtype_code(x), _ptr(x, name="x"), _ptr(ye, x.dtype, "ye"),
+                                          _stream(stream)))
+        return ye
+
+    def scatter(self, ye, y, stream=None):
+        B.check(B.lib().fem_scatter(self._h, _dtype_code(ye), _ptr(ye, name="ye"), _ptr(y, ye.dtype, "y"),
+                                    _stream(stream)))
+        return y
+
+    def diagonal(self, out, constrained=False, stream=None):
+        import torch
+        B.check(B.lib().fem_assemble_diagonal(self._h, _ptr(out, torch.float64, "out"), int(bool(constrained)),
+                                              _stream(stream)))
+        return out
+
+    def rhs(self, fq, b, stream=None):
+        import torch
+        B.check(B.lib().fem_rhs(self._h, _ptr(fq, torch.float64, "fq"), _ptr(b, torch.float64, "b"), _stream(stream)))
+        return b
+
+    def qpoint_coords(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.space.ne, self.nq, 3), dtype=torch.float64, device="cuda")
+        B.check(B.lib().fem_qpoint_coords(self._h, _ptr(out, torch.float64, "out"), _stream(stream)))
+        return out
+
+    def lift_rhs(self, b, g, bc, stream=None):
+        import torch
+        B.check(B.lib().fem_lift_rhs(self._h, _ptr(b, torch.float64, "b"), _ptr(g, torch.float64, "g"),
+                                     _ptr(bc, torch.float64, "bc"), _stream(stream)))
+        return bc
+
+    def solve(self, b, x, rtol=1e-10, maxit=20000, precision="f64", inner_rtol=1e-4, max_outer=30,
+              check_every=16, use_graph=True, stream=None, raise_on_error=True):
+        import torch
+        o = B.SolveOpts()
+        B.lib().fem_solve_opts_default(C.byref(o))
+        o.rtol, o.maxit, o.inner_rtol, o.max_outer = rtol, maxit, inner_rtol, max_outer
+        o.precision = FEM_SOLVE_MIXED if precision == "mixed" else FEM_SOLVE_F64
+        o.check_every, o.use_graph = check_every, int(bool(use_graph))
+        info = B.SolveInfo()
+        st = B.lib().fem_solve(self._h, _ptr(b, torch.float64, "b"), _ptr(x, torch.float64, "x"), C.byref(o),
+                               C.byref(info), _stream(stream))
+        out = {"status": st, "iterations": info.iterations, "outer": info.outer,
+               "converged": bool(info.converged), "relres": info.relres, "bnorm": info.bnorm}
+        if st != B.FEM_OK and raise_on_error:
+            raise FemError(st, B.lib().fem_last_error().decode())
+        return out
+
+    def compliance_grad(self, u, g, stream=None):
+        import torch
+        B.check(B.lib().fem_compliance_grad(self._h, _ptr(u, torch.float64, "u"), _ptr(g, torch.float64, "g"),
+                                            _stream(stream)))
+        return g
+
+    def __del__(self):
+        if getattr(self, "_h", None) and B._lib is not None:
+            B._lib.fem_form_destroy(self._h)
+            self._h = None

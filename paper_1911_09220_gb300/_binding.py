@@ -1,0 +1,98 @@
+"""ctypes binding of libfem.so (the C ABI declared in include/fem.h).
+
+Argument marshalling only: every computation runs in the library's sm_103a
+kernels. The library must have been built (paper_1911_09220_gb300.build);
+loading fails loudly otherwise, there is no fallback.
+"""
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfem.so")
+
+FEM_OK, FEM_EINVAL, FEM_ENOMEM, FEM_EINVERTED, FEM_ENOCONV, FEM_EBREAKDOWN, FEM_ECUDA, FEM_EUNSUPPORTED = range(8)
+FEM_MASS, FEM_DIFFUSION = 0, 1
+FEM_F64, FEM_F32 = 0, 1
+FEM_SOLVE_F64, FEM_SOLVE_MIXED = 0, 1
+
+STATUS_NAMES = {
+    0: "FEM_OK", 1: "FEM_EINVAL", 2: "FEM_ENOMEM", 3: "FEM_EINVERTED", 4: "FEM_ENOCONV",
+    5: "FEM_EBREAKDOWN", 6: "FEM_ECUDA", 7: "FEM_EUNSUPPORTED",
+}
+
+
+class FemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("maxit", C.c_int), ("precision", C.c_int),
+                ("inner_rtol", C.c_double), ("max_outer", C.c_int), ("check_every", C.c_int),
+                ("use_graph", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("outer", C.c_int), ("converged", C.c_int),
+                ("relres", C.c_double), ("bnorm", C.c_double)]
+
+
+P = C.c_void_p
+I64 = C.c_int64
+I = C.c_int
+
+# name -> (restype, argtypes); every entry point declared in include/fem.h
+SIGNATURES = {
+    "fem_version": (C.c_char_p, []),
+    "fem_last_error": (C.c_char_p, []),
+    "fem_supported": (I, [I, I]),
+    "fem_mesh_create": (I, [P, I64, P, I64, C.POINTER(P)]),
+    "fem_mesh_destroy": (None, [P]),
+    "fem_space_create": (I, [P, I, C.POINTER(P)]),
+    "fem_space_destroy": (None, [P]),
+    "fem_space_info": (I, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(I)]),
+    "fem_space_boundary_dofs": (I, [P, P]),
+    "fem_space_element_dofs": (I, [P, P]),
+    "fem_space_dof_coords": (I, [P, P, P]),
+    "fem_form_create": (I, [P, I, I, P, P, C.POINTER(P)]),
+    "fem_form_destroy": (None, [P]),
+    "fem_form_set_coef": (I, [P, P, P]),
+    "fem_form_set_essential": (I, [P, P, I64, P]),
+    "fem_apply": (I, [P, I, P, P, I, P]),
+    "fem_apply_element": (I, [P, I, P, P, P]),
+    "fem_scatter": (I, [P, I, P, P, P]),
+    "fem_assemble_diagonal": (I, [P, P, I, P]),
+    "fem_rhs": (I, [P, P, P, P]),
+    "fem_qpoint_coords": (I, [P, P, P]),
+    "fem_solve_opts_default": (None, [C.POINTER(SolveOpts)]),
+    "fem_solve": (I, [P, P, P, C.POINTER(SolveOpts), C.POINTER(SolveInfo), P]),
+    "fem_lift_rhs": (I, [P, P, P, P, P]),
+    "fem_compliance_grad": (I, [P, P, P, P]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libfem.so once and declare every entry point's signature."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_1911_09220_gb300.build` "
+                "(the CUDA library is required; there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH, mode=C.RTLD_GLOBAL)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != FEM_OK:
+        raise FemError(status, lib().fem_last_error().decode())
+    return status

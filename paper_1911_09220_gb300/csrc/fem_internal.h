@@ -1,0 +1,126 @@
+// Internal declarations shared by the library's host and CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fem.h"
+
+// ---------------------------------------------------------------- errors ----
+fem_status fem_fail(fem_status st, const char* fmt, ...);
+#define FEM_TRY(expr)                          \
+  do {                                         \
+    fem_status _st = (expr);                   \
+    if (_st != FEM_OK) return _st;             \
+  } while (0)
+#define FEM_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t _e = (call);                                                        \
+    if (_e != cudaSuccess)                                                          \
+      return fem_fail(FEM_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,         \
+                      cudaGetErrorString(_e));                                      \
+  } while (0)
+#define FEM_LAUNCHED() FEM_CUDA(cudaGetLastError())
+
+// Device buffer helpers (library-owned memory).
+template <typename T>
+fem_status dev_alloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return FEM_OK;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fem_fail(FEM_ENOMEM, "cudaMalloc(%zu bytes): %s", count * sizeof(T),
+                    cudaGetErrorString(e));
+  }
+  return FEM_OK;
+}
+template <typename T>
+void dev_free(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+// ---------------------------------------------------------------- handles ---
+struct fem_mesh {
+  int64_t nv = 0, ne = 0;
+  std::vector<double> coords;   // [nv][3]
+  std::vector<int32_t> hex;     // [ne][8]
+  double* d_coords = nullptr;
+  int32_t* d_hex = nullptr;
+};
+
+struct fem_space {
+  const fem_mesh* mesh = nullptr;
+  int p = 0, D1 = 0, nd = 0;    // nd = D1^3 local DOFs
+  int64_t ne = 0, ndof = 0;
+  int64_t n_edges = 0, n_faces = 0;
+  std::vector<int32_t> e2l;     // [ne][nd]
+  std::vector<int32_t> bdr;     // boundary DOFs, ascending
+  std::vector<double> nodes;    // GLL nodes on [0,1], D1
+  int32_t* d_e2l = nullptr;     // [ne][nd]
+  int32_t* d_l2e_off = nullptr; // [ndof+1]
+  int32_t* d_l2e_idx = nullptr; // [ne*nd], e*nd + k
+  double* d_nodes = nullptr;
+};
+
+struct fem_form {
+  const fem_space* space = nullptr;
+  int kind = FEM_DIFFUSION;
+  int q1d = 0, nq = 0, ncomp = 0;  // nq = q1d^3, ncomp 6 or 1
+  double* d_coef = nullptr;        // [ne]
+  double* d_D = nullptr;           // [ne][ncomp][nq]
+  float* d_D32 = nullptr;          // lazily made float copy
+  double* d_B = nullptr;           // [q1d][D1] basis values at Gauss points
+  double* d_G = nullptr;           // [q1d][D1] derivatives
+  float* d_B32 = nullptr;
+  float* d_G32 = nullptr;
+  double* d_qpts = nullptr;        // [q1d]
+  double* d_qwts = nullptr;        // [q1d]
+  void* d_ye = nullptr;            // E-vector scratch, ne*nd doubles
+  uint8_t* d_ess_mask = nullptr;   // [ndof], 1 on essential DOFs
+  int32_t* d_ess = nullptr;
+  int64_t n_ess = 0;
+  int* d_flag = nullptr;           // device status word for setup checks
+  // solver workspace (lazy)
+  double* d_work64 = nullptr;
+  size_t work64_len = 0;
+  float* d_work32 = nullptr;
+  size_t work32_len = 0;
+  double* d_red = nullptr;         // reduction partials / scalars
+  size_t red_len = 0;
+  int* h_pinned = nullptr;         // pinned host status words
+};
+
+// ---------------------------------------------------------------- basis -----
+// 1D tables on [0,1]: GLL nodes (D1 = p+1), Gauss-Legendre points/weights (q),
+// B[k][j] = l_j(x_k), G[k][j] = l_j'(x_k) for GLL Lagrange polynomials l_j.
+void fem_gll_nodes(int p, std::vector<double>& nodes);
+void fem_gauss_rule(int q, std::vector<double>& pts, std::vector<double>& wts);
+void fem_lagrange_tables(const std::vector<double>& nodes, const std::vector<double>& pts,
+                         std::vector<double>& B, std::vector<double>& G);
+
+// ---------------------------------------------------------------- kernels ---
+int fem_kernels_supported(int p, int q1d);
+fem_status fem_launch_setup(const fem_form* f, cudaStream_t s);
+fem_status fem_launch_qpoint_coords(const fem_form* f, double* xq, cudaStream_t s);
+fem_status fem_launch_dof_coords(const fem_space* sp, double* out, cudaStream_t s);
+fem_status fem_launch_apply_element(const fem_form* f, int dtype, const void* x, void* ye,
+                                    cudaStream_t s, const int* skip = nullptr);
+// scatter: y_i = sum over inverse map of ye; ess rows (if mask) get x_i (constrained).
+// pdot != nullptr: also writes per-block partial sums of x_i*y_i to pdot[nblocks].
+fem_status fem_launch_scatter(const fem_form* f, int dtype, const void* ye, void* y,
+                              const uint8_t* mask, const void* xess, double* pdot,
+                              int nblocks, cudaStream_t s, const int* skip = nullptr);
+fem_status fem_launch_zero_ess(const fem_form* f, int dtype, const void* x, void* xz,
+                               cudaStream_t s);
+fem_status fem_launch_diag_element(const fem_form* f, double* ye, cudaStream_t s);
+fem_status fem_launch_rhs_element(const fem_form* f, const double* fq, double* ye,
+                                  cudaStream_t s);
+fem_status fem_launch_grad(const fem_form* f, const double* u, double* g, cudaStream_t s);
+fem_status fem_form_ensure_f32(const fem_form* f, cudaStream_t s);
+fem_status fem_launch_mark_ess(const fem_form* f, cudaStream_t s);
+int fem_scatter_blocks(int64_t ndof);

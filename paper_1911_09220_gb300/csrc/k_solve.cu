@@ -1,0 +1,455 @@
+// Jacobi-preconditioned conjugate gradients on the partially assembled
+// operator (Sec. 5.2: CGSolver with a relative tolerance and an iteration cap;
+// Sec. 4.4: with PA there are no matrix entries, so the preconditioner is the
+// assembled diagonal), FP64 or FP32-inner / FP64-outer iterative refinement.
+//
+// One iteration is six launches on the solver stream:
+//   element kernel (p -> E-vector), scatter (q = A_c p, partials of p.q),
+//   alpha (1 block), update (x += a p, r -= a q, z = r / diag, partials of
+//   r.z and r.r), beta (1 block: convergence test, iteration count), p update.
+// Scalars live in device memory; every kernel returns at once when the device
+// `done` word is set, so a CUDA graph of `check_every` iterations can be
+// replayed and the host only polls between replays. Reductions are block
+// partials summed in a fixed order: results are bitwise reproducible.
+#include <cmath>
+#include <cstring>
+
+#include "fem_internal.h"
+#include "k_common.cuh"
+
+namespace {
+
+struct CgScalars {
+  double rz, alpha, beta, rr, bb, tol2, pq;
+  int it, done, status, maxit;
+};
+enum { ST_RUN = 0, ST_CONV = 1, ST_NOCONV = 2, ST_BREAK = 3 };
+
+constexpr int kRedThreads = 256;
+
+__device__ double sum_partials(const double* part, int n, double* red) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
+  return block_sum(v, red);
+}
+
+template <typename T>
+__global__ void k_cg_init(int64_t n, const T* __restrict__ r, const T* __restrict__ diag, T* __restrict__ z,
+                          T* __restrict__ p, const T* __restrict__ b, double* __restrict__ part) {
+  __shared__ double red[32];
+  double rz = 0, rr = 0, bb = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T ri = r[i];
+    const T zi = ri / diag[i];
+    z[i] = zi;
+    p[i] = zi;
+    rz += (double)ri * (double)zi;
+    rr += (double)ri * (double)ri;
+    if (b) bb += (double)b[i] * (double)b[i];
+  }
+  double s;
+  s = block_sum(rz, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  s = block_sum(rr, red);
+  if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = s;
+  s = block_sum(bb, red);
+  if (threadIdx.x == 0) part[2 * gridDim.x + blockIdx.x] = s;
+}
+
+// bb_given >= 0: use it as ||b||^2 (inner solves of the refinement use a
+// normalised right-hand side), else sum the b partials.
+__global__ void k_cg_init_scalars(CgScalars* sc, const double* __restrict__ part, int nb, double rtol,
+                                  double bb_given, int maxit) {
+  __shared__ double red[32];
+  const double rz = sum_partials(part, nb, red);
+  const double rr = sum_partials(part + nb, nb, red);
+  const double bb = sum_partials(part + 2 * nb, nb, red);
+  if (threadIdx.x == 0) {
+    sc->rz = rz;
+    sc->rr = rr;
+    sc->bb = bb_given >= 0 ? bb_given : bb;
+    sc->tol2 = rtol * rtol * sc->bb;
+    sc->it = 0;
+    sc->maxit = maxit;
+    sc->status = ST_RUN;
+    sc->done = 0;
+    if (rr <= sc->tol2) {
+      sc->done = 1;
+      sc->status = ST_CONV;
+    }
+    if (!isfinite(rz) || !isfinite(rr)) {
+      sc->done = 1;
+      sc->status = ST_BREAK;
+    }
+  }
+}
+
+__global__ void k_cg_alpha(CgScalars* sc, const double* __restrict__ part, int nb) {
+  __shared__ double red[32];
+  if (sc->done) return;
+  const double pq = sum_partials(part, nb, red);
+  if (threadIdx.x == 0) {
+    sc->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      sc->done = 1;
+      sc->status = ST_BREAK;
+    } else {
+      sc->alpha = sc->rz / pq;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_cg_update(int64_t n, const CgScalars* __restrict__ sc, T* __restrict__ x, T* __restrict__ r,
+                            T* __restrict__ z, const T* __restrict__ p, const T* __restrict__ q,
+                            const T* __restrict__ diag, double* __restrict__ part) {
+  __shared__ double red[32];
+  if (sc->done) return;
+  const T a = (T)sc->alpha;
+  double rz = 0, rr = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += a * p[i];
+    const T ri = r[i] - a * q[i];
+    r[i] = ri;
+    const T zi = ri / diag[i];
+    z[i] = zi;
+    rz += (double)ri * (double)zi;
+    rr += (double)ri * (double)ri;
+  }
+  double s = block_sum(rz, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  s = block_sum(rr, red);
+  if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void k_cg_beta(CgScalars* sc, const double* __restrict__ part, int nb) {
+  __shared__ double red[32];
+  if (sc->done) return;
+  const double rz = sum_partials(part, nb, red);
+  const double rr = sum_partials(part + nb, nb, red);
+  if (threadIdx.x == 0) {
+    sc->it += 1;
+    sc->rr = rr;
+    if (!isfinite(rz) || !isfinite(rr)) {
+      sc->done = 1;
+      sc->status = ST_BREAK;
+    } else if (rr <= sc->tol2) {
+      sc->done = 1;
+      sc->status = ST_CONV;
+    } else if (sc->it >= sc->maxit) {
+      sc->done = 1;
+      sc->status = ST_NOCONV;
+    } else {
+      sc->beta = rz / sc->rz;
+      sc->rz = rz;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_cg_p(int64_t n, const CgScalars* __restrict__ sc, const T* __restrict__ z, T* __restrict__ p) {
+  if (sc->done) return;
+  const T b = (T)sc->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + b * p[i];
+}
+
+// r = b - y, and partials of r.r (FP64 true residual).
+template <typename TB>
+__global__ void k_residual(int64_t n, const TB* __restrict__ b, const double* __restrict__ y, double* __restrict__ r,
+                           double* __restrict__ part) {
+  __shared__ double red[32];
+  double rr = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = (double)b[i] - y[i];
+    r[i] = ri;
+    rr += ri * ri;
+  }
+  const double s = block_sum(rr, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_sumsq(int64_t n, const double* __restrict__ v, double* __restrict__ part) {
+  __shared__ double red[32];
+  double acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += v[i] * v[i];
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_sum_to(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  __shared__ double red[32];
+  const double s = sum_partials(part, nb, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_scale_to_f32(int64_t n, const double* __restrict__ r, const double* __restrict__ rr,
+                               float* __restrict__ r32, float* __restrict__ x32) {
+  const double inv = 1.0 / sqrt(*rr);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    r32[i] = (float)(r[i] * inv);
+    x32[i] = 0.0f;
+  }
+}
+
+__global__ void k_axpy_scaled(int64_t n, const double* __restrict__ rr, const float* __restrict__ d,
+                              double* __restrict__ x) {
+  const double s = sqrt(*rr);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += s * (double)d[i];
+}
+
+__global__ void k_cast_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// Workspace carved out of the form's buffers.
+struct Work {
+  int64_t n;
+  int nb;                         // blocks of the vector kernels (and partials)
+  double *x, *r, *z, *p, *q, *diag, *t;  // FP64 vectors
+  float *x32, *r32, *z32, *p32, *q32, *diag32;
+  double* part;                   // 3 * nb partials
+  double* scal;                   // misc scalars (rr of refinement)
+  CgScalars* sc;
+};
+
+fem_status get_work(fem_form* f, bool mixed, Work& w) {
+  const int64_t n = f->space->ndof;
+  w.n = n;
+  w.nb = fem_scatter_blocks(n);
+  const size_t need64 = (size_t)7 * n;
+  if (f->work64_len < need64) {
+    dev_free(f->d_work64);
+    FEM_TRY(dev_alloc(&f->d_work64, need64));
+    f->work64_len = need64;
+  }
+  double* b = f->d_work64;
+  w.x = b; w.r = b + n; w.z = b + 2 * n; w.p = b + 3 * n; w.q = b + 4 * n; w.diag = b + 5 * n; w.t = b + 6 * n;
+  if (mixed) {
+    const size_t need32 = (size_t)6 * n;
+    if (f->work32_len < need32) {
+      dev_free(f->d_work32);
+      FEM_TRY(dev_alloc(&f->d_work32, need32));
+      f->work32_len = need32;
+    }
+    float* a = f->d_work32;
+    w.x32 = a; w.r32 = a + n; w.z32 = a + 2 * n; w.p32 = a + 3 * n; w.q32 = a + 4 * n; w.diag32 = a + 5 * n;
+  }
+  const size_t red_need = (size_t)3 * w.nb + 16 + (sizeof(CgScalars) + 7) / 8;
+  if (f->red_len < red_need) {
+    dev_free(f->d_red);
+    FEM_TRY(dev_alloc(&f->d_red, red_need));
+    f->red_len = red_need;
+  }
+  w.part = f->d_red;
+  w.scal = f->d_red + 3 * w.nb;
+  w.sc = reinterpret_cast<CgScalars*>(f->d_red + 3 * w.nb + 16);
+  return FEM_OK;
+}
+
+// One CG iteration on vectors of type T.
+template <typename T>
+fem_status cg_iteration(const fem_form* f, const Work& w, int dtype, T* x, T* r, T* z, T* p, T* q, const T* diag,
+                        cudaStream_t s) {
+  const int* skip = &w.sc->done;
+  FEM_TRY(fem_launch_apply_element(f, dtype, p, f->d_ye, s, skip));
+  FEM_TRY(fem_launch_scatter(f, dtype, f->d_ye, q, f->d_ess_mask, p, w.part, w.nb, s, skip));
+  k_cg_alpha<<<1, kRedThreads, 0, s>>>(w.sc, w.part, w.nb);
+  k_cg_update<T><<<w.nb, 256, 0, s>>>(w.n, w.sc, x, r, z, p, q, diag, w.part);
+  k_cg_beta<<<1, kRedThreads, 0, s>>>(w.sc, w.part, w.nb);
+  k_cg_p<T><<<w.nb, 256, 0, s>>>(w.n, w.sc, z, p);
+  FEM_LAUNCHED();
+  return FEM_OK;
+}
+
+// Run CG iterations until the device `done` word is set. With use_graph the
+// check_every iterations are captured once into a graph on a private stream
+// and replayed on `s`.
+template <typename T>
+fem_status cg_loop(fem_form* f, const Work& w, int dtype, T* x, T* r, T* z, T* p, T* q, const T* diag,
+                   const fem_solve_opts& o, cudaStream_t s, int* status_out, int* it_out) {
+  const int k = o.check_every > 0 ? o.check_every : 16;
+  cudaGraphExec_t exec = nullptr;
+  if (o.use_graph) {
+    cudaStream_t cs;
+    FEM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    fem_status st = FEM_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      st = fem_fail(FEM_ECUDA, "solve: stream capture failed to begin");
+    } else {
+      for (int i = 0; i < k && st == FEM_OK; ++i) st = cg_iteration<T>(f, w, dtype, x, r, z, p, q, diag, cs);
+      cudaError_t e = cudaStreamEndCapture(cs, &g);
+      if (st == FEM_OK && e != cudaSuccess) st = fem_fail(FEM_ECUDA, "solve: end capture: %s", cudaGetErrorString(e));
+    }
+    if (st == FEM_OK && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess)
+      st = fem_fail(FEM_ECUDA, "solve: graph instantiation failed");
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (st != FEM_OK) {
+      if (exec) cudaGraphExecDestroy(exec);
+      return st;
+    }
+  }
+  int* h = f->h_pinned;
+  fem_status st = FEM_OK;
+  const int max_rounds = o.maxit / k + 2;
+  for (int round = 0; round < max_rounds; ++round) {
+    if (exec) {
+      if (cudaGraphLaunch(exec, s) != cudaSuccess) {
+        st = fem_fail(FEM_ECUDA, "solve: graph launch failed");
+        break;
+      }
+    } else {
+      for (int i = 0; i < k && st == FEM_OK; ++i) st = cg_iteration<T>(f, w, dtype, x, r, z, p, q, diag, s);
+      if (st != FEM_OK) break;
+    }
+    if (cudaMemcpyAsync(h, &w.sc->it, 4 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      st = fem_fail(FEM_ECUDA, "solve: status read failed: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    if (h[1]) break;  // done
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (st != FEM_OK) return st;
+  *it_out = h[0];
+  *status_out = h[1] ? h[2] : ST_NOCONV;
+  return FEM_OK;
+}
+
+// ||b - A_c x||^2 into *out (device), r = b - A_c x (FP64).
+fem_status true_residual(fem_form* f, const Work& w, const double* b, const double* x, double* r, double* out,
+                         cudaStream_t s) {
+  FEM_TRY(fem_launch_zero_ess(f, FEM_F64, x, w.t, s));
+  FEM_TRY(fem_launch_apply_element(f, FEM_F64, w.t, f->d_ye, s));
+  FEM_TRY(fem_launch_scatter(f, FEM_F64, f->d_ye, w.q, f->d_ess_mask, x, nullptr, 0, s));
+  k_residual<double><<<w.nb, 256, 0, s>>>(w.n, b, w.q, r, w.part);
+  k_sum_to<<<1, kRedThreads, 0, s>>>(w.part, w.nb, out);
+  FEM_LAUNCHED();
+  return FEM_OK;
+}
+
+fem_status read_doubles(fem_form* f, const double* d, int n, double* h, cudaStream_t s) {
+  FEM_CUDA(cudaMemcpyAsync(f->h_pinned + 8, d, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  FEM_CUDA(cudaStreamSynchronize(s));
+  std::memcpy(h, f->h_pinned + 8, sizeof(double) * n);
+  return FEM_OK;
+}
+
+}  // namespace
+
+extern "C" void fem_solve_opts_default(fem_solve_opts* o) {
+  if (!o) return;
+  o->rtol = 1e-10;
+  o->maxit = 20000;
+  o->precision = FEM_SOLVE_F64;
+  o->inner_rtol = 1e-4;
+  o->max_outer = 30;
+  o->check_every = 16;
+  o->use_graph = 1;
+}
+
+extern "C" fem_status fem_solve(const fem_form* fc, const double* b, double* xio, const fem_solve_opts* opts,
+                                fem_solve_info* info, void* stream) {
+  if (!fc || !b || !xio) return fem_fail(FEM_EINVAL, "fem_solve: NULL argument");
+  if (!fc->d_ess_mask) return fem_fail(FEM_EINVAL, "fem_solve: call fem_form_set_essential first (n may be 0)");
+  fem_solve_opts o;
+  fem_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (!(o.rtol > 0) || o.maxit <= 0) return fem_fail(FEM_EINVAL, "fem_solve: rtol > 0 and maxit > 0 required");
+  if (o.precision != FEM_SOLVE_F64 && o.precision != FEM_SOLVE_MIXED)
+    return fem_fail(FEM_EINVAL, "fem_solve: unknown precision %d", o.precision);
+  fem_form* f = const_cast<fem_form*>(fc);
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool mixed = o.precision == FEM_SOLVE_MIXED;
+  Work w;
+  FEM_TRY(get_work(f, mixed, w));
+  if (mixed) FEM_TRY(fem_form_ensure_f32(f, s));
+  const int64_t n = w.n;
+  FEM_CUDA(cudaMemcpyAsync(w.x, xio, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  FEM_TRY(fem_assemble_diagonal(f, w.diag, 1, s));
+  fem_solve_info inf;
+  std::memset(&inf, 0, sizeof inf);
+  double hb[2];
+  int total_it = 0, outer = 0, status = ST_NOCONV;
+  double* rr_dev = w.scal;       // ||r||^2 of the last true residual
+  // ||b||^2
+  k_sumsq<<<w.nb, 256, 0, s>>>(n, b, w.part);
+  k_sum_to<<<1, kRedThreads, 0, s>>>(w.part, w.nb, w.scal + 1);
+  FEM_LAUNCHED();
+  FEM_TRY(read_doubles(f, w.scal + 1, 1, hb, s));
+  const double bb = hb[0];
+  inf.bnorm = std::sqrt(bb);
+  const double tol2 = o.rtol * o.rtol * bb;
+  if (!std::isfinite(bb)) {
+    if (info) *info = inf;
+    return fem_fail(FEM_EBREAKDOWN, "fem_solve: non-finite right-hand side");
+  }
+  if (!(bb > 0)) {
+    // b = 0: the solution of A_c x = 0 is x = 0
+    FEM_CUDA(cudaMemsetAsync(xio, 0, sizeof(double) * n, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    inf.converged = 1;
+    if (info) *info = inf;
+    return FEM_OK;
+  }
+  double rr = 0;
+  for (;;) {
+    FEM_TRY(true_residual(f, w, b, w.x, w.r, rr_dev, s));
+    FEM_TRY(read_doubles(f, rr_dev, 1, &rr, s));
+    if (!std::isfinite(rr)) {
+      status = ST_BREAK;
+      break;
+    }
+    if (rr <= tol2) {
+      status = ST_CONV;
+      break;
+    }
+    if (total_it >= o.maxit || (mixed && outer >= o.max_outer) || (!mixed && outer > o.max_outer)) {
+      status = ST_NOCONV;
+      break;
+    }
+    int st_in = ST_NOCONV, it_in = 0;
+    fem_solve_opts oi = o;
+    oi.maxit = o.maxit - total_it;
+    if (!mixed) {
+      // restart CG from the current x with the true residual
+      k_cg_init<double><<<w.nb, 256, 0, s>>>(n, w.r, w.diag, w.z, w.p, nullptr, w.part);
+      k_cg_init_scalars<<<1, kRedThreads, 0, s>>>(w.sc, w.part, w.nb, o.rtol, bb, oi.maxit);
+      FEM_LAUNCHED();
+      FEM_TRY(cg_loop<double>(f, w, FEM_F64, w.x, w.r, w.z, w.p, w.q, w.diag, oi, s, &st_in, &it_in));
+    } else {
+      // inner FP32 solve of A d = r / ||r|| to inner_rtol, then x += ||r|| d
+      k_cast_f32<<<w.nb, 256, 0, s>>>(n, w.diag, w.diag32);
+      k_scale_to_f32<<<w.nb, 256, 0, s>>>(n, w.r, rr_dev, w.r32, w.x32);
+      k_cg_init<float><<<w.nb, 256, 0, s>>>(n, w.r32, w.diag32, w.z32, w.p32, nullptr, w.part);
+      k_cg_init_scalars<<<1, kRedThreads, 0, s>>>(w.sc, w.part, w.nb, o.inner_rtol, 1.0, oi.maxit);
+      FEM_LAUNCHED();
+      FEM_TRY(cg_loop<float>(f, w, FEM_F32, w.x32, w.r32, w.z32, w.p32, w.q32, w.diag32, oi, s, &st_in, &it_in));
+      k_axpy_scaled<<<w.nb, 256, 0, s>>>(n, rr_dev, w.x32, w.x);
+      FEM_LAUNCHED();
+    }
+    total_it += it_in;
+    outer += 1;
+    if (st_in == ST_BREAK) {
+      status = ST_BREAK;
+      break;
+    }
+  }
+  FEM_CUDA(cudaMemcpyAsync(xio, w.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  FEM_CUDA(cudaStreamSynchronize(s));
+  inf.iterations = total_it;
+  inf.outer = outer;
+  inf.relres = std::sqrt(rr / bb);
+  inf.converged = status == ST_CONV;
+  if (info) *info = inf;
+  if (status == ST_BREAK) return fem_fail(FEM_EBREAKDOWN, "fem_solve: CG breakdown (p^T A p <= 0 or non-finite)");
+  if (status != ST_CONV)
+    return fem_fail(FEM_ENOCONV, "fem_solve: no convergence after %d iterations (relres %.3e)", total_it,
+                    inf.relres);
+  return FEM_OK;
+}
