@@ -151,6 +151,24 @@ fem_status fem_apply_element(const fem_form* form, int dtype, const void* x,
 fem_status fem_scatter(const fem_form* form, int dtype, const void* ye, void* y,
                        void* stream);
 
+/* y = A x in FP64 (unconstrained), allocating nothing: the paper has no
+ * counterpart; this entry point exists for callers that cannot let the
+ * library allocate device memory when they call it and cannot lend it a
+ * scratch buffer -- e.g. an application whose own pool has reserved nearly
+ * all GPU memory, or a latency-critical loop where a cudaMalloc (which can
+ * synchronise the device and can fail) is not acceptable.
+ * The E-vector scratch is a fixed library-owned device array of 4,194,304
+ * doubles (32 MiB), held on every GPU that loads the library until the
+ * process exits. Limit: ne * (p+1)^3 <= 4,194,304, else FEM_EINVAL (use
+ * fem_apply). x, y: device float64 [ndof], caller-owned, not aliased.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture. Every call shares the one array: calls that
+ * overlap on the GPU (other streams or threads) race. The element kernel
+ * rewrites every scratch entry the scatter reads, so nothing is cleared. */
+fem_status fem_apply_noalloc(const fem_form* form, const double* x, double* y,
+                             void* stream);
+
 /* ---- assembled diagonal (needed for Jacobi: PA has no matrix entries,
  * Sec. 4.4 and Sec. 5.2) ----------------------------------------------------
  * diag_i = sum_e sum_q sum_ab D_ab(q) dphi_i/dxhat_a dphi_i/dxhat_b

@@ -63,6 +63,7 @@ SIGNATURES = {
     "fem_apply": (I, [P, I, P, P, I, P]),
     "fem_apply_element": (I, [P, I, P, P, P]),
     "fem_scatter": (I, [P, I, P, P, P]),
+    "fem_apply_noalloc": (I, [P, P, P, P]),
     "fem_assemble_diagonal": (I, [P, P, I, P]),
     "fem_rhs": (I, [P, P, P, P]),
     "fem_qpoint_coords": (I, [P, P, P]),
