@@ -299,7 +299,7 @@ def main():
     traffic_full = measured_traffic(key)
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_full,
-            "kernel": "k_diffusion_apply<double,5,6,4> (FP64 element kernel)",
+            "kernel": f"k_diffusion_apply<double,{p + 1},{q},NE> (FP64 element kernel)",
             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
             "alg_flops_per_launch": flops, "alg_bytes_per_launch": bytes_alg,
             "hbm_achieved_gbs": bytes_alg / (t_el + statistics.mean(t_scat) * 1e-3) / 1e9,

@@ -230,6 +230,50 @@ fem_status fem_lift_rhs(const fem_form* form, const double* b, const double* g,
  * float64 [ne]. */
 fem_status fem_compliance_grad(const fem_form* form, const double* u, double* g,
                                void* stream);
+/* Compliance J = b^T u (deterministic fixed-order FP64 reduction) into J, a
+ * device float64 scalar. b, u: device float64 [ndof]. */
+fem_status fem_compliance(const fem_form* form, const double* b, const double* u, double* J,
+                          void* stream);
+
+/* ---- batching: many independent problems, several right-hand sides each --
+ * (no batched path in the paper; it extends the element-parallel apply of
+ * Sec. 4.3 across problems). A batch refers to nprob forms (any mix of orders,
+ * sizes and kinds; they must outlive the batch) and nrhs right-hand sides per
+ * problem. Batched vectors are concatenated problem after problem; problem
+ * i's block is [nrhs][ndof_i] and starts at nrhs * off[i], off[i] = sum of
+ * ndof_j for j < i (fem_batch_info). System s = i * nrhs + r.
+ * The element phase is one persistent kernel over (problem, element tile)
+ * work items, each applying its tile to all nrhs right-hand sides (D streams
+ * from HBM once per nrhs); the scatter is one persistent kernel over
+ * (problem, DOF chunk) items. Applies and CG iterations run as CUDA graphs.
+ * Orders p = 1..6 (FEM_EUNSUPPORTED otherwise). */
+fem_status fem_batch_create(const fem_form* const* forms, int nprob, int nrhs, void* stream,
+                            fem_batch** out);
+void fem_batch_destroy(fem_batch* batch);
+/* total_len = nrhs * sum ndof; off_host [nprob + 1] (may be NULL). */
+fem_status fem_batch_info(const fem_batch* batch, int64_t* total_len, int64_t* off_host);
+/* Y = A X (or A_c X when constrained != 0: every form needs its essential
+ * DOFs) for all systems; dtype FEM_F64 or FEM_F32 (float copies of D are made
+ * on first use). X, Y: device arrays of total_len entries, not aliased. The
+ * launches are captured once per (X, Y, dtype, constrained) into a CUDA
+ * graph that later calls replay. */
+fem_status fem_batch_apply(fem_batch* batch, int dtype, const void* X, void* Y, int constrained,
+                           void* stream);
+/* Jacobi-PCG for every system (all systems advance together; converged ones
+ * idle), with the stopping rule and precision options of fem_solve applied
+ * per system. B: constrained right-hand sides; X: initial guesses including
+ * essential values (overwritten). iters_host [nsys] and relres_host [nsys]
+ * receive per-system iterations and final true relative residuals (either
+ * may be NULL). Synchronises stream. Errors: FEM_ENOCONV, FEM_EBREAKDOWN. */
+fem_status fem_batch_solve(fem_batch* batch, const double* B, double* X, const fem_solve_opts* opts,
+                           int* iters_host, double* relres_host, void* stream);
+/* Autotuner: for every (p, q) in the batch, times the batched apply with
+ * candidate element tiles (elements per work item) and keeps the fastest;
+ * results are read from / written to the line-per-entry JSON cache at
+ * cache_path (NULL: no cache), keyed by device name, dtype and (p, q). */
+fem_status fem_batch_tune(fem_batch* batch, int dtype, const char* cache_path, void* stream);
+/* Current element tiles: tiles_host [18], entry 2p + (q - p - 1). */
+fem_status fem_batch_tiles(const fem_batch* batch, int* tiles_host);
 
 #ifdef __cplusplus
 }

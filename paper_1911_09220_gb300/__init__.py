@@ -18,7 +18,7 @@ import numpy as np
 from . import _binding as B
 from ._binding import FemError, FEM_DIFFUSION, FEM_MASS, FEM_F64, FEM_F32, FEM_SOLVE_F64, FEM_SOLVE_MIXED
 
-__all__ = ["Mesh", "Space", "Form", "FemError", "lib", "supported", "version"]
+__all__ = ["Mesh", "Space", "Form", "Batch", "FemError", "lib", "supported", "version"]
 
 
 def lib():
@@ -220,7 +220,80 @@ class Form:
                                             _stream(stream)))
         return g
 
+    def compliance(self, b, u, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(1, dtype=torch.float64, device=b.device)
+        B.check(B.lib().fem_compliance(self._h, _ptr(b, torch.float64, "b"), _ptr(u, torch.float64, "u"),
+                                       _ptr(out, torch.float64, "out"), _stream(stream)))
+        return out
+
     def __del__(self):
         if getattr(self, "_h", None) and B._lib is not None:
             B._lib.fem_form_destroy(self._h)
+            self._h = None
+
+
+class Batch:
+    """Many independent problems (forms) with nrhs right-hand sides each.
+    Batched vectors are concatenated problem after problem; problem i's block
+    is [nrhs][ndof_i] starting at nrhs * off[i] (see include/fem.h)."""
+
+    def __init__(self, forms, nrhs, stream=None):
+        L = B.lib()
+        self.forms = list(forms)
+        self.nrhs = int(nrhs)
+        arr = (C.c_void_p * len(self.forms))(*[f._h.value for f in self.forms])
+        h = C.c_void_p()
+        B.check(L.fem_batch_create(arr, len(self.forms), self.nrhs, _stream(stream), C.byref(h)))
+        self._h = h
+        tot = C.c_int64()
+        off = np.zeros(len(self.forms) + 1, dtype=np.int64)
+        B.check(L.fem_batch_info(h, C.byref(tot), off.ctypes.data))
+        self.total_len, self.off = tot.value, off
+        self.nsys = len(self.forms) * self.nrhs
+
+    def block(self, V, i, r):
+        """View of problem i, right-hand side r inside a batched vector."""
+        n = int(self.off[i + 1] - self.off[i])
+        s0 = self.nrhs * int(self.off[i]) + r * n
+        return V[s0:s0 + n]
+
+    def apply(self, X, Y, constrained=False, stream=None):
+        if X.dtype != Y.dtype:
+            raise TypeError("X and Y must have the same dtype")
+        B.check(B.lib().fem_batch_apply(self._h, _dtype_code(X), _ptr(X, name="X"), _ptr(Y, name="Y"),
+                                        int(bool(constrained)), _stream(stream)))
+        return Y
+
+    def solve(self, Bv, X, rtol=1e-10, maxit=20000, precision="f64", inner_rtol=1e-4, max_outer=30,
+              check_every=16, use_graph=True, stream=None, raise_on_error=True):
+        import torch
+        o = B.SolveOpts()
+        B.lib().fem_solve_opts_default(C.byref(o))
+        o.rtol, o.maxit, o.inner_rtol, o.max_outer = rtol, maxit, inner_rtol, max_outer
+        o.precision = FEM_SOLVE_MIXED if precision == "mixed" else FEM_SOLVE_F64
+        o.check_every, o.use_graph = check_every, int(bool(use_graph))
+        iters = np.zeros(self.nsys, dtype=np.int32)
+        rel = np.zeros(self.nsys, dtype=np.float64)
+        st = B.lib().fem_batch_solve(self._h, _ptr(Bv, torch.float64, "B"), _ptr(X, torch.float64, "X"), C.byref(o),
+                                     iters.ctypes.data, rel.ctypes.data, _stream(stream))
+        if st != B.FEM_OK and raise_on_error:
+            raise FemError(st, B.lib().fem_last_error().decode())
+        return {"status": st, "iterations": iters, "relres": rel}
+
+    def tune(self, dtype="f64", cache_path=None, stream=None):
+        code = FEM_F64 if dtype == "f64" else FEM_F32
+        path = None if cache_path is None else str(cache_path).encode()
+        B.check(B.lib().fem_batch_tune(self._h, code, path, _stream(stream)))
+        return self.tiles()
+
+    def tiles(self):
+        t = np.zeros(18, dtype=np.int32)
+        B.check(B.lib().fem_batch_tiles(self._h, t.ctypes.data))
+        return t
+
+    def __del__(self):
+        if getattr(self, "_h", None) and B._lib is not None:
+            B._lib.fem_batch_destroy(self._h)
             self._h = None

@@ -71,6 +71,14 @@ SIGNATURES = {
     "fem_solve": (I, [P, P, P, C.POINTER(SolveOpts), C.POINTER(SolveInfo), P]),
     "fem_lift_rhs": (I, [P, P, P, P, P]),
     "fem_compliance_grad": (I, [P, P, P, P]),
+    "fem_compliance": (I, [P, P, P, P, P]),
+    "fem_batch_create": (I, [P, I, I, P, C.POINTER(P)]),
+    "fem_batch_destroy": (None, [P]),
+    "fem_batch_info": (I, [P, C.POINTER(I64), P]),
+    "fem_batch_apply": (I, [P, I, P, P, I, P]),
+    "fem_batch_solve": (I, [P, P, P, C.POINTER(SolveOpts), P, P, P]),
+    "fem_batch_tune": (I, [P, I, C.c_char_p, P]),
+    "fem_batch_tiles": (I, [P, P]),
 }
 
 _lib = None

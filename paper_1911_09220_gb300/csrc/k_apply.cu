@@ -3,36 +3,19 @@
 // (Sec. 4.4: B_ki = B1d_{k1 i1} B1d_{k2 i2} B1d_{k3 i3}, applied one
 // direction at a time, O(p^{d+1}) operations per element).
 //
-// Element kernel layout: one element per (Q x Q) thread plane, NE elements per
-// block. Thread (qx, qy) owns a column of points along z; contractions along x
-// and y go through shared memory, contractions along z run in registers.
-//   gather   X[z][y][x]          = x_L[e2l[e][z][y][x]]          (G)
-//   stage 1  BX, GX  [z][y][qx]  = sum_x B/G[qx][x] X             (B, x)
-//   stage 2  bb, gb, bg [z]      = sum_y B/G[qy][y] (BX|GX)       (B, y; registers)
-//   stage 3  grad_q              = sum_z B/G[qz][z] (...)         (B, z)
-//   point    v_q = D_q grad_q (D symmetric, 6 components)          (D)
-//   back z   t0,t1,t2 [dz]      += B/G[qz][dz] v                 (B^T, z)
-//   back y   UA, UB [dz][dy][qx] = sum_qy B/G[qy][dy] t           (B^T, y)
-//   back x   Y[dz][dy][dx]       = sum_qx G[qx][dx] UA + B[qx][dx] UB (B^T, x)
-// Y goes to the E-vector; the scatter kernel sums it into the L-vector
-// through the inverse map in a fixed order (atomic-free G^T).
+// The element operators themselves are in k_element.cuh.
 #include "fem_internal.h"
 #include "k_common.cuh"
+#include "k_element.cuh"
 
 namespace {
 
-// Elements per block for each order: about 128-288 threads per block.
-constexpr int ne_per_block(int p) {
-  return p == 1 ? 32 : p == 2 ? 16 : p == 3 ? 8 : p == 4 ? 4 : p == 5 ? 4 : 2;
+// Elements per block for a (Q x Q) thread plane: Q^2 * NE fills whole (or
+// nearly whole) warps, 128-320 threads per block. Inactive lanes still occupy
+// an issued FP64 instruction, so a half-empty last warp costs throughput.
+constexpr int ne_for_q(int Q) {
+  return Q <= 3 ? 32 : Q == 4 ? 16 : Q == 5 ? 5 : Q == 6 ? 8 : Q == 7 ? 5 : Q == 8 ? 4 : 3;
 }
-
-template <int D1, int Q>
-struct Smem {
-  static constexpr int ND = D1 * D1 * D1;
-  static constexpr int SA = ND + 2 * D1 * D1 * Q;          // X, BX, GX
-  static constexpr int SB = 3 * D1 * Q * Q + 2 * D1 * D1 * Q;  // t0..t2, UA, UB
-  static constexpr int SE = SA > SB ? SA : SB;             // per element, in T
-};
 
 template <typename T, int D1, int Q, int NE>
 __global__ void __launch_bounds__(Q * Q * NE)
@@ -52,157 +35,11 @@ k_diffusion_apply(const int* __restrict__ skip, int ne, const int32_t* __restric
   }
   const int e = blockIdx.x * NE + tz;
   const bool valid = e < ne;
-  T* s = sm + tz * SE;
-  T* sX = s;
-  T* sBX = s + ND;
-  T* sGX = sBX + D1 * D1 * Q;
-  if (valid && tx < D1 && ty < D1) {
-    const int32_t* map = e2l + (size_t)e * ND;
-#pragma unroll
-    for (int z = 0; z < D1; ++z) {
-      const int k = (z * D1 + ty) * D1 + tx;
-      sX[k] = __ldg(x + __ldg(map + k));
-    }
-  }
-  __syncthreads();
-  if (ty < D1) {  // stage 1: threads (qx, dy)
-    T b[D1], g[D1];
-#pragma unroll
-    for (int d = 0; d < D1; ++d) {
-      b[d] = sB[tx * D1 + d];
-      g[d] = sG[tx * D1 + d];
-    }
-#pragma unroll
-    for (int z = 0; z < D1; ++z) {
-      T u = 0, v = 0;
-#pragma unroll
-      for (int d = 0; d < D1; ++d) {
-        const T xv = sX[(z * D1 + ty) * D1 + d];
-        u += b[d] * xv;
-        v += g[d] * xv;
-      }
-      sBX[(z * D1 + ty) * Q + tx] = u;
-      sGX[(z * D1 + ty) * Q + tx] = v;
-    }
-  }
-  __syncthreads();
-  T rbb[D1], rgb[D1], rbg[D1];
-  {  // stage 2: threads (qx, qy)
-    T b[D1], g[D1];
-#pragma unroll
-    for (int d = 0; d < D1; ++d) {
-      b[d] = sB[ty * D1 + d];
-      g[d] = sG[ty * D1 + d];
-    }
-#pragma unroll
-    for (int z = 0; z < D1; ++z) {
-      T bb = 0, gb = 0, bg = 0;
-#pragma unroll
-      for (int d = 0; d < D1; ++d) {
-        const T u = sBX[(z * D1 + d) * Q + tx];
-        const T v = sGX[(z * D1 + d) * Q + tx];
-        bb += b[d] * u;
-        gb += b[d] * v;
-        bg += g[d] * u;
-      }
-      rbb[z] = bb;
-      rgb[z] = gb;
-      rbg[z] = bg;
-    }
-  }
-  T t0[D1], t1[D1], t2[D1];
-#pragma unroll
-  for (int d = 0; d < D1; ++d) t0[d] = t1[d] = t2[d] = 0;
-  const T* De = Dq + (size_t)(valid ? e : 0) * 6 * NQ + ty * Q + tx;
-#pragma unroll 2
-  for (int qz = 0; qz < Q; ++qz) {
-    T g0 = 0, g1 = 0, g2 = 0;
-#pragma unroll
-    for (int z = 0; z < D1; ++z) {
-      const T bz = sB[qz * D1 + z], gz = sG[qz * D1 + z];
-      g0 += bz * rgb[z];
-      g1 += bz * rbg[z];
-      g2 += gz * rbb[z];
-    }
-    const int o = qz * Q * Q;
-    T d00 = 0, d01 = 0, d02 = 0, d11 = 0, d12 = 0, d22 = 0;
-    if (valid) {
-      d00 = __ldg(De + 0 * NQ + o);
-      d01 = __ldg(De + 1 * NQ + o);
-      d02 = __ldg(De + 2 * NQ + o);
-      d11 = __ldg(De + 3 * NQ + o);
-      d12 = __ldg(De + 4 * NQ + o);
-      d22 = __ldg(De + 5 * NQ + o);
-    }
-    const T v0 = d00 * g0 + d01 * g1 + d02 * g2;
-    const T v1 = d01 * g0 + d11 * g1 + d12 * g2;
-    const T v2 = d02 * g0 + d12 * g1 + d22 * g2;
-#pragma unroll
-    for (int d = 0; d < D1; ++d) {
-      const T bz = sB[qz * D1 + d], gz = sG[qz * D1 + d];
-      t0[d] += bz * v0;
-      t1[d] += bz * v1;
-      t2[d] += gz * v2;
-    }
-  }
-  __syncthreads();  // phase-A buffers are dead from here on
-  T* sT0 = s;
-  T* sT1 = sT0 + D1 * Q * Q;
-  T* sT2 = sT1 + D1 * Q * Q;
-  T* sUA = sT2 + D1 * Q * Q;
-  T* sUB = sUA + D1 * D1 * Q;
-#pragma unroll
-  for (int d = 0; d < D1; ++d) {
-    const int k = (d * Q + ty) * Q + tx;
-    sT0[k] = t0[d];
-    sT1[k] = t1[d];
-    sT2[k] = t2[d];
-  }
-  __syncthreads();
-  if (ty < D1) {  // back y: threads (qx, dy)
-    T b[Q], g[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      b[q] = sB[q * D1 + ty];
-      g[q] = sG[q * D1 + ty];
-    }
-#pragma unroll
-    for (int dz = 0; dz < D1; ++dz) {
-      T ua = 0, ub = 0;
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const int k = (dz * Q + q) * Q + tx;
-        ua += b[q] * sT0[k];
-        ub += g[q] * sT1[k] + b[q] * sT2[k];
-      }
-      sUA[(dz * D1 + ty) * Q + tx] = ua;
-      sUB[(dz * D1 + ty) * Q + tx] = ub;
-    }
-  }
-  __syncthreads();
-  if (valid && tx < D1 && ty < D1) {  // back x: threads (dx, dy)
-    T b[Q], g[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      b[q] = sB[q * D1 + tx];
-      g[q] = sG[q * D1 + tx];
-    }
-    T* out = ye + (size_t)e * ND;
-#pragma unroll
-    for (int dz = 0; dz < D1; ++dz) {
-      T y = 0;
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const int k = (dz * D1 + ty) * Q + q;
-        y += g[q] * sUA[k] + b[q] * sUB[k];
-      }
-      out[(dz * D1 + ty) * D1 + tx] = y;
-    }
-  }
+  const size_t ev = valid ? (size_t)e : 0;
+  diffusion_element<T, D1, Q>(tx, ty, valid, e2l + ev * ND, Dq + ev * 6 * NQ, sB, sG, sm + tz * SE, x,
+                              ye + ev * ND);
 }
 
-// Mass: the same passes with B only and one scalar D per point
-// (Sec. 4.4, M_E = B^T D_E B).
 template <typename T, int D1, int Q, int NE>
 __global__ void __launch_bounds__(Q * Q * NE)
 k_mass_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
@@ -218,89 +55,8 @@ k_mass_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e
   for (int i = tid; i < Q * D1; i += Q * Q * NE) sB[i] = Bg[i];
   const int e = blockIdx.x * NE + tz;
   const bool valid = e < ne;
-  T* s = sm + tz * SE;
-  T* sX = s;
-  T* sBX = s + ND;
-  if (valid && tx < D1 && ty < D1) {
-    const int32_t* map = e2l + (size_t)e * ND;
-#pragma unroll
-    for (int z = 0; z < D1; ++z) {
-      const int k = (z * D1 + ty) * D1 + tx;
-      sX[k] = __ldg(x + __ldg(map + k));
-    }
-  }
-  __syncthreads();
-  if (ty < D1) {
-    T b[D1];
-#pragma unroll
-    for (int d = 0; d < D1; ++d) b[d] = sB[tx * D1 + d];
-#pragma unroll
-    for (int z = 0; z < D1; ++z) {
-      T u = 0;
-#pragma unroll
-      for (int d = 0; d < D1; ++d) u += b[d] * sX[(z * D1 + ty) * D1 + d];
-      sBX[(z * D1 + ty) * Q + tx] = u;
-    }
-  }
-  __syncthreads();
-  T rbb[D1];
-  {
-    T b[D1];
-#pragma unroll
-    for (int d = 0; d < D1; ++d) b[d] = sB[ty * D1 + d];
-#pragma unroll
-    for (int z = 0; z < D1; ++z) {
-      T bb = 0;
-#pragma unroll
-      for (int d = 0; d < D1; ++d) bb += b[d] * sBX[(z * D1 + d) * Q + tx];
-      rbb[z] = bb;
-    }
-  }
-  T t0[D1];
-#pragma unroll
-  for (int d = 0; d < D1; ++d) t0[d] = 0;
-  const T* De = Dq + (size_t)(valid ? e : 0) * NQ + ty * Q + tx;
-#pragma unroll 2
-  for (int qz = 0; qz < Q; ++qz) {
-    T u = 0;
-#pragma unroll
-    for (int z = 0; z < D1; ++z) u += sB[qz * D1 + z] * rbb[z];
-    const T v = valid ? __ldg(De + qz * Q * Q) * u : T(0);
-#pragma unroll
-    for (int d = 0; d < D1; ++d) t0[d] += sB[qz * D1 + d] * v;
-  }
-  __syncthreads();
-  T* sT0 = s;
-  T* sUA = sT0 + D1 * Q * Q;
-#pragma unroll
-  for (int d = 0; d < D1; ++d) sT0[(d * Q + ty) * Q + tx] = t0[d];
-  __syncthreads();
-  if (ty < D1) {
-    T b[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) b[q] = sB[q * D1 + ty];
-#pragma unroll
-    for (int dz = 0; dz < D1; ++dz) {
-      T ua = 0;
-#pragma unroll
-      for (int q = 0; q < Q; ++q) ua += b[q] * sT0[(dz * Q + q) * Q + tx];
-      sUA[(dz * D1 + ty) * Q + tx] = ua;
-    }
-  }
-  __syncthreads();
-  if (valid && tx < D1 && ty < D1) {
-    T b[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) b[q] = sB[q * D1 + tx];
-    T* out = ye + (size_t)e * ND;
-#pragma unroll
-    for (int dz = 0; dz < D1; ++dz) {
-      T y = 0;
-#pragma unroll
-      for (int q = 0; q < Q; ++q) y += b[q] * sUA[(dz * D1 + ty) * Q + q];
-      out[(dz * D1 + ty) * D1 + tx] = y;
-    }
-  }
+  const size_t ev = valid ? (size_t)e : 0;
+  mass_element<T, D1, Q>(tx, ty, valid, e2l + ev * ND, Dq + ev * NQ, sB, sm + tz * SE, x, ye + ev * ND);
 }
 
 template <typename K>
@@ -312,7 +68,7 @@ fem_status prepare_smem(K kernel, size_t bytes) {
 template <typename T, int P, int Q>
 fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G, const T* x, T* ye,
                            const int* skip, cudaStream_t s) {
-  constexpr int D1 = P + 1, NE = ne_per_block(P);
+  constexpr int D1 = P + 1, NE = ne_for_q(Q);
   const int ne = (int)f->space->ne;
   const dim3 block(Q, Q, NE);
   const int grid = (ne + NE - 1) / NE;

@@ -39,3 +39,8 @@ __device__ inline double block_sum(double v, double* red) {
 #define FEM_FOR_EACH_PQ(X) \
   X(1, 2) X(1, 3) X(2, 3) X(2, 4) X(3, 4) X(3, 5) X(4, 5) X(4, 6) \
   X(5, 6) X(5, 7) X(6, 7) X(6, 8) X(7, 8) X(7, 9) X(8, 9) X(8, 10)
+
+// Orders compiled into the persistent batched kernel (one kernel holds every
+// variant, so its register count is the maximum over them): p = 1..6.
+#define FEM_FOR_EACH_PQ_BATCH(X) \
+  X(1, 2) X(1, 3) X(2, 3) X(2, 4) X(3, 4) X(3, 5) X(4, 5) X(4, 6) X(5, 6) X(5, 7) X(6, 7) X(6, 8)

@@ -342,6 +342,28 @@ fem_status read_doubles(fem_form* f, const double* d, int n, double* h, cudaStre
 
 }  // namespace
 
+__global__ void k_dot_partials(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                               double* __restrict__ part) {
+  __shared__ double red[32];
+  double acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += a[i] * b[i];
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+extern "C" fem_status fem_compliance(const fem_form* fc, const double* b, const double* u, double* J, void* stream) {
+  if (!fc || !b || !u || !J) return fem_fail(FEM_EINVAL, "fem_compliance: NULL argument");
+  fem_form* f = const_cast<fem_form*>(fc);
+  cudaStream_t s = (cudaStream_t)stream;
+  Work w;
+  FEM_TRY(get_work(f, false, w));
+  k_dot_partials<<<w.nb, 256, 0, s>>>(w.n, b, u, w.part);
+  k_sum_to<<<1, kRedThreads, 0, s>>>(w.part, w.nb, J);
+  FEM_LAUNCHED();
+  return FEM_OK;
+}
+
 extern "C" void fem_solve_opts_default(fem_solve_opts* o) {
   if (!o) return;
   o->rtol = 1e-10;

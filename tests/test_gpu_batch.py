@@ -1,0 +1,134 @@
+"""Batched PA applies and Jacobi-PCG over many independent problems (mixed
+orders, sizes and kinds, several right-hand sides each) against the oracle
+and against the single-problem path; the tile autotuner and its cache."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+from fem_inputs import lognormal, x_uniform, splitmix64
+from oracle import assemble, solve as osolve
+
+from gpu_util import cuda, make_mesh, relerr
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1911_09220_gb300 import build
+    build.build()
+
+
+def _batch(nprob=10, nrhs=3, seed=300, kinds=("diffusion",), oracle=True, Nmax=4):
+    import paper_1911_09220_gb300 as F
+    draws = splitmix64(seed, 3 * nprob)
+    probs = []
+    for i in range(nprob):
+        N = 1 + int(draws[3 * i] % np.uint64(Nmax))
+        p = 1 + int(draws[3 * i + 1] % np.uint64(6))
+        kind = kinds[int(draws[3 * i + 2] % np.uint64(len(kinds)))]
+        c, h = make_mesh(N, seed=seed + i, shuffle=(i % 2 == 1), drop=(1 if N > 1 and i % 3 == 0 else 0))
+        kappa = lognormal(seed + 100 + i, h.shape[0])
+        mesh = F.Mesh(c, h)
+        space = F.Space(mesh, p)
+        form = F.Form(space, kind, p + 2, coef=cuda(kappa))
+        prob = assemble.Problem(c, h, p, p + 2, kappa=kappa, rho=kappa) if oracle else None
+        probs.append(dict(mesh=mesh, space=space, form=form, prob=prob, kind=kind, p=p))
+    return probs, F.Batch([q["form"] for q in probs], nrhs)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batched_apply_matches_oracle_and_single(dtype):
+    import torch
+    probs, bt = _batch(kinds=("diffusion", "mass"))
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    X = cuda(x_uniform(301, bt.total_len), tdt)
+    Y = torch.full_like(X, np.nan)
+    bt.apply(X, Y)
+    bt.apply(X, Y)   # graph replay
+    for i, q in enumerate(probs):
+        for r in range(bt.nrhs):
+            x = bt.block(X, i, r).contiguous()
+            y1 = torch.empty_like(x)
+            q["form"].apply(x, y1)
+            yb = bt.block(Y, i, r)
+            assert relerr(yb.cpu().double().numpy(), y1.cpu().double().numpy()) <= (TOL if dtype == "f64" else 1e-6)
+            if dtype == "f64":
+                ref = q["prob"].apply(q["kind"], x.cpu().numpy())
+                assert relerr(yb.cpu().numpy(), ref) <= TOL
+
+
+def test_batched_constrained_apply():
+    import torch
+    probs, bt = _batch(nprob=6, nrhs=2, seed=320)
+    for q in probs:
+        q["form"].set_essential(q["prob"].num["boundary_dofs"])
+    X = cuda(x_uniform(321, bt.total_len))
+    Y = torch.empty_like(X)
+    bt.apply(X, Y, constrained=True)
+    for i, q in enumerate(probs):
+        Ac = osolve.constrain(q["prob"].K, q["prob"].num["boundary_dofs"])
+        for r in range(bt.nrhs):
+            ref = Ac @ bt.block(X, i, r).cpu().numpy()
+            assert relerr(bt.block(Y, i, r).cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_batched_solve(precision):
+    import torch
+    probs, bt = _batch(nprob=8, nrhs=3, seed=340)
+    Bc = torch.empty(bt.total_len, dtype=torch.float64, device="cuda")
+    raw = cuda(x_uniform(341, bt.total_len))
+    for i, q in enumerate(probs):
+        q["form"].set_essential(q["prob"].num["boundary_dofs"])
+        for r in range(bt.nrhs):
+            q["form"].lift_rhs(bt.block(raw, i, r).contiguous(), torch.zeros(q["space"].ndof, dtype=torch.float64,
+                                                                              device="cuda"), bt.block(Bc, i, r))
+    X = torch.zeros_like(Bc)
+    info = bt.solve(Bc, X, rtol=1e-10, precision=precision, check_every=8)
+    assert np.all(info["relres"] <= 1e-10)
+    for i, q in enumerate(probs):
+        ess = q["prob"].num["boundary_dofs"]
+        Ac = osolve.constrain(q["prob"].K, ess)
+        for r in range(bt.nrhs):
+            b = osolve.constrain_rhs(q["prob"].K, bt.block(raw, i, r).cpu().numpy(), ess)
+            u = bt.block(X, i, r).cpu().numpy()
+            assert np.linalg.norm(b - Ac @ u) / np.linalg.norm(b) <= 1.01e-10, (i, r)
+
+
+def test_autotuner_cache(tmp_path):
+    import torch
+    probs, bt = _batch(nprob=6, nrhs=2, seed=360, oracle=False)
+    X = cuda(x_uniform(361, bt.total_len))
+    Y0 = torch.empty_like(X)
+    bt.apply(X, Y0)
+    path = tmp_path / "tiles.json"
+    tiles = bt.tune("f64", path)
+    lines = [json.loads(l) for l in open(path)]
+    ps = sorted({(q["p"], q["p"] + 2) for q in probs})
+    assert len(lines) == len(ps)
+    for p, q in ps:
+        t = tiles[2 * p + 1]
+        assert 1 <= t <= 256 // (q * q)
+    Y1 = torch.empty_like(X)
+    bt.apply(X, Y1)
+    assert torch.equal(Y0, Y1)        # tiles change the schedule, not the arithmetic
+    # a second tuning reads the cache
+    tiles2 = bt.tune("f64", path)
+    assert np.array_equal(tiles, tiles2)
+
+
+def test_batch_rejects_high_order():
+    import paper_1911_09220_gb300 as F
+    c, h = make_mesh(1)
+    form = F.Form(F.Space(F.Mesh(c, h), 7), "diffusion", 9)
+    with pytest.raises(F.FemError) as ei:
+        F.Batch([form], 2)
+    assert "FEM_EUNSUPPORTED" in str(ei.value)
