@@ -33,7 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_element_kernel.txt")
 # FP64 FMA rate of a GB300 SM: 2 DFMA per clock per SM (derived from the
 # nominal 1.25 TFLOP/s; a DFMA microbenchmark on the box measured 1.19 TFLOP/s
 # at ~1.96 GHz). Peak = 152 SMs x 2 DFMA x 2 flop x 2070 MHz.
@@ -129,6 +129,23 @@ def peaks():
         return {"hbm_gbs": 6800.0, "fallback": True}
 
 
+def time_events(fn, steps, warmup):
+    """Average device time (ms) of fn() over `steps` calls after `warmup`
+    calls, with CUDA events on the current stream."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
 def make_problem(p, N, seed_offset=0):
     from fem_inputs import hex_lattice, lognormal, x_uniform
     c, h = hex_lattice(N, 0.15, seed=10 + p + seed_offset)
@@ -185,6 +202,205 @@ def run_reference(args):
     return 0
 
 
+SWEEP_N = {"4e6": {1: 158, 2: 79, 3: 53, 4: 39, 5: 32, 6: 26, 7: 23, 8: 20},
+           "2e7": {1: 270, 2: 135, 3: 90, 4: 68, 5: 54, 6: 45, 7: 39, 8: 34}}
+
+
+def _sin_rhs(form, b):
+    import torch
+    xq = form.qpoint_coords()
+    fq = (3 * np.pi ** 2 * torch.sin(np.pi * xq[..., 0]) * torch.sin(np.pi * xq[..., 1])
+          * torch.sin(np.pi * xq[..., 2])).contiguous()
+    del xq
+    form.rhs(fq, b)
+
+
+def run_sweep(args):
+    """One JSON line per order p: FP64/FP32 mass and diffusion applies, setup,
+    diagonal, load vector and FP64 / mixed Jacobi-PCG to 1e-10."""
+    import torch
+    from paper_1911_09220_gb300 import build as fbuild
+    fbuild.build()
+    import paper_1911_09220_gb300 as F
+    orders = [int(v) for v in args.orders.split(",")]
+    for p in orders:
+        N = SWEEP_N[args.sweep_size][p]
+        q = p + 2
+        c, h, kappa, xgen = make_problem(p, N)
+        t0 = time.perf_counter()
+        space = F.Space(F.Mesh(c, h), p)
+        t_space = time.perf_counter() - t0
+        n, E = space.ndof, space.ne
+        kap = torch.as_tensor(kappa, device="cuda")
+        x = torch.as_tensor(xgen(n), device="cuda")
+        y = torch.empty_like(x)
+        out = {"p": p, "q1d": q, "N": N, "ndof": n, "elements": E, "space_host_s": t_space}
+        for kind in ("diffusion", "mass"):
+            form = F.Form(space, kind, q, coef=kap)
+            tset = time_events(lambda: form.set_coef(kap), 2, 1)
+            flops, bytes64 = alg_counts(p, q, E, n, kind=kind)
+            _, bytes32 = alg_counts(p, q, E, n, kind=kind, fp=4)
+            t64 = time_events(lambda: form.apply(x, y), args.steps, 3)
+            x32 = x.float()
+            y32 = torch.empty_like(x32)
+            t32 = time_events(lambda: form.apply(x32, y32), args.steps, 3)
+            d = torch.empty_like(x)
+            tdiag = time_events(lambda: form.diagonal(d), 3, 1)
+            out[kind] = {
+                "f64_gdofs": n / t64 * 1e-6, "f64_ms": t64, "f64_tflops": flops / t64 * 1e-9,
+                "f64_frac_fp64_peak": flops / t64 * 1e-9 / FP64_PEAK_TFLOPS,
+                "f32_gdofs": n / t32 * 1e-6, "f32_ms": t32, "f32_alg_gbs": bytes32 / t32 * 1e-6,
+                "f32_frac_hbm": bytes32 / t32 * 1e-6 / peaks().get("hbm_gbs", 6800.0),
+                "setup_ms": tset, "diag_ms": tdiag}
+            if kind == "diffusion":
+                b = torch.empty_like(x)
+                out["rhs_ms"] = time_events(lambda: _sin_rhs(form, b), 2, 1)
+                if not args.no_solve:
+                    form.set_essential(torch.as_tensor(space.boundary_dofs(), device="cuda"))
+                    bc = torch.empty_like(b)
+                    form.lift_rhs(b, torch.zeros_like(b), bc)
+                    sol = {}
+                    for prec in ("f64", "mixed"):
+                        u = torch.zeros_like(b)
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        info = form.solve(bc, u, rtol=1e-10, maxit=args.solve_maxit, precision=prec,
+                                          raise_on_error=False)
+                        torch.cuda.synchronize()
+                        sol[prec] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
+                                     "outer": info["outer"], "relres": info["relres"],
+                                     "converged": info["converged"]}
+                    sol["speedup_mixed"] = sol["f64"]["seconds"] / sol["mixed"]["seconds"]
+                    out["solve"] = sol
+            del form, x32, y32, d
+        print(json.dumps(out), flush=True)
+        del space, x, y
+        torch.cuda.empty_cache()
+    return 0
+
+
+def batch_config(seed=40, nprob=256):
+    """Seeded sizes of the batching workload: N_i ~ U{2..24}, p_i ~ U{1..6}."""
+    from fem_inputs import splitmix64
+    d = splitmix64(seed, 2 * nprob)
+    Ns = [2 + int(v % np.uint64(23)) for v in d[0::2]]
+    ps = [1 + int(v % np.uint64(6)) for v in d[1::2]]
+    return Ns, ps
+
+
+def run_batch(args):
+    """Batching workload: 256 independent diffusion problems, N_i^3 elements
+    (N_i ~ U{2..24}), p_i ~ U{1..6}, q = p + 2, lognormal kappa, 8 right-hand
+    sides each, x ~ U[-1, 1]; FP64 and FP32 batched applies (one persistent
+    element launch + one persistent scatter launch, one CUDA graph), tile
+    autotuning, and the mixed-precision batched solve."""
+    import torch
+    from paper_1911_09220_gb300 import build as fbuild
+    fbuild.build()
+    import paper_1911_09220_gb300 as F
+    from fem_inputs import hex_lattice, lognormal, x_uniform
+    Ns, ps = batch_config(nprob=args.nprob)
+    nrhs = args.nrhs
+    forms, keep = [], []
+    t0 = time.perf_counter()
+    for i, (N, p) in enumerate(zip(Ns, ps)):
+        c, h = hex_lattice(N, 0.15, seed=4000 + i)
+        kappa = lognormal(5000 + i, h.shape[0])
+        sp = F.Space(F.Mesh(c, h), p)
+        fm = F.Form(sp, "diffusion", p + 2, coef=torch.as_tensor(kappa, device="cuda"))
+        forms.append(fm)
+        keep.append(sp)
+    t_setup = time.perf_counter() - t0
+    bt = F.Batch(forms, nrhs)
+    ndof = int(bt.off[-1])
+    E = sum(sp.ne for sp in keep)
+    flops = sum(alg_counts(sp.p, sp.p + 2, sp.ne, sp.ndof)[0] for sp in keep) * nrhs
+    bytes64 = sum(alg_counts(sp.p, sp.p + 2, sp.ne, sp.ndof)[1] - 16 * sp.ndof for sp in keep) + 16 * ndof * nrhs
+    X = torch.as_tensor(x_uniform(41, bt.total_len), device="cuda")
+    Y = torch.empty_like(X)
+    out = {"workload": f"batch: {len(forms)} diffusion problems, N_i~U{{2..24}}, p_i~U{{1..6}}, {nrhs} RHS",
+           "problems": len(forms), "nrhs": nrhs, "ndof_total": ndof, "unknowns": bt.total_len, "elements": E,
+           "host_setup_s": t_setup}
+    cache = os.path.join(tempfile.gettempdir(), "fem_batch_tiles.json")
+    t0 = time.perf_counter()
+    tiles32 = bt.tune("f32", cache)
+    out["tune_f32_s"] = time.perf_counter() - t0
+    out["tiles"] = {f"p{p}q{p + 2}": int(tiles32[2 * p + 1]) for p in sorted(set(ps))}
+    for dt, tdt in (("f32", torch.float32), ("f64", torch.float64)):
+        Xd = X.to(tdt)
+        Yd = torch.empty_like(Xd)
+        t = time_events(lambda: bt.apply(Xd, Yd), args.steps, 2)
+        rec = {"ms": t, "gdofs": bt.total_len / t * 1e-6}
+        if dt == "f64":
+            rec["tflops"] = flops / t * 1e-9
+            rec["frac_fp64_peak"] = flops / t * 1e-9 / FP64_PEAK_TFLOPS
+        else:
+            b32 = bytes64 / 2
+            rec["alg_gbs"] = b32 / t * 1e-6
+        out[f"apply_{dt}"] = rec
+        del Xd, Yd
+    if not args.no_solve:
+        for fm, sp in zip(forms, keep):
+            fm.set_essential(torch.as_tensor(sp.boundary_dofs(), device="cuda"))
+        Bc = torch.empty_like(X)
+        for i, (fm, sp) in enumerate(zip(forms, keep)):
+            zero = torch.zeros(sp.ndof, dtype=torch.float64, device="cuda")
+            for r in range(nrhs):
+                fm.lift_rhs(bt.block(X, i, r).contiguous(), zero, bt.block(Bc, i, r))
+        precs = ["mixed"] + (["f64"] if args.batch_f64_solve else [])
+        for prec in precs:
+            U = torch.zeros_like(Bc)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = bt.solve(Bc, U, rtol=1e-10, precision=prec, maxit=args.solve_maxit, raise_on_error=False)
+            torch.cuda.synchronize()
+            out[f"solve_{prec}"] = {"seconds": time.perf_counter() - t0, "status": info["status"],
+                                    "max_iterations": int(info["iterations"].max()),
+                                    "mean_iterations": float(info["iterations"].mean()),
+                                    "max_relres": float(info["relres"].max())}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_grad(args):
+    """Differentiation workload: 64^3 hexes, 0.1h, p = 2, kappa = 0.01 + rho^3,
+    rho ~ U[0.2, 1], f = 1, homogeneous Dirichlet: compliance solve and the
+    adjoint-kernel gradient through torch.autograd."""
+    import torch
+    from paper_1911_09220_gb300 import build as fbuild
+    fbuild.build()
+    import paper_1911_09220_gb300 as F
+    from paper_1911_09220_gb300.autograd import compliance
+    from fem_inputs import hex_lattice, rho_uniform
+    c, h = hex_lattice(64, 0.1, seed=50)
+    E = h.shape[0]
+    rho = torch.as_tensor(rho_uniform(50, E), device="cuda")
+    space = F.Space(F.Mesh(c, h), 2)
+    form = F.Form(space, "diffusion", 4, coef=0.01 + rho ** 3)
+    form.set_essential(torch.as_tensor(space.boundary_dofs(), device="cuda"))
+    fq = torch.ones((E, form.nq), dtype=torch.float64, device="cuda")
+    b = torch.empty(space.ndof, dtype=torch.float64, device="cuda")
+    form.rhs(fq, b)
+    bc = torch.empty_like(b)
+    form.lift_rhs(b, torch.zeros_like(b), bc)
+    out = {"workload": "compliance gradient, 64^3 hexes, p=2, q=4", "ndof": space.ndof, "elements": E}
+    for prec in ("f64", "mixed"):
+        r = rho.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, u = compliance(0.01 + r ** 3, form, bc, rtol=1e-10, precision=prec)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        J.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        out[prec] = {"forward_s": t1 - t0, "backward_s": t2 - t1, "J": J.item()}
+    g = torch.empty(E, dtype=torch.float64, device="cuda")
+    out["grad_kernel_ms"] = time_events(lambda: form.compliance_grad(u, g), args.steps, 2)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -197,9 +413,21 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--solve-maxit", type=int, default=20000)
+    ap.add_argument("--workload", default="apply", choices=["apply", "sweep", "batch", "grad"])
+    ap.add_argument("--sweep-size", default="4e6", choices=["4e6", "2e7"])
+    ap.add_argument("--orders", default="1,2,3,4,5,6,7,8")
+    ap.add_argument("--nprob", type=int, default=256)
+    ap.add_argument("--nrhs", type=int, default=8)
+    ap.add_argument("--batch-f64-solve", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "grad":
+        return run_grad(args)
 
     import torch
     import torch.distributed as dist
@@ -307,6 +535,28 @@ def main():
             "element_kernel_ms": statistics.mean(t_elem), "scatter_kernel_ms": statistics.mean(t_scat),
             "element_share": statistics.mean(t_elem) / (statistics.mean(t_elem) + statistics.mean(t_scat))}
 
+    # FP32 apply of the same operator (the inner operator of the mixed solver)
+    x32 = x.float()
+    y32 = torch.empty_like(x32)
+    ye32 = torch.empty((E, (p + 1) ** 3), dtype=torch.float32, device=dev)
+    form.apply(x32, y32)
+    t32e = time_events(lambda: form.apply_element(x32, ye32), args.steps, 2)
+    t32 = time_events(lambda: form.apply(x32, y32), args.steps, 2)
+    _, bytes32 = alg_counts(p, q, E, n, fp=4)
+    fp32 = {"gdofs": n / (t32 * 1e-3) / 1e9, "ms_per_apply": t32, "element_kernel_ms": t32e,
+            "element_kernel_hbm_gbs": (bytes32 - 8 * n + 4 * n) / (t32e * 1e-3) / 1e9,
+            "apply_alg_gbs": bytes32 / (t32 * 1e-3) / 1e9,
+            "apply_frac_of_hbm": bytes32 / (t32 * 1e-3) / 1e9 / peaks().get("hbm_gbs", 6800.0),
+            "alg_bytes_per_apply": bytes32}
+    del x32, y32, ye32
+    # FP64 mass apply on the same mesh and coefficient
+    mform = F.Form(space, "mass", q, coef=kap)
+    tm = time_events(lambda: mform.apply(x, y), args.steps, 2)
+    mflops, mbytes = alg_counts(p, q, E, n, kind="mass")
+    mass = {"gdofs": n / (tm * 1e-3) / 1e9, "ms_per_apply": tm, "achieved_tflops": mflops / (tm * 1e-3) / 1e12,
+            "frac_fp64_peak": mflops / (tm * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+    del mform
+
     solve = None
     if not args.no_solve:
         solve = {}
@@ -355,6 +605,7 @@ def main():
                        "elements": E, "parallelism": f"replicas x{world} (independent problems)",
                        "l2": "inputs larger than L2 (D alone 3.26 GB); no flush"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "fp32_apply": fp32, "mass_apply_f64": mass,
             "clocks": clk, "solve": solve,
             "setup_s": {"space_host": t_space, "form_setup": t_setup},
         }

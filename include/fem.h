@@ -68,8 +68,14 @@ enum {
 };
 
 enum { FEM_MASS = 0, FEM_DIFFUSION = 1 };       /* bilinear form kind */
-enum { FEM_F64 = 0, FEM_F32 = 1 };              /* vector / compute dtype */
-enum { FEM_SOLVE_F64 = 0, FEM_SOLVE_MIXED = 1 }; /* solve precision */
+/* Vector / compute type. FEM_DF64: float64 vectors, element arithmetic in
+ * double-float (pairs of floats, 48-bit significand, on the FP32 pipe) with a
+ * double-float copy of D made on first use; the operator agrees with the FP64
+ * one to about 1e-13 relative (values must stay within about 1e+-30). */
+enum { FEM_F64 = 0, FEM_F32 = 1, FEM_DF64 = 2 };
+/* Solve precision: FP64 CG; FP32 inner CG in FP64 refinement; FP64 CG whose
+ * operator applies run in double-float (FEM_DF64). */
+enum { FEM_SOLVE_F64 = 0, FEM_SOLVE_MIXED = 1, FEM_SOLVE_DF64 = 2 };
 
 typedef struct fem_mesh fem_mesh;
 typedef struct fem_space fem_space;
@@ -139,13 +145,15 @@ fem_status fem_form_set_essential(fem_form* form, const int32_t* ess, int64_t n,
  * y = A x (overwrite; MFEM's AddMultPA adds, this call does not).
  * dtype FEM_F64: x, y float64, D float64 (the FP64 path).
  * dtype FEM_F32: x, y float32 with a float32 copy of D made on first use.
+ * dtype FEM_DF64: x, y float64, element arithmetic in double-float.
  * constrained != 0 applies A_c (needs fem_form_set_essential).
  * Runs the element kernel (gather, B/G contractions, D, B^T/G^T) into the
  * form's E-vector scratch and the inverse-map scatter into y. */
 fem_status fem_apply(const fem_form* form, int dtype, const void* x, void* y,
                      int constrained, void* stream);
 /* The two halves of fem_apply with a caller-provided E-vector
- * ye [ne][(p+1)^3] of the same dtype: element kernel, then scatter. */
+ * ye [ne][(p+1)^3] of the vector dtype (float64 for FEM_DF64): element
+ * kernel, then scatter. */
 fem_status fem_apply_element(const fem_form* form, int dtype, const void* x,
                              void* ye, void* stream);
 fem_status fem_scatter(const fem_form* form, int dtype, const void* ye, void* y,

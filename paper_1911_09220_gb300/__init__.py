@@ -16,7 +16,8 @@ import ctypes as C
 import numpy as np
 
 from . import _binding as B
-from ._binding import FemError, FEM_DIFFUSION, FEM_MASS, FEM_F64, FEM_F32, FEM_SOLVE_F64, FEM_SOLVE_MIXED
+from ._binding import (FemError, FEM_DIFFUSION, FEM_MASS, FEM_F64, FEM_F32, FEM_DF64, FEM_SOLVE_F64,
+                       FEM_SOLVE_MIXED, FEM_SOLVE_DF64)
 
 __all__ = ["Mesh", "Space", "Form", "Batch", "FemError", "lib", "supported", "version"]
 
@@ -156,16 +157,29 @@ class Form:
                                                self.ess.numel(), _stream(stream)))
 
     # ---- operator
-    def apply(self, x, y, constrained=False, stream=None):
+    @staticmethod
+    def _code(x, arith):
+        if arith is None:
+            return _dtype_code(x)
+        if arith == "df64":
+            import torch
+            if x.dtype != torch.float64:
+                raise TypeError("arith='df64' takes float64 vectors")
+            return FEM_DF64
+        raise ValueError(f"unknown arith {arith!r}")
+
+    def apply(self, x, y, constrained=False, stream=None, arith=None):
+        """y = A x. arith=None computes in the tensors' dtype; arith='df64'
+        takes float64 vectors and computes in double-float."""
         if x.dtype != y.dtype:
             raise TypeError("x and y must have the same dtype")
-        B.check(B.lib().fem_apply(self._h, _dtype_code(x), _ptr(x, name="x"), _ptr(y, name="y"),
+        B.check(B.lib().fem_apply(self._h, self._code(x, arith), _ptr(x, name="x"), _ptr(y, name="y"),
                                   int(bool(constrained)), _stream(stream)))
         return y
 
-    def apply_element(self, x, ye, stream=None):
-        B.check(B.lib().fem_apply_element(self._h, _dtype_code(x), _ptr(x, name="x"), _ptr(ye, x.dtype, "ye"),
-                                          _stream(stream)))
+    def apply_element(self, x, ye, stream=None, arith=None):
+        B.check(B.lib().fem_apply_element(self._h, self._code(x, arith), _ptr(x, name="x"),
+                                          _ptr(ye, x.dtype, "ye"), _stream(stream)))
         return ye
 
     def scatter(self, ye, y, stream=None):
@@ -203,7 +217,7 @@ class Form:
         o = B.SolveOpts()
         B.lib().fem_solve_opts_default(C.byref(o))
         o.rtol, o.maxit, o.inner_rtol, o.max_outer = rtol, maxit, inner_rtol, max_outer
-        o.precision = FEM_SOLVE_MIXED if precision == "mixed" else FEM_SOLVE_F64
+        o.precision = {"f64": FEM_SOLVE_F64, "mixed": FEM_SOLVE_MIXED, "df64": FEM_SOLVE_DF64}[precision]
         o.check_every, o.use_graph = check_every, int(bool(use_graph))
         info = B.SolveInfo()
         st = B.lib().fem_solve(self._h, _ptr(b, torch.float64, "b"), _ptr(x, torch.float64, "x"), C.byref(o),

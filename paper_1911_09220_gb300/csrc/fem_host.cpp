@@ -369,6 +369,14 @@ extern "C" fem_status fem_form_create(const fem_space* sp, int kind, int q1d, co
   fem_gauss_rule(q1d, pts, wts);
   fem_lagrange_tables(sp->nodes, pts, B, G);
   std::vector<float> B32(B.begin(), B.end()), G32(G.begin(), G.end());
+  // double-float pairs: hi = fl32(v), lo = fl32(v - hi)
+  std::vector<float> Bdf(2 * B.size()), Gdf(2 * G.size());
+  for (size_t i = 0; i < B.size(); ++i) {
+    Bdf[2 * i] = (float)B[i];
+    Bdf[2 * i + 1] = (float)(B[i] - (double)Bdf[2 * i]);
+    Gdf[2 * i] = (float)G[i];
+    Gdf[2 * i + 1] = (float)(G[i] - (double)Gdf[2 * i]);
+  }
   fem_status st = FEM_OK;
   auto up = [&](auto** dst, const auto& src) {
     if (st != FEM_OK) return;
@@ -381,6 +389,8 @@ extern "C" fem_status fem_form_create(const fem_space* sp, int kind, int q1d, co
   up(&f->d_G, G);
   up(&f->d_B32, B32);
   up(&f->d_G32, G32);
+  up(&f->d_Bdf, Bdf);
+  up(&f->d_Gdf, Gdf);
   up(&f->d_qpts, pts);
   up(&f->d_qwts, wts);
   if (st == FEM_OK) st = dev_alloc(&f->d_coef, (size_t)sp->ne);
@@ -418,7 +428,8 @@ extern "C" fem_status fem_form_set_coef(fem_form* f, const double* coef, void* s
   FEM_TRY(fem_launch_setup(f, s));
   FEM_CUDA(cudaMemcpyAsync(f->h_pinned, f->d_flag, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
   FEM_CUDA(cudaStreamSynchronize(s));
-  dev_free(f->d_D32);  // any float copy is stale now
+  dev_free(f->d_D32);  // any float / double-float copy is stale now
+  dev_free(f->d_Ddf);
   if (f->h_pinned[0] != 0)
     return fem_fail(FEM_EINVERTED, "fem_form: det J <= 0 at a quadrature point of element %d",
                     f->h_pinned[1]);
@@ -434,6 +445,9 @@ extern "C" void fem_form_destroy(fem_form* f) {
   dev_free(f->d_G);
   dev_free(f->d_B32);
   dev_free(f->d_G32);
+  dev_free(f->d_Bdf);
+  dev_free(f->d_Gdf);
+  dev_free(f->d_Ddf);
   dev_free(f->d_qpts);
   dev_free(f->d_qwts);
   if (f->d_ye) cudaFree(f->d_ye);

@@ -78,6 +78,9 @@ struct fem_form {
   double* d_G = nullptr;           // [q1d][D1] derivatives
   float* d_B32 = nullptr;
   float* d_G32 = nullptr;
+  float* d_Bdf = nullptr;          // [q1d][D1] double-float pairs (hi, lo)
+  float* d_Gdf = nullptr;
+  float* d_Ddf = nullptr;          // lazily made double-float copy of D (pairs)
   double* d_qpts = nullptr;        // [q1d]
   double* d_qwts = nullptr;        // [q1d]
   void* d_ye = nullptr;            // E-vector scratch, ne*nd doubles
@@ -122,5 +125,6 @@ fem_status fem_launch_rhs_element(const fem_form* f, const double* fq, double* y
                                   cudaStream_t s);
 fem_status fem_launch_grad(const fem_form* f, const double* u, double* g, cudaStream_t s);
 fem_status fem_form_ensure_f32(const fem_form* f, cudaStream_t s);
+fem_status fem_form_ensure_df64(const fem_form* f, cudaStream_t s);
 fem_status fem_launch_mark_ess(const fem_form* f, cudaStream_t s);
 int fem_scatter_blocks(int64_t ndof);

@@ -17,11 +17,11 @@ constexpr int ne_for_q(int Q) {
   return Q <= 3 ? 32 : Q == 4 ? 16 : Q == 5 ? 5 : Q == 6 ? 8 : Q == 7 ? 5 : Q == 8 ? 4 : 3;
 }
 
-template <typename T, int D1, int Q, int NE>
+template <typename T, int D1, int Q, int NE, typename TX>
 __global__ void __launch_bounds__(Q * Q * NE)
 k_diffusion_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
                   const T* __restrict__ Dq, const T* __restrict__ Bg, const T* __restrict__ Gg,
-                  const T* __restrict__ x, T* __restrict__ ye) {
+                  const TX* __restrict__ x, TX* __restrict__ ye) {
   constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = Smem<D1, Q>::SE;
   if (skip && *skip) return;  // a captured solver iteration after convergence
   __shared__ T sB[Q * D1], sG[Q * D1];
@@ -30,21 +30,21 @@ k_diffusion_apply(const int* __restrict__ skip, int ne, const int32_t* __restric
   const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
   const int tid = tx + Q * (ty + Q * tz);
   for (int i = tid; i < Q * D1; i += Q * Q * NE) {
-    sB[i] = Bg[i];
-    sG[i] = Gg[i];
+    sB[i] = fe_ldg(Bg + i);
+    sG[i] = fe_ldg(Gg + i);
   }
   const int e = blockIdx.x * NE + tz;
   const bool valid = e < ne;
   const size_t ev = valid ? (size_t)e : 0;
-  diffusion_element<T, D1, Q>(tx, ty, valid, e2l + ev * ND, Dq + ev * 6 * NQ, sB, sG, sm + tz * SE, x,
+  diffusion_element<T, D1, Q, TX>(tx, ty, valid, e2l + ev * ND, Dq + ev * 6 * NQ, sB, sG, sm + tz * SE, x,
                               ye + ev * ND);
 }
 
-template <typename T, int D1, int Q, int NE>
+template <typename T, int D1, int Q, int NE, typename TX>
 __global__ void __launch_bounds__(Q * Q * NE)
 k_mass_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
-             const T* __restrict__ Dq, const T* __restrict__ Bg, const T* __restrict__ x,
-             T* __restrict__ ye) {
+             const T* __restrict__ Dq, const T* __restrict__ Bg, const TX* __restrict__ x,
+             TX* __restrict__ ye) {
   constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = Smem<D1, Q>::SE;
   if (skip && *skip) return;
   __shared__ T sB[Q * D1];
@@ -52,11 +52,11 @@ k_mass_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
   const int tid = tx + Q * (ty + Q * tz);
-  for (int i = tid; i < Q * D1; i += Q * Q * NE) sB[i] = Bg[i];
+  for (int i = tid; i < Q * D1; i += Q * Q * NE) sB[i] = fe_ldg(Bg + i);
   const int e = blockIdx.x * NE + tz;
   const bool valid = e < ne;
   const size_t ev = valid ? (size_t)e : 0;
-  mass_element<T, D1, Q>(tx, ty, valid, e2l + ev * ND, Dq + ev * NQ, sB, sm + tz * SE, x, ye + ev * ND);
+  mass_element<T, D1, Q, TX>(tx, ty, valid, e2l + ev * ND, Dq + ev * NQ, sB, sm + tz * SE, x, ye + ev * ND);
 }
 
 template <typename K>
@@ -65,8 +65,8 @@ fem_status prepare_smem(K kernel, size_t bytes) {
   return FEM_OK;
 }
 
-template <typename T, int P, int Q>
-fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G, const T* x, T* ye,
+template <typename T, int P, int Q, typename TX = T>
+fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G, const TX* x, TX* ye,
                            const int* skip, cudaStream_t s) {
   constexpr int D1 = P + 1, NE = ne_for_q(Q);
   const int ne = (int)f->space->ne;
@@ -74,11 +74,11 @@ fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G
   const int grid = (ne + NE - 1) / NE;
   const size_t bytes = sizeof(T) * NE * Smem<D1, Q>::SE;
   if (f->kind == FEM_DIFFUSION) {
-    auto kern = k_diffusion_apply<T, D1, Q, NE>;
+    auto kern = k_diffusion_apply<T, D1, Q, NE, TX>;
     FEM_TRY(prepare_smem(kern, bytes));
     kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, B, G, x, ye);
   } else {
-    auto kern = k_mass_apply<T, D1, Q, NE>;
+    auto kern = k_mass_apply<T, D1, Q, NE, TX>;
     FEM_TRY(prepare_smem(kern, bytes));
     kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, B, x, ye);
   }
@@ -122,6 +122,11 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restr
     b[i] = (float)a[i];
 }
 
+__global__ void k_to_df64(int64_t n, const double* __restrict__ a, df64* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = df64(a[i]);
+}
+
 }  // namespace
 
 int fem_sm_count() {
@@ -156,6 +161,16 @@ fem_status fem_form_ensure_f32(const fem_form* fc, cudaStream_t s) {
   return FEM_OK;
 }
 
+fem_status fem_form_ensure_df64(const fem_form* fc, cudaStream_t s) {
+  fem_form* f = const_cast<fem_form*>(fc);
+  if (f->d_Ddf) return FEM_OK;
+  const size_t n = (size_t)f->space->ne * f->ncomp * f->nq;
+  FEM_TRY(dev_alloc(&f->d_Ddf, 2 * n));
+  k_to_df64<<<grid_for((int64_t)n, 256), 256, 0, s>>>((int64_t)n, f->d_D, reinterpret_cast<df64*>(f->d_Ddf));
+  FEM_LAUNCHED();
+  return FEM_OK;
+}
+
 fem_status fem_launch_apply_element(const fem_form* f, int dtype, const void* x, void* ye, cudaStream_t s,
                                     const int* skip) {
   const int p = f->space->p, q = f->q1d;
@@ -170,6 +185,16 @@ fem_status fem_launch_apply_element(const fem_form* f, int dtype, const void* x,
 #define X(P, Q)                                                                                            \
   if (p == P && q == Q)                                                                                    \
     return launch_apply_pq<float, P, Q>(f, f->d_D32, f->d_B32, f->d_G32, (const float*)x, (float*)ye, skip, s);
+    FEM_FOR_EACH_PQ(X)
+#undef X
+  } else if (dtype == FEM_DF64) {
+    FEM_TRY(fem_form_ensure_df64(f, s));
+    const df64* D = reinterpret_cast<const df64*>(f->d_Ddf);
+    const df64* B = reinterpret_cast<const df64*>(f->d_Bdf);
+    const df64* G = reinterpret_cast<const df64*>(f->d_Gdf);
+#define X(P, Q)                                                                                            \
+  if (p == P && q == Q)                                                                                    \
+    return launch_apply_pq<df64, P, Q, double>(f, D, B, G, (const double*)x, (double*)ye, skip, s);
     FEM_FOR_EACH_PQ(X)
 #undef X
   } else {
@@ -227,27 +252,31 @@ extern "C" fem_status fem_apply_element(const fem_form* f, int dtype, const void
 
 extern "C" fem_status fem_scatter(const fem_form* f, int dtype, const void* ye, void* y, void* stream) {
   if (!f || !ye || !y) return fem_fail(FEM_EINVAL, "fem_scatter: NULL argument");
-  if (dtype != FEM_F64 && dtype != FEM_F32) return fem_fail(FEM_EINVAL, "fem_scatter: unknown dtype %d", dtype);
-  return fem_launch_scatter(f, dtype, ye, y, nullptr, nullptr, nullptr, 0, (cudaStream_t)stream);
+  if (dtype != FEM_F64 && dtype != FEM_F32 && dtype != FEM_DF64)
+    return fem_fail(FEM_EINVAL, "fem_scatter: unknown dtype %d", dtype);
+  const int vt = dtype == FEM_F32 ? FEM_F32 : FEM_F64;
+  return fem_launch_scatter(f, vt, ye, y, nullptr, nullptr, nullptr, 0, (cudaStream_t)stream);
 }
 
 extern "C" fem_status fem_apply(const fem_form* fc, int dtype, const void* x, void* y, int constrained,
                                 void* stream) {
   if (!fc || !x || !y) return fem_fail(FEM_EINVAL, "fem_apply: NULL argument");
   if (x == y) return fem_fail(FEM_EINVAL, "fem_apply: y must not alias x");
-  if (dtype != FEM_F64 && dtype != FEM_F32) return fem_fail(FEM_EINVAL, "fem_apply: unknown dtype %d", dtype);
+  if (dtype != FEM_F64 && dtype != FEM_F32 && dtype != FEM_DF64)
+    return fem_fail(FEM_EINVAL, "fem_apply: unknown dtype %d", dtype);
   fem_form* f = const_cast<fem_form*>(fc);
   cudaStream_t s = (cudaStream_t)stream;
+  const int vt = dtype == FEM_F32 ? FEM_F32 : FEM_F64;  // vector type
   if (constrained && !f->d_ess_mask)
     return fem_fail(FEM_EINVAL, "fem_apply: constrained apply needs fem_form_set_essential");
   void* ye = f->d_ye;  // sized for doubles; float E-vectors use the front half
   if (constrained) {
-    FEM_TRY(ensure_work(f, dtype, (size_t)f->space->ndof));
-    void* xz = dtype == FEM_F64 ? (void*)f->d_work64 : (void*)f->d_work32;
-    FEM_TRY(fem_launch_zero_ess(f, dtype, x, xz, s));
+    FEM_TRY(ensure_work(f, vt, (size_t)f->space->ndof));
+    void* xz = vt == FEM_F64 ? (void*)f->d_work64 : (void*)f->d_work32;
+    FEM_TRY(fem_launch_zero_ess(f, vt, x, xz, s));
     FEM_TRY(fem_launch_apply_element(f, dtype, xz, ye, s));
-    return fem_launch_scatter(f, dtype, ye, y, f->d_ess_mask, x, nullptr, 0, s);
+    return fem_launch_scatter(f, vt, ye, y, f->d_ess_mask, x, nullptr, 0, s);
   }
   FEM_TRY(fem_launch_apply_element(f, dtype, x, ye, s));
-  return fem_launch_scatter(f, dtype, ye, y, nullptr, nullptr, nullptr, 0, s);
+  return fem_launch_scatter(f, vt, ye, y, nullptr, nullptr, nullptr, 0, s);
 }

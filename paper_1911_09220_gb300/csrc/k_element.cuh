@@ -22,6 +22,8 @@
 
 #include <stdint.h>
 
+#include "k_df64.cuh"
+
 template <int D1, int Q>
 struct Smem {
   static constexpr int ND = D1 * D1 * D1;
@@ -33,10 +35,11 @@ struct Smem {
 // map: the element's DOF list (e2l + e*(p+1)^3); De: its D block
 // (D + e*6*q^3); out: its E-vector slice. sB/sG: [Q][D1] tables in smem,
 // written before the call. Dereferenced only when valid.
-template <typename T, int D1, int Q>
+// T: compute type (double, float or df64); TX: type of x and out.
+template <typename T, int D1, int Q, typename TX = T>
 __device__ __forceinline__ void diffusion_element(int tx, int ty, bool valid, const int32_t* __restrict__ map,
                                                   const T* __restrict__ De, const T* sB, const T* sG, T* s,
-                                                  const T* __restrict__ x, T* __restrict__ out) {
+                                                  const TX* __restrict__ x, TX* __restrict__ out) {
   constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q;
   T* sX = s;
   T* sBX = s + ND;
@@ -45,7 +48,7 @@ __device__ __forceinline__ void diffusion_element(int tx, int ty, bool valid, co
 #pragma unroll
     for (int z = 0; z < D1; ++z) {
       const int k = (z * D1 + ty) * D1 + tx;
-      sX[k] = __ldg(x + __ldg(map + k));
+      sX[k] = fe_from<T>(__ldg(x + __ldg(map + k)));
     }
   }
   __syncthreads();
@@ -65,8 +68,8 @@ __device__ __forceinline__ void diffusion_element(int tx, int ty, bool valid, co
         u += b[d] * xv;
         v += g[d] * xv;
       }
-      sBX[(z * D1 + ty) * Q + tx] = u;
-      sGX[(z * D1 + ty) * Q + tx] = v;
+      sBX[(z * D1 + ty) * Q + tx] = fe_norm(u);
+      sGX[(z * D1 + ty) * Q + tx] = fe_norm(v);
     }
   }
   __syncthreads();
@@ -89,9 +92,9 @@ __device__ __forceinline__ void diffusion_element(int tx, int ty, bool valid, co
         gb += b[d] * v;
         bg += g[d] * u;
       }
-      rbb[z] = bb;
-      rgb[z] = gb;
-      rbg[z] = bg;
+      rbb[z] = fe_norm(bb);
+      rgb[z] = fe_norm(gb);
+      rbg[z] = fe_norm(bg);
     }
   }
   T t0[D1], t1[D1], t2[D1];
@@ -108,19 +111,22 @@ __device__ __forceinline__ void diffusion_element(int tx, int ty, bool valid, co
       g1 += bz * rbg[z];
       g2 += gz * rbb[z];
     }
+    g0 = fe_norm(g0);
+    g1 = fe_norm(g1);
+    g2 = fe_norm(g2);
     const int o = qz * Q * Q;
     T d00 = 0, d01 = 0, d02 = 0, d11 = 0, d12 = 0, d22 = 0;
     if (valid) {
-      d00 = __ldg(Dp + 0 * NQ + o);
-      d01 = __ldg(Dp + 1 * NQ + o);
-      d02 = __ldg(Dp + 2 * NQ + o);
-      d11 = __ldg(Dp + 3 * NQ + o);
-      d12 = __ldg(Dp + 4 * NQ + o);
-      d22 = __ldg(Dp + 5 * NQ + o);
+      d00 = fe_ldg(Dp + 0 * NQ + o);
+      d01 = fe_ldg(Dp + 1 * NQ + o);
+      d02 = fe_ldg(Dp + 2 * NQ + o);
+      d11 = fe_ldg(Dp + 3 * NQ + o);
+      d12 = fe_ldg(Dp + 4 * NQ + o);
+      d22 = fe_ldg(Dp + 5 * NQ + o);
     }
-    const T v0 = d00 * g0 + d01 * g1 + d02 * g2;
-    const T v1 = d01 * g0 + d11 * g1 + d12 * g2;
-    const T v2 = d02 * g0 + d12 * g1 + d22 * g2;
+    const T v0 = fe_norm(d00 * g0 + d01 * g1 + d02 * g2);
+    const T v1 = fe_norm(d01 * g0 + d11 * g1 + d12 * g2);
+    const T v2 = fe_norm(d02 * g0 + d12 * g1 + d22 * g2);
 #pragma unroll
     for (int d = 0; d < D1; ++d) {
       const T bz = sB[qz * D1 + d], gz = sG[qz * D1 + d];
@@ -138,9 +144,9 @@ __device__ __forceinline__ void diffusion_element(int tx, int ty, bool valid, co
 #pragma unroll
   for (int d = 0; d < D1; ++d) {
     const int k = (d * Q + ty) * Q + tx;
-    sT0[k] = t0[d];
-    sT1[k] = t1[d];
-    sT2[k] = t2[d];
+    sT0[k] = fe_norm(t0[d]);
+    sT1[k] = fe_norm(t1[d]);
+    sT2[k] = fe_norm(t2[d]);
   }
   __syncthreads();
   if (ty < D1) {  // back y: threads (qx, dy)
@@ -159,8 +165,8 @@ __device__ __forceinline__ void diffusion_element(int tx, int ty, bool valid, co
         ua += b[q] * sT0[k];
         ub += g[q] * sT1[k] + b[q] * sT2[k];
       }
-      sUA[(dz * D1 + ty) * Q + tx] = ua;
-      sUB[(dz * D1 + ty) * Q + tx] = ub;
+      sUA[(dz * D1 + ty) * Q + tx] = fe_norm(ua);
+      sUB[(dz * D1 + ty) * Q + tx] = fe_norm(ub);
     }
   }
   __syncthreads();
@@ -179,17 +185,17 @@ __device__ __forceinline__ void diffusion_element(int tx, int ty, bool valid, co
         const int k = (dz * D1 + ty) * Q + q;
         y += g[q] * sUA[k] + b[q] * sUB[k];
       }
-      out[(dz * D1 + ty) * D1 + tx] = y;
+      fe_store(&out[(dz * D1 + ty) * D1 + tx], y);
     }
   }
 }
 
 // Mass: the same passes with B only and one scalar D per point
 // (Sec. 4.4, M_E = B^T D_E B). De: the element's D block (D + e*q^3).
-template <typename T, int D1, int Q>
+template <typename T, int D1, int Q, typename TX = T>
 __device__ __forceinline__ void mass_element(int tx, int ty, bool valid, const int32_t* __restrict__ map,
                                              const T* __restrict__ De, const T* sB, T* s,
-                                             const T* __restrict__ x, T* __restrict__ out) {
+                                             const TX* __restrict__ x, TX* __restrict__ out) {
   constexpr int ND = D1 * D1 * D1;
   T* sX = s;
   T* sBX = s + ND;
@@ -197,7 +203,7 @@ __device__ __forceinline__ void mass_element(int tx, int ty, bool valid, const i
 #pragma unroll
     for (int z = 0; z < D1; ++z) {
       const int k = (z * D1 + ty) * D1 + tx;
-      sX[k] = __ldg(x + __ldg(map + k));
+      sX[k] = fe_from<T>(__ldg(x + __ldg(map + k)));
     }
   }
   __syncthreads();
@@ -210,7 +216,7 @@ __device__ __forceinline__ void mass_element(int tx, int ty, bool valid, const i
       T u = 0;
 #pragma unroll
       for (int d = 0; d < D1; ++d) u += b[d] * sX[(z * D1 + ty) * D1 + d];
-      sBX[(z * D1 + ty) * Q + tx] = u;
+      sBX[(z * D1 + ty) * Q + tx] = fe_norm(u);
     }
   }
   __syncthreads();
@@ -224,7 +230,7 @@ __device__ __forceinline__ void mass_element(int tx, int ty, bool valid, const i
       T bb = 0;
 #pragma unroll
       for (int d = 0; d < D1; ++d) bb += b[d] * sBX[(z * D1 + d) * Q + tx];
-      rbb[z] = bb;
+      rbb[z] = fe_norm(bb);
     }
   }
   T t0[D1];
@@ -236,7 +242,7 @@ __device__ __forceinline__ void mass_element(int tx, int ty, bool valid, const i
     T u = 0;
 #pragma unroll
     for (int z = 0; z < D1; ++z) u += sB[qz * D1 + z] * rbb[z];
-    const T v = valid ? __ldg(Dp + qz * Q * Q) * u : T(0);
+    const T v = valid ? fe_ldg(Dp + qz * Q * Q) * fe_norm(u) : T(0);
 #pragma unroll
     for (int d = 0; d < D1; ++d) t0[d] += sB[qz * D1 + d] * v;
   }
@@ -244,7 +250,7 @@ __device__ __forceinline__ void mass_element(int tx, int ty, bool valid, const i
   T* sT0 = s;
   T* sUA = sT0 + D1 * Q * Q;
 #pragma unroll
-  for (int d = 0; d < D1; ++d) sT0[(d * Q + ty) * Q + tx] = t0[d];
+  for (int d = 0; d < D1; ++d) sT0[(d * Q + ty) * Q + tx] = fe_norm(t0[d]);
   __syncthreads();
   if (ty < D1) {
     T b[Q];
@@ -255,7 +261,7 @@ __device__ __forceinline__ void mass_element(int tx, int ty, bool valid, const i
       T ua = 0;
 #pragma unroll
       for (int q = 0; q < Q; ++q) ua += b[q] * sT0[(dz * Q + q) * Q + tx];
-      sUA[(dz * D1 + ty) * Q + tx] = ua;
+      sUA[(dz * D1 + ty) * Q + tx] = fe_norm(ua);
     }
   }
   __syncthreads();
@@ -268,7 +274,7 @@ __device__ __forceinline__ void mass_element(int tx, int ty, bool valid, const i
       T y = 0;
 #pragma unroll
       for (int q = 0; q < Q; ++q) y += b[q] * sUA[(dz * D1 + ty) * Q + q];
-      out[(dz * D1 + ty) * D1 + tx] = y;
+      fe_store(&out[(dz * D1 + ty) * D1 + tx], y);
     }
   }
 }

@@ -13,6 +13,7 @@
 // partials summed in a fixed order: results are bitwise reproducible.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "fem_internal.h"
 #include "k_common.cuh"
@@ -251,12 +252,14 @@ fem_status get_work(fem_form* f, bool mixed, Work& w) {
 }
 
 // One CG iteration on vectors of type T.
+// dtype: element-kernel type (FEM_F64, FEM_F32 or FEM_DF64); the vectors are T.
 template <typename T>
 fem_status cg_iteration(const fem_form* f, const Work& w, int dtype, T* x, T* r, T* z, T* p, T* q, const T* diag,
                         cudaStream_t s) {
   const int* skip = &w.sc->done;
+  const int vt = std::is_same<T, float>::value ? FEM_F32 : FEM_F64;
   FEM_TRY(fem_launch_apply_element(f, dtype, p, f->d_ye, s, skip));
-  FEM_TRY(fem_launch_scatter(f, dtype, f->d_ye, q, f->d_ess_mask, p, w.part, w.nb, s, skip));
+  FEM_TRY(fem_launch_scatter(f, vt, f->d_ye, q, f->d_ess_mask, p, w.part, w.nb, s, skip));
   k_cg_alpha<<<1, kRedThreads, 0, s>>>(w.sc, w.part, w.nb);
   k_cg_update<T><<<w.nb, 256, 0, s>>>(w.n, w.sc, x, r, z, p, q, diag, w.part);
   k_cg_beta<<<1, kRedThreads, 0, s>>>(w.sc, w.part, w.nb);
@@ -383,7 +386,7 @@ extern "C" fem_status fem_solve(const fem_form* fc, const double* b, double* xio
   fem_solve_opts_default(&o);
   if (opts) o = *opts;
   if (!(o.rtol > 0) || o.maxit <= 0) return fem_fail(FEM_EINVAL, "fem_solve: rtol > 0 and maxit > 0 required");
-  if (o.precision != FEM_SOLVE_F64 && o.precision != FEM_SOLVE_MIXED)
+  if (o.precision != FEM_SOLVE_F64 && o.precision != FEM_SOLVE_MIXED && o.precision != FEM_SOLVE_DF64)
     return fem_fail(FEM_EINVAL, "fem_solve: unknown precision %d", o.precision);
   fem_form* f = const_cast<fem_form*>(fc);
   cudaStream_t s = (cudaStream_t)stream;
@@ -391,6 +394,8 @@ extern "C" fem_status fem_solve(const fem_form* fc, const double* b, double* xio
   Work w;
   FEM_TRY(get_work(f, mixed, w));
   if (mixed) FEM_TRY(fem_form_ensure_f32(f, s));
+  const int op64 = o.precision == FEM_SOLVE_DF64 ? FEM_DF64 : FEM_F64;  // FP64-vector operator
+  if (op64 == FEM_DF64) FEM_TRY(fem_form_ensure_df64(f, s));
   const int64_t n = w.n;
   FEM_CUDA(cudaMemcpyAsync(w.x, xio, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   FEM_TRY(fem_assemble_diagonal(f, w.diag, 1, s));
@@ -443,7 +448,7 @@ extern "C" fem_status fem_solve(const fem_form* fc, const double* b, double* xio
       k_cg_init<double><<<w.nb, 256, 0, s>>>(n, w.r, w.diag, w.z, w.p, nullptr, w.part);
       k_cg_init_scalars<<<1, kRedThreads, 0, s>>>(w.sc, w.part, w.nb, o.rtol, bb, oi.maxit);
       FEM_LAUNCHED();
-      FEM_TRY(cg_loop<double>(f, w, FEM_F64, w.x, w.r, w.z, w.p, w.q, w.diag, oi, s, &st_in, &it_in));
+      FEM_TRY(cg_loop<double>(f, w, op64, w.x, w.r, w.z, w.p, w.q, w.diag, oi, s, &st_in, &it_in));
     } else {
       // inner FP32 solve of A d = r / ||r|| to inner_rtol, then x += ||r|| d
       k_cast_f32<<<w.nb, 256, 0, s>>>(n, w.diag, w.diag32);

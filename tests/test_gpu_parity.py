@@ -65,6 +65,39 @@ def test_apply_parity_fp64(kind, p):
     assert torch.equal(y, y2)
 
 
+@pytest.mark.parametrize("kind", ["diffusion", "mass"])
+@pytest.mark.parametrize("p", range(1, 9))
+def test_apply_parity_df64(kind, p):
+    """Double-float element arithmetic: same 1e-12 bar as native FP64."""
+    import torch
+    N, drop = SIZES[p]
+    c, h = make_mesh(N, seed=110 + p, shuffle=(p % 2 == 1), drop=drop)
+    cs = Case(c, h, p, kind=kind, coef_seed=120 + p)
+    x = x_uniform(130 + p, cs.n)
+    y = torch.empty(cs.n, dtype=torch.float64, device="cuda")
+    cs.form.apply(cuda(x), y, arith="df64")
+    ref = cs.prob.apply(kind, x)
+    assert relerr(y.cpu().numpy(), ref) <= TOL
+    # and against the native FP64 path
+    y64 = torch.empty_like(y)
+    cs.form.apply(cuda(x), y64)
+    assert relerr(y.cpu().numpy(), y64.cpu().numpy()) <= TOL
+
+
+def test_df64_constrained_and_small_magnitudes():
+    import torch
+    c, h = make_mesh(3, seed=140, shuffle=True)
+    cs = Case(c, h, 4)
+    ess = cs.prob.num["boundary_dofs"]
+    cs.form.set_essential(ess)
+    for scale in (1.0, 1e-20, 1e20):
+        x = x_uniform(141, cs.n) * scale
+        y = torch.empty(cs.n, dtype=torch.float64, device="cuda")
+        cs.form.apply(cuda(x), y, constrained=True, arith="df64")
+        ref = osolve.constrain(cs.prob.K, ess) @ x
+        assert relerr(y.cpu().numpy(), ref) <= TOL, scale
+
+
 @pytest.mark.parametrize("q_off", [1, 2])
 @pytest.mark.parametrize("p", [2, 5])
 def test_apply_both_quadrature_sizes(p, q_off):
