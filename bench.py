@@ -549,6 +549,13 @@ def main():
             "apply_frac_of_hbm": bytes32 / (t32 * 1e-3) / 1e9 / peaks().get("hbm_gbs", 6800.0),
             "alg_bytes_per_apply": bytes32}
     del x32, y32, ye32
+    # double-float element arithmetic (FP64 vectors, FP32 pipe)
+    form.apply(x, y, arith="df64")
+    tdfe = time_events(lambda: form.apply_element(x, ye, arith="df64"), args.steps, 2)
+    tdf = time_events(lambda: form.apply(x, y, arith="df64"), args.steps, 2)
+    df64 = {"gdofs": n / (tdf * 1e-3) / 1e9, "ms_per_apply": tdf, "element_kernel_ms": tdfe,
+            "alg_fp64_equiv_tflops": flops / (tdfe * 1e-3) / 1e12,
+            "speedup_vs_fp64_element": statistics.mean(t_elem) / tdfe}
     # FP64 mass apply on the same mesh and coefficient
     mform = F.Form(space, "mass", q, coef=kap)
     tm = time_events(lambda: mform.apply(x, y), args.steps, 2)
@@ -572,7 +579,7 @@ def main():
         bc = torch.empty_like(b)
         form.lift_rhs(b, torch.zeros_like(b), bc)
         sols = {}
-        for prec in ("f64", "mixed"):
+        for prec in ("f64", "mixed", "df64"):
             u = torch.zeros_like(b)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -584,6 +591,8 @@ def main():
             sols[prec] = u
         diff = (sols["mixed"] - sols["f64"]).abs().max().item() / sols["f64"].abs().max().item()
         solve["mixed_vs_f64_maxrel"] = diff
+        solve["df64_vs_f64_maxrel"] = (sols["df64"] - sols["f64"]).abs().max().item() / sols["f64"].abs().max().item()
+        solve["speedup_df64"] = solve["f64"]["seconds"] / solve["df64"]["seconds"]
         solve["speedup_mixed"] = solve["f64"]["seconds"] / solve["mixed"]["seconds"]
         solve["rtol"] = 1e-10
 
@@ -605,7 +614,7 @@ def main():
                        "elements": E, "parallelism": f"replicas x{world} (independent problems)",
                        "l2": "inputs larger than L2 (D alone 3.26 GB); no flush"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
-            "fp32_apply": fp32, "mass_apply_f64": mass,
+            "fp32_apply": fp32, "mass_apply_f64": mass, "df64_apply": df64,
             "clocks": clk, "solve": solve,
             "setup_s": {"space_host": t_space, "form_setup": t_setup},
         }
