@@ -358,6 +358,7 @@ extern "C" fem_status fem_form_create(const fem_space* sp, int kind, int q1d, co
     return fem_fail(FEM_EINVAL, "fem_form_create: unknown kind %d", kind);
   if (!fem_kernels_supported(sp->p, q1d))
     return fem_fail(FEM_EUNSUPPORTED, "fem_form_create: (p=%d, q1d=%d) not compiled", sp->p, q1d);
+  FEM_TRY(fem_apply_tables_init());
   cudaStream_t s = (cudaStream_t)stream;
   fem_form* f = new fem_form();
   f->space = sp;

@@ -128,3 +128,7 @@ fem_status fem_form_ensure_f32(const fem_form* f, cudaStream_t s);
 fem_status fem_form_ensure_df64(const fem_form* f, cudaStream_t s);
 fem_status fem_launch_mark_ess(const fem_form* f, cudaStream_t s);
 int fem_scatter_blocks(int64_t ndof);
+// Constant-memory 1D tables of the element kernels (one copy per translation
+// unit): filled once per device from form / batch creation.
+fem_status fem_apply_tables_init();
+fem_status fem_batch_tables_init();

@@ -20,43 +20,41 @@ constexpr int ne_for_q(int Q) {
 template <typename T, int D1, int Q, int NE, typename TX>
 __global__ void __launch_bounds__(Q * Q * NE)
 k_diffusion_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
-                  const T* __restrict__ Dq, const T* __restrict__ Bg, const T* __restrict__ Gg,
-                  const TX* __restrict__ x, TX* __restrict__ ye) {
-  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = Smem<D1, Q>::SE;
+                  const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye) {
+  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<D1, Q>::SE;
   if (skip && *skip) return;  // a captured solver iteration after convergence
-  __shared__ T sB[Q * D1], sG[Q * D1];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-  const int tid = tx + Q * (ty + Q * tz);
-  for (int i = tid; i < Q * D1; i += Q * Q * NE) {
-    sB[i] = fe_ldg(Bg + i);
-    sG[i] = fe_ldg(Gg + i);
+  const int t = threadIdx.x + Q * threadIdx.y, tz = threadIdx.z;
+  const int e0 = blockIdx.x * NE;
+  if (t == 0 && tz == 0) {  // D of the block's elements: read in stage S3, fetch into L2 now
+    const int nel = min(NE, ne - e0);
+    l2_prefetch_range(Dq + (size_t)e0 * 6 * NQ, sizeof(T) * (size_t)nel * 6 * NQ);
   }
-  const int e = blockIdx.x * NE + tz;
+  const int e = e0 + tz;
   const bool valid = e < ne;
   const size_t ev = valid ? (size_t)e : 0;
-  diffusion_element<T, D1, Q, TX>(tx, ty, valid, e2l + ev * ND, Dq + ev * 6 * NQ, sB, sG, sm + tz * SE, x,
-                              ye + ev * ND);
+  diffusion_element<T, D1, Q, TX>(t, valid, e2l + ev * ND, Dq + ev * 6 * NQ, sm + tz * SE, x, ye + ev * ND);
 }
 
 template <typename T, int D1, int Q, int NE, typename TX>
 __global__ void __launch_bounds__(Q * Q * NE)
 k_mass_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
-             const T* __restrict__ Dq, const T* __restrict__ Bg, const TX* __restrict__ x,
-             TX* __restrict__ ye) {
-  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = Smem<D1, Q>::SE;
+             const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye) {
+  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<D1, Q>::SE;
   if (skip && *skip) return;
-  __shared__ T sB[Q * D1];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-  const int tid = tx + Q * (ty + Q * tz);
-  for (int i = tid; i < Q * D1; i += Q * Q * NE) sB[i] = fe_ldg(Bg + i);
-  const int e = blockIdx.x * NE + tz;
+  const int t = threadIdx.x + Q * threadIdx.y, tz = threadIdx.z;
+  const int e0 = blockIdx.x * NE;
+  if (t == 0 && tz == 0) {
+    const int nel = min(NE, ne - e0);
+    l2_prefetch_range(Dq + (size_t)e0 * NQ, sizeof(T) * (size_t)nel * NQ);
+  }
+  const int e = e0 + tz;
   const bool valid = e < ne;
   const size_t ev = valid ? (size_t)e : 0;
-  mass_element<T, D1, Q, TX>(tx, ty, valid, e2l + ev * ND, Dq + ev * NQ, sB, sm + tz * SE, x, ye + ev * ND);
+  mass_element<T, D1, Q, TX>(t, valid, e2l + ev * ND, Dq + ev * NQ, sm + tz * SE, x, ye + ev * ND);
 }
 
 template <typename K>
@@ -72,15 +70,17 @@ fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G
   const int ne = (int)f->space->ne;
   const dim3 block(Q, Q, NE);
   const int grid = (ne + NE - 1) / NE;
-  const size_t bytes = sizeof(T) * NE * Smem<D1, Q>::SE;
+  const size_t bytes = sizeof(T) * NE * ElemSmem<D1, Q>::SE;
+  (void)B;
+  (void)G;
   if (f->kind == FEM_DIFFUSION) {
     auto kern = k_diffusion_apply<T, D1, Q, NE, TX>;
     FEM_TRY(prepare_smem(kern, bytes));
-    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, B, G, x, ye);
+    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, x, ye);
   } else {
     auto kern = k_mass_apply<T, D1, Q, NE, TX>;
     FEM_TRY(prepare_smem(kern, bytes));
-    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, B, x, ye);
+    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, x, ye);
   }
   FEM_LAUNCHED();
   return FEM_OK;
@@ -150,6 +150,8 @@ int fem_kernels_supported(int p, int q1d) {
 }
 
 int fem_scatter_blocks(int64_t ndof) { return grid_for(ndof, 256); }
+
+fem_status fem_apply_tables_init() { return fem_tables_ensure(); }
 
 fem_status fem_form_ensure_f32(const fem_form* fc, cudaStream_t s) {
   fem_form* f = const_cast<fem_form*>(fc);

@@ -63,18 +63,6 @@ __device__ __forceinline__ const double* D_of<double>(const BProb& P) { return P
 template <>
 __device__ __forceinline__ const float* D_of<float>(const BProb& P) { return P.D32; }
 template <typename T>
-__device__ __forceinline__ const T* B_of(const BProb& P);
-template <>
-__device__ __forceinline__ const double* B_of<double>(const BProb& P) { return P.B64; }
-template <>
-__device__ __forceinline__ const float* B_of<float>(const BProb& P) { return P.B32; }
-template <typename T>
-__device__ __forceinline__ const T* G_of(const BProb& P);
-template <>
-__device__ __forceinline__ const double* G_of<double>(const BProb& P) { return P.G64; }
-template <>
-__device__ __forceinline__ const float* G_of<float>(const BProb& P) { return P.G32; }
-template <typename T>
 __device__ __forceinline__ const T* diag_of(const BProb& P);
 template <>
 __device__ __forceinline__ const double* diag_of<double>(const BProb& P) { return P.diag64; }
@@ -87,10 +75,10 @@ __host__ __device__ constexpr int planes_for(int Q) { return (kBT + Q * Q - 1) /
 
 template <typename T, int D1, int Q>
 __device__ __noinline__ void run_tile(const BProb& P, int e0, int tile, int nrhs, const int* __restrict__ done,
-                         const T* __restrict__ X, T* __restrict__ YE, const T* sB, const T* sG, T* sm) {
-  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = Smem<D1, Q>::SE;
+                                      const T* __restrict__ X, T* __restrict__ YE, T* sm) {
+  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<D1, Q>::SE;
   const int tid = threadIdx.x;
-  const int tx = tid % Q, ty = (tid / Q) % Q, tz = tid / (Q * Q);
+  const int t = tid % (Q * Q), tz = tid / (Q * Q);
   const int e = e0 + tz;
   const bool valid = tz < tile && e < P.ne;
   const size_t ev = valid ? (size_t)e : 0;
@@ -101,9 +89,9 @@ __device__ __noinline__ void run_tile(const BProb& P, int e0, int tile, int nrhs
     const T* x = X + P.xoff + (int64_t)r * P.ndof;
     T* ye = YE + P.yeoff + ((int64_t)r * P.ne + ev) * ND;
     if (P.kind == FEM_DIFFUSION)
-      diffusion_element<T, D1, Q>(tx, ty, valid, P.e2l + ev * ND, D + ev * 6 * NQ, sB, sG, slab, x, ye);
+      diffusion_element<T, D1, Q>(t, valid, P.e2l + ev * ND, D + ev * 6 * NQ, slab, x, ye);
     else
-      mass_element<T, D1, Q>(tx, ty, valid, P.e2l + ev * ND, D + ev * NQ, sB, slab, x, ye);
+      mass_element<T, D1, Q>(t, valid, P.e2l + ev * ND, D + ev * NQ, slab, x, ye);
   }
 }
 
@@ -112,23 +100,16 @@ __global__ void __launch_bounds__(kBT)
 k_batch_element(const BProb* __restrict__ probs, const BItem* __restrict__ items, int nitems,
                 const int* __restrict__ tiles, int nrhs, const int* __restrict__ done, const T* __restrict__ X,
                 T* __restrict__ YE) {
-  __shared__ T sB[10 * 9], sG[10 * 9];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const BItem item = items[it];
     const BProb& P = probs[item.prob];
     const int p = P.p, q = P.q;
-    __syncthreads();  // the previous item is done with sB, sG and the slabs
-    const T* Bg = B_of<T>(P);
-    const T* Gg = G_of<T>(P);
-    for (int i = threadIdx.x; i < q * (p + 1); i += blockDim.x) {
-      sB[i] = Bg[i];
-      sG[i] = Gg[i];
-    }
+    __syncthreads();  // the previous item is done with the slabs
     const int tile = tiles[p * 2 + (q - p - 1)];
 #define CASE(PP, QQ) \
-  if (p == PP && q == QQ) run_tile<T, PP + 1, QQ>(P, item.e0, tile, nrhs, done, X, YE, sB, sG, sm);
+  if (p == PP && q == QQ) run_tile<T, PP + 1, QQ>(P, item.e0, tile, nrhs, done, X, YE, sm);
     FEM_FOR_EACH_PQ_BATCH(CASE)
 #undef CASE
   }
@@ -443,7 +424,8 @@ __global__ void k_cast_vec(int64_t n, const double* __restrict__ a, float* __res
 template <typename T>
 size_t slab_bytes(int p, int q) {
   const int D1 = p + 1, Q = q;
-  const int SA = D1 * D1 * D1 + 2 * D1 * D1 * Q, SB = 3 * D1 * Q * Q + 2 * D1 * D1 * Q;
+  const int XP = D1 | 1, YP = D1 | 1, QP = Q | 1;
+  const int SA = D1 * D1 * XP + 2 * D1 * Q * YP + 3 * D1 * Q * Q, SB = 3 * D1 * Q * Q + 2 * D1 * D1 * QP;
   return sizeof(T) * (size_t)planes_for(Q) * (size_t)(SA > SB ? SA : SB);
 }
 
@@ -637,10 +619,13 @@ fem_status bcg_loop(fem_batch* b, T* X, T* R, T* Z, T* Pv, T* Qv, T* XZ, const f
 
 }  // namespace
 
+fem_status fem_batch_tables_init() { return fem_tables_ensure(); }
+
 extern "C" fem_status fem_batch_create(const fem_form* const* forms, int nprob, int nrhs, void* stream,
                                        fem_batch** out) {
   if (!out || !forms || nprob <= 0 || nrhs <= 0) return fem_fail(FEM_EINVAL, "fem_batch_create: bad arguments");
   *out = nullptr;
+  FEM_TRY(fem_batch_tables_init());
   fem_batch* b = new fem_batch();
   b->nprob = nprob;
   b->nrhs = nrhs;
