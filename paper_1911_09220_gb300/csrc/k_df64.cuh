@@ -45,6 +45,9 @@ __device__ __forceinline__ df64 operator+(const df64 a, const df64 b) {
   return df64(s, err + (a.lo + b.lo));
 }
 
+__device__ __forceinline__ df64 operator-(const df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(const df64 a, const df64 b) { return a + (-b); }
+
 __device__ __forceinline__ df64& operator+=(df64& a, const df64 b) {
   a = a + b;
   return a;

@@ -9,8 +9,10 @@
 // contraction stage gives each active thread one *line* of its input tensor:
 // the thread reads the line (K values) from shared memory into registers and
 // produces every output of that line (M values), so each loaded value feeds
-// M (or 2M, 3M) FMAs. The 1D coefficients come from constant memory at
-// compile-time indices (k_tables.cuh): they are FMA operands, not loads.
+// many FMAs. Each line goes through the even-odd (folded) form of its 1D
+// operator (eo_apply below), and the folded coefficients come from constant
+// memory at compile-time indices (k_tables.cuh): they are FMA operands, not
+// loads.
 //   gather  X[z][y][x]           = x_L[map[z][y][x]]                   (G)
 //   S1  (z, y) lines:  BX, GX[z][qx][y] = sum_x B/G[qx][x] X[z][y][x]   (x)
 //   S2  (z, qx) lines: BB, GB, BG[z][qy][qx] = sum_y B/G[qy][y] (BX|GX) (y)
@@ -32,6 +34,53 @@
 #include "k_df64.cuh"
 #include "k_tables.cuh"
 
+// ------------------------------------------------------------- even-odd ----
+// One line through a folded 1D operator (k_tables.cuh): y[M] = A x[K], where
+// e/o are the line's even and odd parts. P_k uses e, N_k uses o, and
+// y_k = P_k + N_k, y_{M-1-k} = S (P_k - N_k): about half the multiply-adds
+// of the plain M x K product.
+template <typename T, int K>
+__device__ __forceinline__ void eo_split(const T* x, T* e, T* o) {
+#pragma unroll
+  for (int j = 0; j < K / 2; ++j) {
+    e[j] = fe_norm(x[j] + x[K - 1 - j]);
+    o[j] = fe_norm(x[j] - x[K - 1 - j]);
+  }
+  if (K & 1) e[K / 2] = x[K / 2];
+}
+
+template <typename T, int M, int K, int S, int OFF>
+__device__ __forceinline__ void eo_apply(const T* e, const T* o, T* y) {
+  constexpr int hK = K / 2, cK = (K + 1) / 2, hM = M / 2, cM = (M + 1) / 2;
+#pragma unroll
+  for (int k = 0; k < cM; ++k) {
+    const bool mid = (M & 1) && (k == hM);
+    T P = 0, N = 0;
+    if (!mid || S > 0) {
+#pragma unroll
+      for (int j = 0; j < cK; ++j) P += EO<T>::c(OFF + k * cK + j) * e[j];
+    }
+    if (!mid || S < 0) {
+#pragma unroll
+      for (int j = 0; j < hK; ++j) N += EO<T>::c(OFF + cM * cK + k * hK + j) * o[j];
+    }
+    if (mid) {
+      y[k] = fe_norm(S > 0 ? P : N);
+    } else {
+      y[k] = fe_norm(P + N);
+      y[M - 1 - k] = fe_norm(S > 0 ? P - N : N - P);
+    }
+  }
+}
+
+// y = A x for one line (split and apply).
+template <typename T, int M, int K, int S, int OFF>
+__device__ __forceinline__ void eo_line(const T* x, T* y) {
+  T e[(K + 1) / 2], o[K / 2 > 0 ? K / 2 : 1];
+  eo_split<T, K>(x, e, o);
+  eo_apply<T, M, K, S, OFF>(e, o, y);
+}
+
 template <int D1, int Q>
 struct ElemSmem {
   static constexpr int XP = D1 | 1;  // padded x rows of X
@@ -51,7 +100,8 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
                                                   TX* __restrict__ out) {
   using L = ElemSmem<D1, Q>;
   constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, QQ = Q * Q, XP = L::XP, YP = L::YP, QP = L::QP;
-  constexpr int OFF = tab_off(D1, Q);
+  constexpr int BF = eo_off(D1, Q, 0), GF = eo_off(D1, Q, 1), BT = eo_off(D1, Q, 2), GT = eo_off(D1, Q, 3);
+  constexpr int cD = (D1 + 1) / 2, hD = D1 / 2 > 0 ? D1 / 2 : 1;
   T* sX = s;                                // [z][y][XP]
   T* sBX = sX + D1 * D1 * XP;               // [z][qx][YP]
   T* sGX = sBX + D1 * Q * YP;
@@ -67,93 +117,73 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
   __syncthreads();
   if (t < D1 * D1) {  // S1: line (z, y) along x
     const int z = t / D1, y = t % D1;
-    T xr[D1];
+    T xr[D1], e[cD], o[hD], bx[Q], gx[Q];
 #pragma unroll
     for (int d = 0; d < D1; ++d) xr[d] = sX[t * XP + d];
+    eo_split<T, D1>(xr, e, o);
+    eo_apply<T, Q, D1, 1, BF>(e, o, bx);
+    eo_apply<T, Q, D1, -1, GF>(e, o, gx);
 #pragma unroll
     for (int qx = 0; qx < Q; ++qx) {
-      T u = 0, v = 0;
-#pragma unroll
-      for (int d = 0; d < D1; ++d) {
-        u += Tab<T>::B(OFF + qx * D1 + d) * xr[d];
-        v += Tab<T>::G(OFF + qx * D1 + d) * xr[d];
-      }
-      sBX[(z * Q + qx) * YP + y] = fe_norm(u);
-      sGX[(z * Q + qx) * YP + y] = fe_norm(v);
+      sBX[(z * Q + qx) * YP + y] = bx[qx];
+      sGX[(z * Q + qx) * YP + y] = gx[qx];
     }
   }
   __syncthreads();
   if (t < D1 * Q) {  // S2: line (z, qx) along y
     const int z = t / Q, qx = t % Q;
-    T br[D1], gr[D1];
+    T br[D1], gr[D1], e[cD], o[hD], bb[Q], bg[Q], gb[Q];
 #pragma unroll
     for (int d = 0; d < D1; ++d) {
       br[d] = sBX[t * YP + d];
       gr[d] = sGX[t * YP + d];
     }
+    eo_split<T, D1>(br, e, o);
+    eo_apply<T, Q, D1, 1, BF>(e, o, bb);
+    eo_apply<T, Q, D1, -1, GF>(e, o, bg);
+    eo_line<T, Q, D1, 1, BF>(gr, gb);
 #pragma unroll
     for (int qy = 0; qy < Q; ++qy) {
-      T bb = 0, gb = 0, bg = 0;
-#pragma unroll
-      for (int d = 0; d < D1; ++d) {
-        const T b = Tab<T>::B(OFF + qy * D1 + d);
-        bb += b * br[d];
-        gb += b * gr[d];
-        bg += Tab<T>::G(OFF + qy * D1 + d) * br[d];
-      }
-      const int o = (z * Q + qy) * Q + qx;
-      sBB[o] = fe_norm(bb);
-      sGB[o] = fe_norm(gb);
-      sBG[o] = fe_norm(bg);
+      const int o2 = (z * Q + qy) * Q + qx;
+      sBB[o2] = bb[qy];
+      sGB[o2] = gb[qy];
+      sBG[o2] = bg[qy];
     }
   }
   __syncthreads();
   T t0[D1], t1[D1], t2[D1];
-#pragma unroll
-  for (int d = 0; d < D1; ++d) t0[d] = t1[d] = t2[d] = 0;
   if (t < QQ) {  // S3: line (qy, qx) along z, D at every point, back along z
-    T rbb[D1], rgb[D1], rbg[D1];
+    T rbb[D1], rgb[D1], rbg[D1], g0[Q], g1[Q], g2[Q];
 #pragma unroll
     for (int z = 0; z < D1; ++z) {
       rbb[z] = sBB[z * QQ + t];
       rgb[z] = sGB[z * QQ + t];
       rbg[z] = sBG[z * QQ + t];
     }
+    eo_line<T, Q, D1, 1, BF>(rgb, g0);
+    eo_line<T, Q, D1, 1, BF>(rbg, g1);
+    eo_line<T, Q, D1, -1, GF>(rbb, g2);
     const T* Dp = De + t;
 #pragma unroll
     for (int qz = 0; qz < Q; ++qz) {
-      T g0 = 0, g1 = 0, g2 = 0;
-#pragma unroll
-      for (int z = 0; z < D1; ++z) {
-        const T b = Tab<T>::B(OFF + qz * D1 + z);
-        g0 += b * rgb[z];
-        g1 += b * rbg[z];
-        g2 += Tab<T>::G(OFF + qz * D1 + z) * rbb[z];
-      }
-      g0 = fe_norm(g0);
-      g1 = fe_norm(g1);
-      g2 = fe_norm(g2);
-      const int o = qz * QQ;
+      const int o2 = qz * QQ;
       T d00 = 0, d01 = 0, d02 = 0, d11 = 0, d12 = 0, d22 = 0;
       if (valid) {
-        d00 = fe_ldg(Dp + 0 * NQ + o);
-        d01 = fe_ldg(Dp + 1 * NQ + o);
-        d02 = fe_ldg(Dp + 2 * NQ + o);
-        d11 = fe_ldg(Dp + 3 * NQ + o);
-        d12 = fe_ldg(Dp + 4 * NQ + o);
-        d22 = fe_ldg(Dp + 5 * NQ + o);
+        d00 = fe_ldg(Dp + 0 * NQ + o2);
+        d01 = fe_ldg(Dp + 1 * NQ + o2);
+        d02 = fe_ldg(Dp + 2 * NQ + o2);
+        d11 = fe_ldg(Dp + 3 * NQ + o2);
+        d12 = fe_ldg(Dp + 4 * NQ + o2);
+        d22 = fe_ldg(Dp + 5 * NQ + o2);
       }
-      const T v0 = fe_norm(d00 * g0 + d01 * g1 + d02 * g2);
-      const T v1 = fe_norm(d01 * g0 + d11 * g1 + d12 * g2);
-      const T v2 = fe_norm(d02 * g0 + d12 * g1 + d22 * g2);
-#pragma unroll
-      for (int d = 0; d < D1; ++d) {
-        const T b = Tab<T>::B(OFF + qz * D1 + d);
-        t0[d] += b * v0;
-        t1[d] += b * v1;
-        t2[d] += Tab<T>::G(OFF + qz * D1 + d) * v2;
-      }
+      const T a0 = g0[qz], a1 = g1[qz], a2 = g2[qz];
+      g0[qz] = fe_norm(d00 * a0 + d01 * a1 + d02 * a2);
+      g1[qz] = fe_norm(d01 * a0 + d11 * a1 + d12 * a2);
+      g2[qz] = fe_norm(d02 * a0 + d12 * a1 + d22 * a2);
     }
+    eo_line<T, D1, Q, 1, BT>(g0, t0);
+    eo_line<T, D1, Q, 1, BT>(g1, t1);
+    eo_line<T, D1, Q, -1, GT>(g2, t2);
   }
   __syncthreads();  // phase-A arrays are dead from here on
   T* sT0 = s;                               // [dz][qy][qx]
@@ -164,54 +194,43 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
   if (t < QQ) {
 #pragma unroll
     for (int d = 0; d < D1; ++d) {
-      sT0[d * QQ + t] = fe_norm(t0[d]);
-      sT1[d * QQ + t] = fe_norm(t1[d]);
-      sT2[d * QQ + t] = fe_norm(t2[d]);
+      sT0[d * QQ + t] = t0[d];
+      sT1[d * QQ + t] = t1[d];
+      sT2[d * QQ + t] = t2[d];
     }
   }
   __syncthreads();
   if (t < D1 * Q) {  // S4: line (dz, qx) along qy
     const int dz = t / Q, qx = t % Q;
-    T a0[Q], a1[Q], a2[Q];
+    T a0[Q], a1[Q], a2[Q], ua[D1], u1[D1], u2[D1];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const int o = (dz * Q + q) * Q + qx;
-      a0[q] = sT0[o];
-      a1[q] = sT1[o];
-      a2[q] = sT2[o];
+      const int o2 = (dz * Q + q) * Q + qx;
+      a0[q] = sT0[o2];
+      a1[q] = sT1[o2];
+      a2[q] = sT2[o2];
     }
+    eo_line<T, D1, Q, 1, BT>(a0, ua);
+    eo_line<T, D1, Q, -1, GT>(a1, u1);
+    eo_line<T, D1, Q, 1, BT>(a2, u2);
 #pragma unroll
     for (int dy = 0; dy < D1; ++dy) {
-      T ua = 0, ub = 0;
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const T b = Tab<T>::B(OFF + q * D1 + dy);
-        ua += b * a0[q];
-        ub += Tab<T>::G(OFF + q * D1 + dy) * a1[q];
-        ub += b * a2[q];
-      }
-      sUA[(dz * D1 + dy) * QP + qx] = fe_norm(ua);
-      sUB[(dz * D1 + dy) * QP + qx] = fe_norm(ub);
+      sUA[(dz * D1 + dy) * QP + qx] = ua[dy];
+      sUB[(dz * D1 + dy) * QP + qx] = fe_norm(u1[dy] + u2[dy]);
     }
   }
   __syncthreads();
   if (valid && t < D1 * D1) {  // S5: line (dz, dy) along qx
-    T ua[Q], ub[Q];
+    T ua[Q], ub[Q], y1[D1], y2[D1];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       ua[q] = sUA[t * QP + q];
       ub[q] = sUB[t * QP + q];
     }
+    eo_line<T, D1, Q, -1, GT>(ua, y1);
+    eo_line<T, D1, Q, 1, BT>(ub, y2);
 #pragma unroll
-    for (int dx = 0; dx < D1; ++dx) {
-      T y = 0;
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        y += Tab<T>::G(OFF + q * D1 + dx) * ua[q];
-        y += Tab<T>::B(OFF + q * D1 + dx) * ub[q];
-      }
-      fe_store(&out[t * D1 + dx], y);
-    }
+    for (int dx = 0; dx < D1; ++dx) fe_store(&out[t * D1 + dx], y1[dx] + y2[dx]);
   }
 }
 
@@ -223,7 +242,7 @@ __device__ __forceinline__ void mass_element(int t, bool valid, const int32_t* _
                                              TX* __restrict__ out) {
   using L = ElemSmem<D1, Q>;
   constexpr int ND = D1 * D1 * D1, QQ = Q * Q, XP = L::XP, YP = L::YP, QP = L::QP;
-  constexpr int OFF = tab_off(D1, Q);
+  constexpr int BF = eo_off(D1, Q, 0), BT = eo_off(D1, Q, 2);
   T* sX = s;
   T* sBX = sX + D1 * D1 * XP;
   T* sBB = sBX + D1 * Q * YP;
@@ -236,83 +255,59 @@ __device__ __forceinline__ void mass_element(int t, bool valid, const int32_t* _
   __syncthreads();
   if (t < D1 * D1) {
     const int z = t / D1, y = t % D1;
-    T xr[D1];
+    T xr[D1], bx[Q];
 #pragma unroll
     for (int d = 0; d < D1; ++d) xr[d] = sX[t * XP + d];
+    eo_line<T, Q, D1, 1, BF>(xr, bx);
 #pragma unroll
-    for (int qx = 0; qx < Q; ++qx) {
-      T u = 0;
-#pragma unroll
-      for (int d = 0; d < D1; ++d) u += Tab<T>::B(OFF + qx * D1 + d) * xr[d];
-      sBX[(z * Q + qx) * YP + y] = fe_norm(u);
-    }
+    for (int qx = 0; qx < Q; ++qx) sBX[(z * Q + qx) * YP + y] = bx[qx];
   }
   __syncthreads();
   if (t < D1 * Q) {
     const int z = t / Q, qx = t % Q;
-    T br[D1];
+    T br[D1], bb[Q];
 #pragma unroll
     for (int d = 0; d < D1; ++d) br[d] = sBX[t * YP + d];
+    eo_line<T, Q, D1, 1, BF>(br, bb);
 #pragma unroll
-    for (int qy = 0; qy < Q; ++qy) {
-      T bb = 0;
-#pragma unroll
-      for (int d = 0; d < D1; ++d) bb += Tab<T>::B(OFF + qy * D1 + d) * br[d];
-      sBB[(z * Q + qy) * Q + qx] = fe_norm(bb);
-    }
+    for (int qy = 0; qy < Q; ++qy) sBB[(z * Q + qy) * Q + qx] = bb[qy];
   }
   __syncthreads();
   T t0[D1];
-#pragma unroll
-  for (int d = 0; d < D1; ++d) t0[d] = 0;
   if (t < QQ) {
-    T rbb[D1];
+    T rbb[D1], u[Q];
 #pragma unroll
     for (int z = 0; z < D1; ++z) rbb[z] = sBB[z * QQ + t];
+    eo_line<T, Q, D1, 1, BF>(rbb, u);
 #pragma unroll
-    for (int qz = 0; qz < Q; ++qz) {
-      T u = 0;
-#pragma unroll
-      for (int z = 0; z < D1; ++z) u += Tab<T>::B(OFF + qz * D1 + z) * rbb[z];
-      const T v = valid ? fe_ldg(De + t + qz * QQ) * fe_norm(u) : T(0);
-      const T vn = fe_norm(v);
-#pragma unroll
-      for (int d = 0; d < D1; ++d) t0[d] += Tab<T>::B(OFF + qz * D1 + d) * vn;
-    }
+    for (int qz = 0; qz < Q; ++qz) u[qz] = valid ? fe_norm(fe_ldg(De + t + qz * QQ) * u[qz]) : T(0);
+    eo_line<T, D1, Q, 1, BT>(u, t0);
   }
   __syncthreads();
   T* sT0 = s;
   T* sUA = sT0 + D1 * QQ;
   if (t < QQ) {
 #pragma unroll
-    for (int d = 0; d < D1; ++d) sT0[d * QQ + t] = fe_norm(t0[d]);
+    for (int d = 0; d < D1; ++d) sT0[d * QQ + t] = t0[d];
   }
   __syncthreads();
   if (t < D1 * Q) {
     const int dz = t / Q, qx = t % Q;
-    T a0[Q];
+    T a0[Q], ua[D1];
 #pragma unroll
     for (int q = 0; q < Q; ++q) a0[q] = sT0[(dz * Q + q) * Q + qx];
+    eo_line<T, D1, Q, 1, BT>(a0, ua);
 #pragma unroll
-    for (int dy = 0; dy < D1; ++dy) {
-      T ua = 0;
-#pragma unroll
-      for (int q = 0; q < Q; ++q) ua += Tab<T>::B(OFF + q * D1 + dy) * a0[q];
-      sUA[(dz * D1 + dy) * QP + qx] = fe_norm(ua);
-    }
+    for (int dy = 0; dy < D1; ++dy) sUA[(dz * D1 + dy) * QP + qx] = ua[dy];
   }
   __syncthreads();
   if (valid && t < D1 * D1) {
-    T ua[Q];
+    T ua[Q], y[D1];
 #pragma unroll
     for (int q = 0; q < Q; ++q) ua[q] = sUA[t * QP + q];
+    eo_line<T, D1, Q, 1, BT>(ua, y);
 #pragma unroll
-    for (int dx = 0; dx < D1; ++dx) {
-      T y = 0;
-#pragma unroll
-      for (int q = 0; q < Q; ++q) y += Tab<T>::B(OFF + q * D1 + dx) * ua[q];
-      fe_store(&out[t * D1 + dx], y);
-    }
+    for (int dx = 0; dx < D1; ++dx) fe_store(&out[t * D1 + dx], y[dx]);
   }
 }
 
