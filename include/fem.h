@@ -126,8 +126,9 @@ fem_status fem_space_dof_coords(const fem_space* space, double* out, void* strea
  *   Sec. 5.3, which stores alpha W adj(J) adj(J)^T / det J in 2D);
  * kind = FEM_MASS stores D_q = coef_e w_q det J_q (Sec. 4.4, (D_E)_kk).
  * coef: device float64 [ne] per-element coefficient, or NULL for 1.
- * Layout in HBM: [ne][6][q1d^3] (diffusion) or [ne][q1d^3] (mass), float64,
- * point index lexicographic (x fastest). Synchronises `stream` to read the
+ * Layout in HBM: [ne][q1d^3][6] (diffusion, the six components of a point
+ * contiguous) or [ne][q1d^3] (mass), float64, point index lexicographic
+ * (x fastest). Synchronises `stream` to read the
  * det J check. Errors: FEM_EINVERTED if any det J <= 0, FEM_EUNSUPPORTED if
  * (p, q1d) is not compiled. */
 fem_status fem_form_create(const fem_space* space, int kind, int q1d,

@@ -395,7 +395,7 @@ extern "C" fem_status fem_form_create(const fem_space* sp, int kind, int q1d, co
   up(&f->d_qpts, pts);
   up(&f->d_qwts, wts);
   if (st == FEM_OK) st = dev_alloc(&f->d_coef, (size_t)sp->ne);
-  if (st == FEM_OK) st = dev_alloc(&f->d_D, (size_t)sp->ne * f->ncomp * f->nq);
+  if (st == FEM_OK) st = dev_alloc(&f->d_D, (size_t)sp->ne * f->ncomp * f->nq + 2);  // +16 bytes slack
   if (st == FEM_OK) st = dev_alloc((double**)&f->d_ye, (size_t)sp->ne * sp->nd);
   if (st == FEM_OK) st = dev_alloc(&f->d_flag, 4);
   if (st == FEM_OK && cudaMallocHost((void**)&f->h_pinned, 64) != cudaSuccess)

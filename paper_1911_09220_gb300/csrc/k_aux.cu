@@ -52,9 +52,10 @@ k_diag(int ne, int kind, const double* __restrict__ Dq, const double* __restrict
 #pragma unroll
     for (int d = 0; d < D1; ++d) a[d] = 0.0;
     if (valid) {
-      const double* De = Dq + ((size_t)e * ncomp + c) * NQ + ty * Q + tx;
+      // point-major D: component c of point q at (e * NQ + q) * ncomp + c
+      const double* De = Dq + ((size_t)e * NQ + ty * Q + tx) * ncomp + c;
       for (int qz = 0; qz < Q; ++qz) {
-        const double v = fac * De[qz * Q * Q];
+        const double v = fac * De[(size_t)qz * Q * Q * ncomp];
 #pragma unroll
         for (int d = 0; d < D1; ++d) a[d] += sq(sB, sG, kz, qz * D1 + d) * v;
       }
@@ -216,7 +217,7 @@ k_grad(int ne, const int32_t* __restrict__ e2l, const double* __restrict__ Dq,
   }
   double acc = 0.0;
   if (valid) {
-    const double* De = Dq + (size_t)e * 6 * NQ + ty * Q + tx;
+    const double* De = Dq + ((size_t)e * NQ + ty * Q + tx) * 6;
     for (int qz = 0; qz < Q; ++qz) {
       double g0 = 0, g1 = 0, g2 = 0;
       for (int z = 0; z < D1; ++z) {
@@ -224,9 +225,8 @@ k_grad(int ne, const int32_t* __restrict__ e2l, const double* __restrict__ Dq,
         g1 += sB[qz * D1 + z] * rbg[z];
         g2 += sG[qz * D1 + z] * rbb[z];
       }
-      const int o = qz * Q * Q;
-      const double d00 = De[o], d01 = De[NQ + o], d02 = De[2 * NQ + o], d11 = De[3 * NQ + o],
-                   d12 = De[4 * NQ + o], d22 = De[5 * NQ + o];
+      const double* d = De + (size_t)qz * Q * Q * 6;
+      const double d00 = d[0], d01 = d[1], d02 = d[2], d11 = d[3], d12 = d[4], d22 = d[5];
       acc += g0 * (d00 * g0 + d01 * g1 + d02 * g2) + g1 * (d01 * g0 + d11 * g1 + d12 * g2) +
              g2 * (d02 * g0 + d12 * g1 + d22 * g2);
     }

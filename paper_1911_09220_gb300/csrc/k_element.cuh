@@ -81,6 +81,111 @@ __device__ __forceinline__ void eo_line(const T* x, T* y) {
   eo_apply<T, M, K, S, OFF>(e, o, y);
 }
 
+// D read from shared memory (a staged tile) or from global memory.
+template <bool DS>
+__device__ __forceinline__ double d_load(const double* p) {
+  if constexpr (DS) return *p;
+  else return fe_ldg(p);
+}
+template <bool DS>
+__device__ __forceinline__ float d_load(const float* p) {
+  if constexpr (DS) return *p;
+  else return fe_ldg(p);
+}
+template <bool DS>
+__device__ __forceinline__ df64 d_load(const df64* p) {
+  if constexpr (DS) return *p;
+  else return fe_ldg(p);
+}
+
+// The six D components of one point (point-major layout, 16-byte aligned
+// for double and df64 records of 48 bytes, 8-byte aligned for float records
+// of 24 bytes): three vector loads instead of six scalar ones.
+template <bool DS>
+__device__ __forceinline__ void d_load6(const double* p, double* d) {
+  if constexpr (DS) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) d[c] = p[c];
+  } else {
+    const double2* v = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double2 w = __ldg(v + k);
+      d[2 * k] = w.x;
+      d[2 * k + 1] = w.y;
+    }
+  }
+}
+template <bool DS>
+__device__ __forceinline__ void d_load6(const float* p, float* d) {
+  if constexpr (DS) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) d[c] = p[c];
+  } else {
+    const float2* v = reinterpret_cast<const float2*>(p);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float2 w = __ldg(v + k);
+      d[2 * k] = w.x;
+      d[2 * k + 1] = w.y;
+    }
+  }
+}
+template <bool DS>
+__device__ __forceinline__ void d_load6(const df64* p, df64* d) {
+  if constexpr (DS) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) d[c] = p[c];
+  } else {
+    const float4* v = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float4 w = __ldg(v + k);
+      d[2 * k] = df64(w.x, w.y);
+      d[2 * k + 1] = df64(w.z, w.w);
+    }
+  }
+}
+
+// ------------------------------------------------ staged D (bulk copy) ----
+// One thread of the block copies the block's contiguous D tile from global
+// to shared memory with a single cp.async.bulk whose completion is counted on
+// an mbarrier (transaction bytes); every thread later waits on the barrier's
+// phase 0 before reading the tile. The wait is bounded: after `limit`
+// unsuccessful polls the block records the failure in *err and goes on (its
+// results are then wrong and the caller reports the flag), so no thread can
+// spin forever.
+__device__ __forceinline__ void stage_init(uint64_t* bar) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// src, dst 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void stage_issue(uint64_t* bar, void* dst, const void* src, unsigned bytes) {
+  const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+               "l"(src), "r"(bytes), "r"(b)
+               : "memory");
+}
+
+__device__ __forceinline__ void stage_wait(uint64_t* bar, int* err) {
+  const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  const unsigned limit = 1u << 22;
+  for (unsigned it = 0; it < limit; ++it) {
+    unsigned ok = 0;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(b)
+        : "memory");
+    if (ok) return;
+  }
+  if (err) atomicOr(err, 1);
+}
+
 template <int D1, int Q>
 struct ElemSmem {
   static constexpr int XP = D1 | 1;  // padded x rows of X
@@ -92,14 +197,18 @@ struct ElemSmem {
 };
 
 // map: the element's DOF list (e2l + e*(p+1)^3); De: its D block
-// (D + e*6*q^3); out: its E-vector slice. Dereferenced only when valid.
+// (D + e*q^3*6, point-major [q][6]); out: its E-vector slice. Dereferenced
+// only when valid.
 // T: compute type (double, float or df64); TX: type of x and out.
-template <typename T, int D1, int Q, typename TX = T>
+// DS: De points into a shared-memory tile staged by the caller, who passes
+// its barrier as bar (waited on before the tile is read) and an error word.
+template <typename T, int D1, int Q, typename TX = T, bool DS = false>
 __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32_t* __restrict__ map,
                                                   const T* __restrict__ De, T* s, const TX* __restrict__ x,
-                                                  TX* __restrict__ out) {
+                                                  TX* __restrict__ out, uint64_t* bar = nullptr,
+                                                  int* err = nullptr) {
   using L = ElemSmem<D1, Q>;
-  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, QQ = Q * Q, XP = L::XP, YP = L::YP, QP = L::QP;
+  constexpr int ND = D1 * D1 * D1, QQ = Q * Q, XP = L::XP, YP = L::YP, QP = L::QP;
   constexpr int BF = eo_off(D1, Q, 0), GF = eo_off(D1, Q, 1), BT = eo_off(D1, Q, 2), GT = eo_off(D1, Q, 3);
   constexpr int cD = (D1 + 1) / 2, hD = D1 / 2 > 0 ? D1 / 2 : 1;
   T* sX = s;                                // [z][y][XP]
@@ -163,19 +272,18 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
     eo_line<T, Q, D1, 1, BF>(rgb, g0);
     eo_line<T, Q, D1, 1, BF>(rbg, g1);
     eo_line<T, Q, D1, -1, GF>(rbb, g2);
-    const T* Dp = De + t;
+    if (DS) stage_wait(bar, err);
+    const T* Dp = De + (size_t)t * 6;  // point-major: [q][6]
 #pragma unroll
     for (int qz = 0; qz < Q; ++qz) {
-      const int o2 = qz * QQ;
-      T d00 = 0, d01 = 0, d02 = 0, d11 = 0, d12 = 0, d22 = 0;
+      T dd[6];
       if (valid) {
-        d00 = fe_ldg(Dp + 0 * NQ + o2);
-        d01 = fe_ldg(Dp + 1 * NQ + o2);
-        d02 = fe_ldg(Dp + 2 * NQ + o2);
-        d11 = fe_ldg(Dp + 3 * NQ + o2);
-        d12 = fe_ldg(Dp + 4 * NQ + o2);
-        d22 = fe_ldg(Dp + 5 * NQ + o2);
+        d_load6<DS>(Dp + (size_t)qz * QQ * 6, dd);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) dd[c] = 0;
       }
+      const T d00 = dd[0], d01 = dd[1], d02 = dd[2], d11 = dd[3], d12 = dd[4], d22 = dd[5];
       const T a0 = g0[qz], a1 = g1[qz], a2 = g2[qz];
       g0[qz] = fe_norm(d00 * a0 + d01 * a1 + d02 * a2);
       g1[qz] = fe_norm(d01 * a0 + d11 * a1 + d12 * a2);
@@ -236,10 +344,10 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
 
 // Mass: the same lines with B only and one scalar D per point
 // (Sec. 4.4, M_E = B^T D_E B). De: the element's D block (D + e*q^3).
-template <typename T, int D1, int Q, typename TX = T>
+template <typename T, int D1, int Q, typename TX = T, bool DS = false>
 __device__ __forceinline__ void mass_element(int t, bool valid, const int32_t* __restrict__ map,
                                              const T* __restrict__ De, T* s, const TX* __restrict__ x,
-                                             TX* __restrict__ out) {
+                                             TX* __restrict__ out, uint64_t* bar = nullptr, int* err = nullptr) {
   using L = ElemSmem<D1, Q>;
   constexpr int ND = D1 * D1 * D1, QQ = Q * Q, XP = L::XP, YP = L::YP, QP = L::QP;
   constexpr int BF = eo_off(D1, Q, 0), BT = eo_off(D1, Q, 2);
@@ -279,8 +387,9 @@ __device__ __forceinline__ void mass_element(int t, bool valid, const int32_t* _
 #pragma unroll
     for (int z = 0; z < D1; ++z) rbb[z] = sBB[z * QQ + t];
     eo_line<T, Q, D1, 1, BF>(rbb, u);
+    if (DS) stage_wait(bar, err);
 #pragma unroll
-    for (int qz = 0; qz < Q; ++qz) u[qz] = valid ? fe_norm(fe_ldg(De + t + qz * QQ) * u[qz]) : T(0);
+    for (int qz = 0; qz < Q; ++qz) u[qz] = valid ? fe_norm(d_load<DS>(De + t + qz * QQ) * u[qz]) : T(0);
     eo_line<T, D1, Q, 1, BT>(u, t0);
   }
   __syncthreads();

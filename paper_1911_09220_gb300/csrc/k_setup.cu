@@ -89,13 +89,14 @@ __global__ void k_setup(int64_t ne, int Q, int kind, const double* __restrict__ 
     if (kind == FEM_DIFFUSION) {
       const double s = w / det;
       // D_ab = s * sum_c adj[a][c] adj[b][c] = s * sum_c C[c][a] C[c][b]
-      double* De = Dout + e * 6 * nq + q;
-      De[0 * nq] = s * (C[0][0] * C[0][0] + C[1][0] * C[1][0] + C[2][0] * C[2][0]);
-      De[1 * nq] = s * (C[0][0] * C[0][1] + C[1][0] * C[1][1] + C[2][0] * C[2][1]);
-      De[2 * nq] = s * (C[0][0] * C[0][2] + C[1][0] * C[1][2] + C[2][0] * C[2][2]);
-      De[3 * nq] = s * (C[0][1] * C[0][1] + C[1][1] * C[1][1] + C[2][1] * C[2][1]);
-      De[4 * nq] = s * (C[0][1] * C[0][2] + C[1][1] * C[1][2] + C[2][1] * C[2][2]);
-      De[5 * nq] = s * (C[0][2] * C[0][2] + C[1][2] * C[1][2] + C[2][2] * C[2][2]);
+      // point-major: the six components of a point are contiguous
+      double* De = Dout + (e * nq + q) * 6;
+      De[0] = s * (C[0][0] * C[0][0] + C[1][0] * C[1][0] + C[2][0] * C[2][0]);
+      De[1] = s * (C[0][0] * C[0][1] + C[1][0] * C[1][1] + C[2][0] * C[2][1]);
+      De[2] = s * (C[0][0] * C[0][2] + C[1][0] * C[1][2] + C[2][0] * C[2][2]);
+      De[3] = s * (C[0][1] * C[0][1] + C[1][1] * C[1][1] + C[2][1] * C[2][1]);
+      De[4] = s * (C[0][1] * C[0][2] + C[1][1] * C[1][2] + C[2][1] * C[2][2]);
+      De[5] = s * (C[0][2] * C[0][2] + C[1][2] * C[1][2] + C[2][2] * C[2][2]);
     } else {
       Dout[e * nq + q] = w * det;
     }
