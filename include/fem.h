@@ -73,9 +73,13 @@ enum { FEM_MASS = 0, FEM_DIFFUSION = 1 };       /* bilinear form kind */
  * double-float copy of D made on first use; the operator agrees with the FP64
  * one to about 1e-13 relative (values must stay within about 1e+-30). */
 enum { FEM_F64 = 0, FEM_F32 = 1, FEM_DF64 = 2 };
-/* Solve precision: FP64 CG; FP32 inner CG in FP64 refinement; FP64 CG whose
- * operator applies run in double-float (FEM_DF64). */
-enum { FEM_SOLVE_F64 = 0, FEM_SOLVE_MIXED = 1, FEM_SOLVE_DF64 = 2 };
+/* Solve precision: FP64 CG; FP32 inner CG restarted inside FP64 iterative
+ * refinement; FP64 CG whose operator applies run in double-float
+ * (FEM_DF64); FP32 CG with FP64 reliable updates (the FP32 increment is
+ * folded into the FP64 solution and the residual replaced by the FP64 true
+ * residual whenever it has dropped by inner_rtol, without restarting the
+ * search direction). */
+enum { FEM_SOLVE_F64 = 0, FEM_SOLVE_MIXED = 1, FEM_SOLVE_DF64 = 2, FEM_SOLVE_MIXED_RU = 3 };
 
 typedef struct fem_mesh fem_mesh;
 typedef struct fem_space fem_space;
@@ -210,7 +214,8 @@ typedef struct {
   double rtol;          /* relative tolerance, e.g. 1e-10 */
   int maxit;            /* cap on (inner, for mixed) CG iterations */
   int precision;        /* FEM_SOLVE_F64 or FEM_SOLVE_MIXED */
-  double inner_rtol;    /* mixed: inner relative tolerance (e.g. 1e-4) */
+  double inner_rtol;    /* mixed: inner relative tolerance (e.g. 1e-4); reliable
+                           updates: residual drop between updates (e.g. 1e-2) */
   int max_outer;        /* mixed: cap on refinement steps */
   int check_every;      /* iterations per CUDA-graph launch between host polls */
   int use_graph;        /* capture check_every iterations in a CUDA graph */

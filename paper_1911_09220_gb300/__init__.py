@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _binding as B
 from ._binding import (FemError, FEM_DIFFUSION, FEM_MASS, FEM_F64, FEM_F32, FEM_DF64, FEM_SOLVE_F64,
-                       FEM_SOLVE_MIXED, FEM_SOLVE_DF64)
+                       FEM_SOLVE_MIXED, FEM_SOLVE_DF64, FEM_SOLVE_MIXED_RU)
 
 __all__ = ["Mesh", "Space", "Form", "Batch", "FemError", "lib", "supported", "version"]
 
@@ -211,13 +211,21 @@ class Form:
                                      _ptr(bc, torch.float64, "bc"), _stream(stream)))
         return bc
 
-    def solve(self, b, x, rtol=1e-10, maxit=20000, precision="f64", inner_rtol=1e-4, max_outer=30,
+    def solve(self, b, x, rtol=1e-10, maxit=20000, precision="f64", inner_rtol=None, max_outer=30,
               check_every=16, use_graph=True, stream=None, raise_on_error=True):
+        """Jacobi-PCG on the constrained operator. precision: "f64", "df64"
+        (FP64 CG, double-float operator), "mixed" (FP32 inner CG restarted in
+        FP64 refinement; inner_rtol default 1e-4) or "mixed_ru" (FP32 CG with
+        FP64 reliable updates; inner_rtol = residual drop between updates,
+        default 1e-2)."""
         import torch
         o = B.SolveOpts()
         B.lib().fem_solve_opts_default(C.byref(o))
+        if inner_rtol is None:
+            inner_rtol = 1e-2 if precision == "mixed_ru" else 1e-4
         o.rtol, o.maxit, o.inner_rtol, o.max_outer = rtol, maxit, inner_rtol, max_outer
-        o.precision = {"f64": FEM_SOLVE_F64, "mixed": FEM_SOLVE_MIXED, "df64": FEM_SOLVE_DF64}[precision]
+        o.precision = {"f64": FEM_SOLVE_F64, "mixed": FEM_SOLVE_MIXED, "df64": FEM_SOLVE_DF64,
+                       "mixed_ru": FEM_SOLVE_MIXED_RU}[precision]
         o.check_every, o.use_graph = check_every, int(bool(use_graph))
         info = B.SolveInfo()
         st = B.lib().fem_solve(self._h, _ptr(b, torch.float64, "b"), _ptr(x, torch.float64, "x"), C.byref(o),

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_PKG, "libfem.so")
 FEM_OK, FEM_EINVAL, FEM_ENOMEM, FEM_EINVERTED, FEM_ENOCONV, FEM_EBREAKDOWN, FEM_ECUDA, FEM_EUNSUPPORTED = range(8)
 FEM_MASS, FEM_DIFFUSION = 0, 1
 FEM_F64, FEM_F32, FEM_DF64 = 0, 1, 2
-FEM_SOLVE_F64, FEM_SOLVE_MIXED, FEM_SOLVE_DF64 = 0, 1, 2
+FEM_SOLVE_F64, FEM_SOLVE_MIXED, FEM_SOLVE_DF64, FEM_SOLVE_MIXED_RU = 0, 1, 2, 3
 
 STATUS_NAMES = {
     0: "FEM_OK", 1: "FEM_EINVAL", 2: "FEM_ENOMEM", 3: "FEM_EINVERTED", 4: "FEM_ENOCONV",

@@ -22,9 +22,12 @@ namespace {
 
 struct CgScalars {
   double rz, alpha, beta, rr, bb, tol2, pq;
+  double upd2;      // reliable updates: stop for an FP64 update once r.r <= upd2
+  double rz_new;    // r.z of the iteration that stopped for an update
   int it, done, status, maxit;
+  int ru;           // 1: reliable-update mode
 };
-enum { ST_RUN = 0, ST_CONV = 1, ST_NOCONV = 2, ST_BREAK = 3 };
+enum { ST_RUN = 0, ST_CONV = 1, ST_NOCONV = 2, ST_BREAK = 3, ST_UPDATE = 4 };
 
 constexpr int kRedThreads = 256;
 
@@ -74,6 +77,8 @@ __global__ void k_cg_init_scalars(CgScalars* sc, const double* __restrict__ part
     sc->maxit = maxit;
     sc->status = ST_RUN;
     sc->done = 0;
+    sc->ru = 0;
+    sc->upd2 = 0.0;
     if (rr <= sc->tol2) {
       sc->done = 1;
       sc->status = ST_CONV;
@@ -134,6 +139,12 @@ __global__ void k_cg_beta(CgScalars* sc, const double* __restrict__ part, int nb
     if (!isfinite(rz) || !isfinite(rr)) {
       sc->done = 1;
       sc->status = ST_BREAK;
+    } else if (sc->ru && (rr <= sc->upd2 || rr <= sc->tol2)) {
+      // reliable-update mode: hand over to the host for an FP64 update (the
+      // true residual decides convergence); beta waits for the new residual
+      sc->done = 1;
+      sc->status = ST_UPDATE;
+      sc->rz_new = rz;
     } else if (rr <= sc->tol2) {
       sc->done = 1;
       sc->status = ST_CONV;
@@ -145,6 +156,58 @@ __global__ void k_cg_beta(CgScalars* sc, const double* __restrict__ part, int nb
       sc->rz = rz;
     }
   }
+}
+
+// After a reliable update replaced r: z = r / diag and partials of r.z.
+template <typename T>
+__global__ void k_cg_rz(int64_t n, const T* __restrict__ r, const T* __restrict__ diag, T* __restrict__ z,
+                        double* __restrict__ part) {
+  __shared__ double red[32];
+  double rz = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T ri = r[i];
+    const T zi = ri / diag[i];
+    z[i] = zi;
+    rz += (double)ri * (double)zi;
+  }
+  const double s = block_sum(rz, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// Resume after a reliable update: beta from the new r.z, next update
+// threshold, iteration continues (p = z + beta p follows).
+__global__ void k_cg_resume(CgScalars* sc, const double* __restrict__ part, int nb, double upd2) {
+  __shared__ double red[32];
+  const double rz = sum_partials(part, nb, red);
+  if (threadIdx.x == 0) {
+    sc->beta = rz / sc->rz;
+    sc->rz = rz;
+    sc->upd2 = upd2;
+    sc->status = ST_RUN;
+    sc->done = 0;
+    if (!isfinite(rz) || !(rz > 0.0)) {
+      sc->done = 1;
+      sc->status = ST_BREAK;
+    }
+  }
+}
+
+__global__ void k_cg_set_ru(CgScalars* sc, double upd2) {
+  sc->ru = 1;
+  sc->upd2 = upd2;
+}
+
+// x += (double) d; d = 0 (fold the FP32 increment into the FP64 solution).
+__global__ void k_fold(int64_t n, double* __restrict__ x, float* __restrict__ d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += (double)d[i];
+    d[i] = 0.0f;
+  }
+}
+
+__global__ void k_cast_r32(int64_t n, const double* __restrict__ r, float* __restrict__ r32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r32[i] = (float)r[i];
 }
 
 template <typename T>
@@ -386,11 +449,13 @@ extern "C" fem_status fem_solve(const fem_form* fc, const double* b, double* xio
   fem_solve_opts_default(&o);
   if (opts) o = *opts;
   if (!(o.rtol > 0) || o.maxit <= 0) return fem_fail(FEM_EINVAL, "fem_solve: rtol > 0 and maxit > 0 required");
-  if (o.precision != FEM_SOLVE_F64 && o.precision != FEM_SOLVE_MIXED && o.precision != FEM_SOLVE_DF64)
+  if (o.precision != FEM_SOLVE_F64 && o.precision != FEM_SOLVE_MIXED && o.precision != FEM_SOLVE_DF64 &&
+      o.precision != FEM_SOLVE_MIXED_RU)
     return fem_fail(FEM_EINVAL, "fem_solve: unknown precision %d", o.precision);
   fem_form* f = const_cast<fem_form*>(fc);
   cudaStream_t s = (cudaStream_t)stream;
-  const bool mixed = o.precision == FEM_SOLVE_MIXED;
+  const bool ru = o.precision == FEM_SOLVE_MIXED_RU;
+  const bool mixed = o.precision == FEM_SOLVE_MIXED || ru;
   Work w;
   FEM_TRY(get_work(f, mixed, w));
   if (mixed) FEM_TRY(fem_form_ensure_f32(f, s));
@@ -425,7 +490,58 @@ extern "C" fem_status fem_solve(const fem_form* fc, const double* b, double* xio
     return FEM_OK;
   }
   double rr = 0;
-  for (;;) {
+  if (ru) {
+    // FP32 CG with reliable updates: the search direction is never restarted;
+    // when the FP32 residual has dropped by delta since the last update, the
+    // FP32 increment is folded into the FP64 solution and the residual is
+    // replaced by the FP64 true residual b - A_c x.
+    const double delta2 = o.inner_rtol * o.inner_rtol;
+    float* x32 = w.x32;
+    float* r32 = w.r32;
+    FEM_TRY(true_residual(f, w, b, w.x, w.r, rr_dev, s));
+    FEM_TRY(read_doubles(f, rr_dev, 1, &rr, s));
+    status = ST_NOCONV;
+    if (!std::isfinite(rr)) status = ST_BREAK;
+    else if (rr <= tol2) status = ST_CONV;
+    if (status == ST_NOCONV) {
+      k_cast_f32<<<w.nb, 256, 0, s>>>(n, w.diag, w.diag32);
+      k_cast_r32<<<w.nb, 256, 0, s>>>(n, w.r, r32);
+      FEM_CUDA(cudaMemsetAsync(x32, 0, sizeof(float) * n, s));
+      k_cg_init<float><<<w.nb, 256, 0, s>>>(n, r32, w.diag32, w.z32, w.p32, nullptr, w.part);
+      k_cg_init_scalars<<<1, kRedThreads, 0, s>>>(w.sc, w.part, w.nb, o.rtol, bb, o.maxit);
+      k_cg_set_ru<<<1, 1, 0, s>>>(w.sc, delta2 * rr);
+      FEM_LAUNCHED();
+      for (;;) {
+        fem_solve_opts oi = o;
+        int st_in = ST_NOCONV, it_in = 0;
+        FEM_TRY(cg_loop<float>(f, w, FEM_F32, x32, r32, w.z32, w.p32, w.q32, w.diag32, oi, s, &st_in, &it_in));
+        total_it = it_in;  // the device counter runs across updates
+        k_fold<<<w.nb, 256, 0, s>>>(n, w.x, x32);
+        FEM_LAUNCHED();
+        ++outer;
+        FEM_TRY(true_residual(f, w, b, w.x, w.r, rr_dev, s));
+        FEM_TRY(read_doubles(f, rr_dev, 1, &rr, s));
+        if (!std::isfinite(rr) || st_in == ST_BREAK) {
+          status = ST_BREAK;
+          break;
+        }
+        if (rr <= tol2) {
+          status = ST_CONV;
+          break;
+        }
+        if (total_it >= o.maxit || st_in == ST_NOCONV || outer > 100000) {
+          status = ST_NOCONV;
+          break;
+        }
+        k_cast_r32<<<w.nb, 256, 0, s>>>(n, w.r, r32);
+        k_cg_rz<float><<<w.nb, 256, 0, s>>>(n, r32, w.diag32, w.z32, w.part);
+        k_cg_resume<<<1, kRedThreads, 0, s>>>(w.sc, w.part, w.nb, delta2 * rr);
+        k_cg_p<float><<<w.nb, 256, 0, s>>>(n, w.sc, w.z32, w.p32);
+        FEM_LAUNCHED();
+      }
+    }
+  }
+  for (; !ru;) {
     FEM_TRY(true_residual(f, w, b, w.x, w.r, rr_dev, s));
     FEM_TRY(read_doubles(f, rr_dev, 1, &rr, s));
     if (!std::isfinite(rr)) {

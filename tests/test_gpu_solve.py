@@ -42,7 +42,7 @@ def _torch_f_sin3(xq):
     return 3 * np.pi ** 2 * torch.sin(np.pi * xq[..., 0]) * torch.sin(np.pi * xq[..., 1]) * torch.sin(np.pi * xq[..., 2])
 
 
-@pytest.mark.parametrize("precision", ["f64", "mixed", "df64"])
+@pytest.mark.parametrize("precision", ["f64", "mixed", "df64", "mixed_ru"])
 @pytest.mark.parametrize("graph", [True, False])
 def test_config1_solve(precision, graph):
     """4x4x4 mesh, +-0.1h, Q2, 4^3 Gauss points, kappa = 1, 729 DOFs,
@@ -88,7 +88,7 @@ def test_solve_lognormal_nonzero_dirichlet(p):
     bc = torch.empty(cs.n, dtype=torch.float64, device="cuda")
     cs.form.lift_rhs(cuda(bvec), cuda(gvec), bc)
     x = cuda(np.where(np.isin(np.arange(cs.n), ess), gvec, 0.0))
-    for precision in ("f64", "mixed", "df64"):
+    for precision in ("f64", "mixed", "df64", "mixed_ru"):
         xx = x.clone()
         info = cs.form.solve(bc, xx, rtol=1e-10, precision=precision)
         u = xx.cpu().numpy()
