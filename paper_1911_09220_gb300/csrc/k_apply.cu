@@ -9,101 +9,9 @@
 #include "fem_internal.h"
 #include "k_common.cuh"
 #include "k_element.cuh"
+#include "k_apply_kernels.cuh"
 
 namespace {
-
-// Elements per block for a (Q x Q) thread plane: Q^2 * NE fills whole (or
-// nearly whole) warps, 128-320 threads per block. Inactive lanes still occupy
-// an issued FP64 instruction, so a half-empty last warp costs throughput.
-constexpr int ne_for_q(int Q) {
-  return Q <= 3 ? 32 : Q == 4 ? 16 : Q == 5 ? 5 : Q == 6 ? 8 : Q == 7 ? 5 : Q == 8 ? 4 : 3;
-}
-
-// Shared-memory plan of a block: NE element slabs, then (STAGE) the staged D
-// tile of the block's elements (+16 bytes for the alignment shift), then the
-// mbarrier.
-template <typename T, int D1, int Q, int NE, int NCOMP, bool STAGE>
-struct BlockSmem {
-  static constexpr size_t slabs = (sizeof(T) * NE * ElemSmem<D1, Q>::SE + 15) / 16 * 16;
-  static constexpr size_t tile = STAGE ? (sizeof(T) * NE * NCOMP * Q * Q * Q + 16 + 15) / 16 * 16 : 0;
-  static constexpr size_t bytes = slabs + tile + (STAGE ? 16 : 0);
-};
-
-// Issue the bulk copy of the block's D tile (elements e0 .. e0+nel-1) and
-// return where element 0 of the tile lands in shared memory. The source is
-// rounded down to 16 bytes (the array is padded by 16 bytes at the end).
-template <typename T, int NCOMP, int NQ>
-__device__ __forceinline__ const T* stage_tile(unsigned char* tile, uint64_t* bar, const T* Dq, int e0, int nel,
-                                               bool issuer) {
-  const uintptr_t src = reinterpret_cast<uintptr_t>(Dq + (size_t)e0 * NCOMP * NQ);
-  const uintptr_t src_al = src & ~(uintptr_t)15;
-  const unsigned shift = (unsigned)(src - src_al);
-  if (issuer) {
-    const unsigned bytes = (unsigned)(sizeof(T) * (size_t)nel * NCOMP * NQ);
-    const unsigned total = (bytes + shift + 15u) & ~15u;
-    stage_issue(bar, tile, reinterpret_cast<const void*>(src_al), total);
-  }
-  return reinterpret_cast<const T*>(tile + shift);
-}
-
-template <typename T, int D1, int Q, int NE, typename TX, bool STAGE>
-__global__ void __launch_bounds__(Q * Q * NE)
-k_diffusion_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
-                  const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye, int* __restrict__ err) {
-  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<D1, Q>::SE;
-  using BS = BlockSmem<T, D1, Q, NE, 6, STAGE>;
-  if (skip && *skip) return;  // a captured solver iteration after convergence
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  const int t = threadIdx.x + Q * threadIdx.y, tz = threadIdx.z;
-  const int e0 = blockIdx.x * NE;
-  const int nel = min(NE, ne - e0);
-  const int e = e0 + tz;
-  const bool valid = e < ne;
-  const size_t ev = valid ? (size_t)e : 0;
-  if constexpr (STAGE) {
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + BS::slabs + BS::tile);
-    const bool issuer = t == 0 && tz == 0;
-    if (issuer) stage_init(bar);
-    __syncthreads();
-    const T* tileD = stage_tile<T, 6, NQ>(smem_raw + BS::slabs, bar, Dq, e0, nel, issuer);
-    diffusion_element<T, D1, Q, TX, true>(t, valid, e2l + ev * ND, tileD + (size_t)tz * 6 * NQ, sm + tz * SE, x,
-                                          ye + ev * ND, bar, err);
-  } else {
-    if (t == 0 && tz == 0)  // D of the block's elements: read in stage S3, fetch into L2 now
-      l2_prefetch_range(Dq + (size_t)e0 * 6 * NQ, sizeof(T) * (size_t)nel * 6 * NQ);
-    diffusion_element<T, D1, Q, TX>(t, valid, e2l + ev * ND, Dq + ev * 6 * NQ, sm + tz * SE, x, ye + ev * ND);
-  }
-}
-
-template <typename T, int D1, int Q, int NE, typename TX, bool STAGE>
-__global__ void __launch_bounds__(Q * Q * NE)
-k_mass_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
-             const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye, int* __restrict__ err) {
-  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<D1, Q>::SE;
-  using BS = BlockSmem<T, D1, Q, NE, 1, STAGE>;
-  if (skip && *skip) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  const int t = threadIdx.x + Q * threadIdx.y, tz = threadIdx.z;
-  const int e0 = blockIdx.x * NE;
-  const int nel = min(NE, ne - e0);
-  const int e = e0 + tz;
-  const bool valid = e < ne;
-  const size_t ev = valid ? (size_t)e : 0;
-  if constexpr (STAGE) {
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + BS::slabs + BS::tile);
-    const bool issuer = t == 0 && tz == 0;
-    if (issuer) stage_init(bar);
-    __syncthreads();
-    const T* tileD = stage_tile<T, 1, NQ>(smem_raw + BS::slabs, bar, Dq, e0, nel, issuer);
-    mass_element<T, D1, Q, TX, true>(t, valid, e2l + ev * ND, tileD + (size_t)tz * NQ, sm + tz * SE, x,
-                                     ye + ev * ND, bar, err);
-  } else {
-    if (t == 0 && tz == 0) l2_prefetch_range(Dq + (size_t)e0 * NQ, sizeof(T) * (size_t)nel * NQ);
-    mass_element<T, D1, Q, TX>(t, valid, e2l + ev * ND, Dq + ev * NQ, sm + tz * SE, x, ye + ev * ND);
-  }
-}
 
 template <typename K>
 fem_status prepare_smem(K kernel, size_t bytes) {
@@ -145,22 +53,53 @@ fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G
   return FEM_OK;
 }
 
+// y_i = sum over the inverse map of ye (fixed order: the slots of DOF i in
+// increasing (element, local index) order), optional constraint rows
+// (y_i = xin_i where mask_i) and per-block partial sums of xin . y. Each
+// thread keeps kU DOFs in flight (their off -> idx -> ye load chains are
+// independent), the DOFs of one round being kU grid strides apart so that
+// every load stays coalesced across the warp.
 template <typename T>
 __global__ void k_scatter(const int* __restrict__ skip, int64_t ndof, const int32_t* __restrict__ off,
                           const int32_t* __restrict__ idx, const T* __restrict__ ye, T* __restrict__ y,
                           const uint8_t* __restrict__ mask, const T* __restrict__ xin,
                           double* __restrict__ pdot) {
+  constexpr int kU = 4;
   __shared__ double red[32];
   if (skip && *skip) return;
   double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ndof;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t a = __ldg(off + i), b = __ldg(off + i + 1);
-    T sum = 0;
-    for (int32_t k = a; k < b; ++k) sum += __ldg(ye + __ldg(idx + k));
-    if (mask && mask[i]) sum = xin[i];
-    y[i] = sum;
-    if (pdot) acc += (double)xin[i] * (double)sum;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < ndof; base += stride * kU) {
+    int32_t a[kU], b[kU];
+    int len = 0;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = base + u * stride;
+      a[u] = i < ndof ? __ldg(off + i) : 0;
+      b[u] = i < ndof ? __ldg(off + i + 1) : 0;
+      len = max(len, b[u] - a[u]);
+    }
+    T sum[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) sum[u] = 0;
+    for (int j = 0; j < len; ++j) {
+      int32_t sl[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) sl[u] = a[u] + j < b[u] ? __ldg(idx + a[u] + j) : -1;
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (sl[u] >= 0) sum[u] += __ldg(ye + sl[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = base + u * stride;
+      if (i < ndof) {
+        T v = sum[u];
+        if (mask && mask[i]) v = xin[i];
+        y[i] = v;
+        if (pdot) acc += (double)xin[i] * (double)v;
+      }
+    }
   }
   if (pdot) {
     const double tot = block_sum(acc, red);
