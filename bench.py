@@ -261,6 +261,12 @@ def run_sweep(args):
             x32 = x.float()
             y32 = torch.empty_like(x32)
             t32 = time_events(lambda: form.apply(x32, y32), args.steps, 3)
+            ye = torch.empty((E, (p + 1) ** 3), dtype=torch.float64, device="cuda")
+            ye32 = torch.empty((E, (p + 1) ** 3), dtype=torch.float32, device="cuda")
+            te64 = time_events(lambda: form.apply_element(x, ye), args.steps, 3)
+            te32 = time_events(lambda: form.apply_element(x32, ye32), args.steps, 3)
+            tedf = time_events(lambda: form.apply_element(x, ye, arith="df64"), args.steps, 3)
+            del ye, ye32
             d = torch.empty_like(x)
             tdiag = time_events(lambda: form.diagonal(d), 3, 1)
             out[kind] = {
@@ -268,7 +274,8 @@ def run_sweep(args):
                 "f64_frac_fp64_peak": flops / t64 * 1e-9 / FP64_PEAK_TFLOPS,
                 "f32_gdofs": n / t32 * 1e-6, "f32_ms": t32, "f32_alg_gbs": bytes32 / t32 * 1e-6,
                 "f32_frac_hbm": bytes32 / t32 * 1e-6 / peaks().get("hbm_gbs", 6800.0),
-                "setup_ms": tset, "diag_ms": tdiag}
+                "setup_ms": tset, "diag_ms": tdiag,
+                "element_ms": {"f64": te64, "f32": te32, "df64": tedf}}
             if kind == "diffusion":
                 b = torch.empty_like(x)
                 out["rhs_ms"] = time_events(lambda: _sin_rhs(form, b), 2, 1)

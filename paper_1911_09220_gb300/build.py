@@ -43,8 +43,16 @@ def _sources():
     return [os.path.join(CSRC, s) for s in srcs], headers
 
 
+def _defines():
+    """Build options from the environment: FEM_NE_TABLE=large|small selects
+    one candidate elements-per-block table for every element type (used to
+    re-measure the choice); unset or `measured` gives the measured table."""
+    t = os.environ.get("FEM_NE_TABLE", "measured")
+    return {"large": ["-DFEM_NE_TABLE=1"], "small": ["-DFEM_NE_TABLE=2"]}.get(t, [])
+
+
 def _compile(src, obj, nvcc, cuda_home, verbose_ptxas):
-    inc = ["-I", INCLUDE, "-I", CSRC]
+    inc = ["-I", INCLUDE, "-I", CSRC, *_defines()]
     if src.endswith(".cu"):
         cmd = [nvcc, "-c", src, "-o", obj, "-std=c++17", "-O3", "-lineinfo", *ARCH,
                "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", *inc]
@@ -65,6 +73,12 @@ def build(force=False, jobs=None, verbose_ptxas=False, quiet=True):
     os.makedirs(BUILD, exist_ok=True)
     srcs, headers = _sources()
     hdr_mtime = max(os.path.getmtime(h) for h in headers)
+    stamp = os.path.join(BUILD, "options")
+    opts = " ".join(_defines())
+    if not os.path.exists(stamp) or open(stamp).read() != opts:
+        force = True
+        with open(stamp, "w") as fh:
+            fh.write(opts)
     todo = []
     objs = []
     for s in srcs:

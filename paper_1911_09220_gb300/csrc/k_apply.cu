@@ -30,7 +30,7 @@ constexpr bool stages_D() { return false; }
 template <typename T, int P, int Q, typename TX = T>
 fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G, const TX* x, TX* ye,
                            const int* skip, cudaStream_t s) {
-  constexpr int D1 = P + 1, NE = ne_for_q(Q);
+  constexpr int D1 = P + 1, NE = ne_for<T>(Q);
   const int ne = (int)f->space->ne;
   const dim3 block(Q, Q, NE);
   const int grid = (ne + NE - 1) / NE;

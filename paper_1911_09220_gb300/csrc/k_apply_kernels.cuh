@@ -4,10 +4,32 @@
 #pragma once
 
 // Elements per block for a (Q x Q) thread plane: Q^2 * NE fills whole (or
-// nearly whole) warps, 128-320 threads per block. Inactive lanes still occupy
-// an issued FP64 instruction, so a half-empty last warp costs throughput.
-constexpr int ne_for_q(int Q) {
+// nearly whole) warps (inactive lanes still occupy an issued FP64
+// instruction). The choice per element type and Q comes from measuring both
+// candidates of every order on GB300 (p = 1..8, q = p + 2, ~4e6 DOFs): the
+// FP64 kernels keep the larger blocks (more warps hide the FP64 pipe's
+// latency), the FP32 kernels run faster with smaller blocks for Q >= 6 (more
+// independent blocks in flight on their memory latency), and double-float
+// prefers the smaller block at Q = 3, 5, 8, 9.
+constexpr int ne_large(int Q) {
   return Q <= 3 ? 32 : Q == 4 ? 16 : Q == 5 ? 5 : Q == 6 ? 8 : Q == 7 ? 5 : Q == 8 ? 4 : 3;
+}
+constexpr int ne_small(int Q) {
+  return Q == 2 ? 16 : Q == 3 ? 14 : Q == 4 ? 8 : Q == 5 ? 10 : Q == 6 ? 4 : Q == 7 ? 2 : Q == 8 ? 2 : Q == 9 ? 1 : 2;
+}
+// FEM_NE_TABLE (build option): 1 = large for every type, 2 = small for
+// every type (the candidate tables of the measurement), else the measured
+// choice.
+template <typename T>
+constexpr int ne_for(int Q) {
+#if defined(FEM_NE_TABLE) && FEM_NE_TABLE == 1
+  return ne_large(Q);
+#elif defined(FEM_NE_TABLE) && FEM_NE_TABLE == 2
+  return ne_small(Q);
+#endif
+  if (std::is_same<T, float>::value) return Q >= 6 ? ne_small(Q) : ne_large(Q);
+  if (std::is_same<T, double>::value) return Q == 10 ? ne_small(Q) : ne_large(Q);
+  return (Q == 3 || Q == 5 || Q == 8 || Q == 9) ? ne_small(Q) : ne_large(Q);  // double-float
 }
 
 // Shared-memory plan of a block: NE element slabs, then (STAGE) the staged D

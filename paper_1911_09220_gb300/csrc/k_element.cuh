@@ -31,6 +31,8 @@
 
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "k_df64.cuh"
 #include "k_tables.cuh"
 
@@ -186,6 +188,37 @@ __device__ __forceinline__ void stage_wait(uint64_t* bar, int* err) {
   if (err) atomicOr(err, 1);
 }
 
+// Gather the element's DOF values x[map[k]] into the padded X rows: each
+// thread first loads all its map entries, then all its x values, so the
+// dependent load pairs of its ceil(D1^3 / Q^2) points are in flight together.
+// (The FP64 kernel, bound by its arithmetic pipe, measured 1.2 % faster with
+// the plain strided loop, which it keeps.)
+template <typename T, int D1, int Q, typename TX>
+__device__ __forceinline__ void gather_x(int t, bool valid, const int32_t* __restrict__ map,
+                                         const TX* __restrict__ x, T* sX, int XP) {
+  constexpr int ND = D1 * D1 * D1, QQ = Q * Q, NG = (ND + QQ - 1) / QQ;
+  if constexpr (std::is_same<T, double>::value) {
+    if (valid) {
+      for (int k = t; k < ND; k += QQ) sX[(k / D1) * XP + k % D1] = fe_from<T>(__ldg(x + __ldg(map + k)));
+    }
+  } else {
+    int32_t m[NG];
+#pragma unroll
+    for (int j = 0; j < NG; ++j) {
+      const int k = t + j * QQ;
+      m[j] = (valid && k < ND) ? __ldg(map + k) : -1;
+    }
+    TX v[NG];
+#pragma unroll
+    for (int j = 0; j < NG; ++j) v[j] = m[j] >= 0 ? __ldg(x + m[j]) : TX(0);
+#pragma unroll
+    for (int j = 0; j < NG; ++j) {
+      const int k = t + j * QQ;
+      if (m[j] >= 0) sX[(k / D1) * XP + k % D1] = fe_from<T>(v[j]);
+    }
+  }
+}
+
 template <int D1, int Q>
 struct ElemSmem {
   static constexpr int XP = D1 | 1;  // padded x rows of X
@@ -208,7 +241,7 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
                                                   TX* __restrict__ out, uint64_t* bar = nullptr,
                                                   int* err = nullptr) {
   using L = ElemSmem<D1, Q>;
-  constexpr int ND = D1 * D1 * D1, QQ = Q * Q, XP = L::XP, YP = L::YP, QP = L::QP;
+  constexpr int QQ = Q * Q, XP = L::XP, YP = L::YP, QP = L::QP;
   constexpr int BF = eo_off(D1, Q, 0), GF = eo_off(D1, Q, 1), BT = eo_off(D1, Q, 2), GT = eo_off(D1, Q, 3);
   constexpr int cD = (D1 + 1) / 2, hD = D1 / 2 > 0 ? D1 / 2 : 1;
   T* sX = s;                                // [z][y][XP]
@@ -217,12 +250,7 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
   T* sBB = sGX + D1 * Q * YP;               // [z][qy][qx]
   T* sGB = sBB + D1 * QQ;
   T* sBG = sGB + D1 * QQ;
-  if (valid) {
-    for (int k = t; k < ND; k += QQ) {
-      const int xi = k % D1, row = k / D1;
-      sX[row * XP + xi] = fe_from<T>(__ldg(x + __ldg(map + k)));
-    }
-  }
+  gather_x<T, D1, Q, TX>(t, valid, map, x, sX, XP);
   __syncthreads();
   if (t < D1 * D1) {  // S1: line (z, y) along x
     const int z = t / D1, y = t % D1;
@@ -349,17 +377,12 @@ __device__ __forceinline__ void mass_element(int t, bool valid, const int32_t* _
                                              const T* __restrict__ De, T* s, const TX* __restrict__ x,
                                              TX* __restrict__ out, uint64_t* bar = nullptr, int* err = nullptr) {
   using L = ElemSmem<D1, Q>;
-  constexpr int ND = D1 * D1 * D1, QQ = Q * Q, XP = L::XP, YP = L::YP, QP = L::QP;
+  constexpr int QQ = Q * Q, XP = L::XP, YP = L::YP, QP = L::QP;
   constexpr int BF = eo_off(D1, Q, 0), BT = eo_off(D1, Q, 2);
   T* sX = s;
   T* sBX = sX + D1 * D1 * XP;
   T* sBB = sBX + D1 * Q * YP;
-  if (valid) {
-    for (int k = t; k < ND; k += QQ) {
-      const int xi = k % D1, row = k / D1;
-      sX[row * XP + xi] = fe_from<T>(__ldg(x + __ldg(map + k)));
-    }
-  }
+  gather_x<T, D1, Q, TX>(t, valid, map, x, sX, XP);
   __syncthreads();
   if (t < D1 * D1) {
     const int z = t / D1, y = t % D1;
