@@ -22,11 +22,11 @@ partial-assembly discussion of Sec. 4.4):
 """
 
 from .rng import splitmix64, uniform01, uniform, normal, permutation
-from .mesh import hex_lattice, CUBE_ROTATIONS, lattice_dofs, submesh
+from .mesh import hex_lattice, CUBE_ROTATIONS, lattice_dofs, submesh, quad_lattice
 from .fields import lognormal, x_uniform, rho_uniform
 
 __all__ = [
     "splitmix64", "uniform01", "uniform", "normal", "permutation",
-    "hex_lattice", "CUBE_ROTATIONS", "lattice_dofs", "submesh",
+    "hex_lattice", "CUBE_ROTATIONS", "lattice_dofs", "submesh", "quad_lattice",
     "lognormal", "x_uniform", "rho_uniform",
 ]

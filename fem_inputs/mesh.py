@@ -114,3 +114,40 @@ def submesh(coords, hexes, keep):
     remap[order] = np.arange(order.size)
     return (np.ascontiguousarray(np.asarray(coords)[order]),
             np.ascontiguousarray(remap[hexes].astype(np.int32)))
+
+
+def quad_lattice(N, perturb=0.0, seed=1, shuffle=False, shuffle_seed=None):
+    """N^2 quadrilaterals on the unit square, local vertex order 0:(0,0)
+    1:(1,0) 2:(1,1) 3:(0,1) (counter-clockwise). Returns (coords float64
+    [nv,2], quads int32 [E,4]). Perturbation and shuffling as in
+    hex_lattice (boundary vertices move only along the boundary; shuffling
+    renumbers vertices and elements and rotates each element's vertex list
+    cyclically)."""
+    N = int(N)
+    if N < 1:
+        raise ValueError("N must be >= 1")
+    n1 = N + 1
+    h = 1.0 / N
+    j, i = np.meshgrid(np.arange(n1), np.arange(n1), indexing="ij")
+    idx = np.stack([i.ravel(), j.ravel()], axis=1)
+    coords = idx.astype(np.float64) / N
+    if perturb > 0.0:
+        nv = idx.shape[0]
+        d = uniform(seed, 2 * nv, -1.0, 1.0).reshape(nv, 2) * (perturb * h)
+        coords = coords + np.where((idx > 0) & (idx < N), d, 0.0)
+    ej, ei = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    base = (ei.ravel() + n1 * ej.ravel()).astype(np.int64)
+    quads = base[:, None] + np.array([0, 1, 1 + n1, n1], dtype=np.int64)[None, :]
+    if shuffle:
+        s = seed if shuffle_seed is None else shuffle_seed
+        nv = coords.shape[0]
+        vperm = permutation(s * 7 + 1, nv)
+        inv = np.empty(nv, dtype=np.int64)
+        inv[vperm] = np.arange(nv)
+        coords = coords[vperm]
+        quads = inv[quads]
+        quads = quads[permutation(s * 7 + 2, quads.shape[0])]
+        rot = (splitmix64(s * 7 + 3, quads.shape[0]) % np.uint64(4)).astype(np.int64)
+        cyc = np.array([[0, 1, 2, 3], [1, 2, 3, 0], [2, 3, 0, 1], [3, 0, 1, 2]], dtype=np.int64)
+        quads = np.take_along_axis(quads, cyc[rot], axis=1)
+    return np.ascontiguousarray(coords), np.ascontiguousarray(quads.astype(np.int32))

@@ -25,7 +25,8 @@ matrix with the same quadrature):
 * global CSR assembly, SpMV and diagonal (`assemble`);
 * essential-BC elimination, load vector, Jacobi-PCG and dense Cholesky
   (`solve`, Sec. 2 and Sec. 5.1);
-* the compliance gradient dJ/dkappa_e = -u_e^T Khat_e u_e (`gradient`).
+* the compliance gradient dJ/dkappa_e = -u_e^T Khat_e u_e (`gradient`);
+* the same definitions on quadrilaterals in 2D (`twod`).
 
 Parity status: every function is pinned by `tests/test_oracle_*.py` against
 closed forms, invariants or brute force, except the mixed-precision error,
@@ -33,4 +34,4 @@ which has no oracle of its own (parity unpinned beyond the FP64 outer
 residual; the error against this FP64 oracle is reported per result).
 """
 
-from . import rules, lagrange, numbering, element, assemble, solve, gradient  # noqa: F401
+from . import rules, lagrange, numbering, element, assemble, solve, gradient, twod  # noqa: F401
