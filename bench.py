@@ -40,10 +40,18 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_element_kernel.txt")
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
-def alg_counts(p, q, E, n, kind="diffusion", fp=8):
+def alg_counts(p, q, E, n, kind="diffusion", fp=8, dim=3):
     """Algorithmic flops and bytes of one apply (stream D once, read the map
     once, read x and write y once)."""
     D1, Q = p + 1, q
+    if dim == 2:
+        if kind == "diffusion":
+            flops_e = 2 * (4 * Q * D1 ** 2 + 4 * Q ** 2 * D1) + 6 * Q ** 2
+            bytes_ = 3 * fp * Q ** 2 * E + 4 * D1 ** 2 * E + 2 * fp * n
+        else:
+            flops_e = 2 * (2 * Q * D1 ** 2 + 2 * Q ** 2 * D1) + Q ** 2
+            bytes_ = fp * Q ** 2 * E + 4 * D1 ** 2 * E + 2 * fp * n
+        return flops_e * E, bytes_
     if kind == "diffusion":
         flops_e = 2 * (4 * Q * D1 ** 3 + 6 * Q ** 2 * D1 ** 2 + 6 * Q ** 3 * D1) + 15 * Q ** 3
         bytes_ = 6 * fp * Q ** 3 * E + 4 * D1 ** 3 * E + 2 * fp * n
@@ -387,6 +395,74 @@ def run_batch(args):
     return 0
 
 
+# The 2D Example-1 workload of the paper's GPU table: about 1.3M DOFs for
+# p = 1, 2, 4, 8 on an N x N quadrilateral mesh ((N p + 1)^2 DOFs).
+PAPER2D_N = {1: 1140, 2: 570, 4: 285, 8: 143}
+# Seconds for 200 CG iterations on one GV100 in the paper's table (context
+# only: another GPU, another code): best GPU backend and the plain CUDA one.
+PAPER2D_GV100_S = {1: (0.19, 0.36), 2: (0.15, 0.26), 4: (0.12, 0.17), 8: (0.12, 0.15)}
+
+
+def run_paper2d(args):
+    """2D Poisson (Example 1): -Laplace u = 1 on the unit square, perturbed
+    (0.15h) quadrilateral mesh, homogeneous Dirichlet conditions, partial
+    assembly, 200 CG iterations, p in {1, 2, 4, 8} at about 1.3M DOFs. One
+    JSON line per order: 200 iterations of plain CG and of Jacobi-PCG (FP64
+    and FP32 vectors), and the FP64 / FP32 / double-float apply."""
+    import torch
+    from paper_1911_09220_gb300 import build as fbuild
+    fbuild.build()
+    import paper_1911_09220_gb300 as F
+    from fem_inputs import quad_lattice
+    orders = [int(v) for v in args.orders.split(",") if int(v) in PAPER2D_N] if args.orders != "1,2,3,4,5,6,7,8" \
+        else [1, 2, 4, 8]
+    for p in orders:
+        N = PAPER2D_N[p]
+        q = p + 2
+        c, qd = quad_lattice(N, 0.15, seed=60 + p)
+        space = F.Space(F.Mesh2D(c, qd), p)
+        n, E = space.ndof, space.ne
+        form = F.Form(space, "diffusion", q)
+        form.set_essential(torch.as_tensor(space.boundary_dofs(), device="cuda"))
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        form.rhs(torch.ones((E, form.nq), dtype=torch.float64, device="cuda"), b)
+        bc = torch.empty_like(b)
+        form.lift_rhs(b, torch.zeros_like(b), bc)
+        out = {"workload": f"2D Poisson Ex1, p={p}, q={q}, {N}^2 quads perturbed 0.15h, 200 CG iterations",
+               "p": p, "q1d": q, "N": N, "ndof": n, "elements": E,
+               "paper_gv100_s": {"best_gpu": PAPER2D_GV100_S[p][0], "cuda": PAPER2D_GV100_S[p][1]}}
+        for name, prec, pc in (("cg_f64", "f64", "none"), ("pcg_f64", "f64", "jacobi"),
+                               ("pcg_df64", "df64", "jacobi")):
+            ts = []
+            for rep in range(3):
+                u = torch.zeros_like(b)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info = form.solve(bc, u, rtol=1e-30, maxit=200, precision=prec, precond=pc, raise_on_error=False,
+                                  check_every=50)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            out[name] = {"seconds": min(ts), "iterations": info["iterations"], "relres": info["relres"]}
+        x = torch.as_tensor(np.linspace(-1.0, 1.0, n), device="cuda")
+        y = torch.empty_like(x)
+        flops, _ = alg_counts(p, q, E, n, dim=2)
+        _, bytes32 = alg_counts(p, q, E, n, fp=4, dim=2)
+        t64 = time_events(lambda: form.apply(x, y), args.steps, 3)
+        x32, y32 = x.float(), torch.empty(n, dtype=torch.float32, device="cuda")
+        t32 = time_events(lambda: form.apply(x32, y32), args.steps, 3)
+        ye = torch.empty((E, (p + 1) ** 2), dtype=torch.float64, device="cuda")
+        te64 = time_events(lambda: form.apply_element(x, ye), args.steps, 3)
+        tedf = time_events(lambda: form.apply_element(x, ye, arith="df64"), args.steps, 3)
+        out["apply"] = {"f64_ms": t64, "f64_gdofs": n / t64 * 1e-6, "f64_element_ms": te64,
+                        "f64_element_frac_fp64_peak": flops / te64 * 1e-9 / FP64_PEAK_TFLOPS,
+                        "df64_element_ms": tedf, "f32_ms": t32, "f32_gdofs": n / t32 * 1e-6,
+                        "f32_alg_gbs": bytes32 / t32 * 1e-6}
+        print(json.dumps(out), flush=True)
+        del form, space, x, y, x32, y32, ye, b, bc
+        torch.cuda.empty_cache()
+    return 0
+
+
 def run_grad(args):
     """Differentiation workload: 64^3 hexes, 0.1h, p = 2, kappa = 0.01 + rho^3,
     rho ~ U[0.2, 1], f = 1, homogeneous Dirichlet: compliance solve and the
@@ -438,7 +514,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--solve-maxit", type=int, default=20000)
-    ap.add_argument("--workload", default="apply", choices=["apply", "sweep", "batch", "grad"])
+    ap.add_argument("--workload", default="apply", choices=["apply", "sweep", "batch", "grad", "paper2d"])
     ap.add_argument("--sweep-size", default="4e6", choices=["4e6", "2e7"])
     ap.add_argument("--orders", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--nprob", type=int, default=256)
@@ -451,6 +527,8 @@ def main():
         return run_sweep(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "paper2d":
+        return run_paper2d(args)
     if args.workload == "grad":
         return run_grad(args)
 

@@ -80,6 +80,9 @@ enum { FEM_F64 = 0, FEM_F32 = 1, FEM_DF64 = 2 };
  * residual whenever it has dropped by inner_rtol, without restarting the
  * search direction). */
 enum { FEM_SOLVE_F64 = 0, FEM_SOLVE_MIXED = 1, FEM_SOLVE_DF64 = 2, FEM_SOLVE_MIXED_RU = 3 };
+/* Preconditioner of fem_solve: Jacobi (assembled diagonal, Sec. 5.2) or none
+ * (plain CG, the iteration of the paper's Example 1 timings, Sec. 5.3). */
+enum { FEM_PC_JACOBI = 0, FEM_PC_NONE = 1 };
 
 typedef struct fem_mesh fem_mesh;
 typedef struct fem_space fem_space;
@@ -102,13 +105,25 @@ int fem_supported(int p, int q1d);
  * vertex is referenced by no element. */
 fem_status fem_mesh_create(const double* coords_host, int64_t nv,
                            const int32_t* hex_host, int64_t ne, fem_mesh** out);
+/* Quadrilateral (2D) mesh, the d = 2 case of the same definitions:
+ * coords_host [nv][2] float64; quad_host [ne][4] int32, local vertex order
+ * 0:(0,0) 1:(1,0) 2:(1,1) 3:(0,1) (counter-clockwise on [0,1]^2, bilinear
+ * map). Everything built on it takes the 2D shapes stated below ((p+1)^2
+ * local DOFs, q1d^2 points, [..][2] coordinates). Not accepted by
+ * fem_batch_create (FEM_EUNSUPPORTED). Same ownership and errors as
+ * fem_mesh_create. */
+fem_status fem_mesh2d_create(const double* coords_host, int64_t nv,
+                             const int32_t* quad_host, int64_t ne, fem_mesh** out);
 void fem_mesh_destroy(fem_mesh* mesh);
 
 /* ---- H1 space of order p (Sec. 3.4 "Finite Element Spaces") ----------------
  * Builds the global numbering, the element->DOF table e2l [ne][(p+1)^3]
  * (lexicographic local order, x fastest), its inverse (CSR, entries sorted by
  * element then local index: the fixed summation order of the scatter) and the
- * boundary DOFs (DOFs on faces with exactly one adjacent element). Host-side
+ * boundary DOFs (DOFs on faces with exactly one adjacent element). On a 2D
+ * mesh: vertices, then edges by first appearance (local edges (0,1), (1,2),
+ * (3,2), (0,3), DOFs from the lower to the higher global vertex), then
+ * interiors; e2l [ne][(p+1)^2]; boundary = edges with one element. Host-side
  * setup, synchronous. Errors: FEM_EINVAL (p < 1), FEM_EUNSUPPORTED (p > 8 or
  * ne (p+1)^3 >= 2^31). */
 fem_status fem_space_create(const fem_mesh* mesh, int p, fem_space** out);
@@ -120,7 +135,8 @@ fem_status fem_space_boundary_dofs(const fem_space* space, int32_t* out_host);
 /* The element->DOF table: out_host [ne][(p+1)^3] int32. */
 fem_status fem_space_element_dofs(const fem_space* space, int32_t* out_host);
 /* Physical location of every DOF (the trilinear map of its first element at
- * the GLL node): out [ndof][3] float64 device. Asynchronous on stream. */
+ * the GLL node): out [ndof][3] float64 device ([ndof][2] in 2D).
+ * Asynchronous on stream. */
 fem_status fem_space_dof_coords(const fem_space* space, double* out, void* stream);
 
 /* ---- partial-assembly setup (Sec. 4.3: setup phase "evaluates and stores D")
@@ -132,7 +148,8 @@ fem_status fem_space_dof_coords(const fem_space* space, double* out, void* strea
  * coef: device float64 [ne] per-element coefficient, or NULL for 1.
  * Layout in HBM: [ne][q1d^3][6] (diffusion, the six components of a point
  * contiguous) or [ne][q1d^3] (mass), float64, point index lexicographic
- * (x fastest). Synchronises `stream` to read the
+ * (x fastest). 2D: [ne][q1d^2][3] (components 00, 01, 11) or [ne][q1d^2].
+ * Synchronises `stream` to read the
  * det J check. Errors: FEM_EINVERTED if any det J <= 0, FEM_EUNSUPPORTED if
  * (p, q1d) is not compiled. */
 fem_status fem_form_create(const fem_space* space, int kind, int q1d,
@@ -191,12 +208,12 @@ fem_status fem_assemble_diagonal(const fem_form* form, double* diag,
                                  int constrained, void* stream);
 
 /* ---- load vector (Sec. 2, b_i = int f phi_i) -------------------------------
- * fq: device float64 [ne][q1d^3], source values at the form's quadrature
+ * fq: device float64 [ne][q1d^3] ([ne][q1d^2] in 2D), source values at the form's quadrature
  * points; b: device float64 [ndof], overwritten with
  * b_i = sum_e sum_q w_q det J_q fq(e,q) phi_i(q). */
 fem_status fem_rhs(const fem_form* form, const double* fq, double* b, void* stream);
 /* Physical coordinates of the quadrature points: xq device float64
- * [ne][q1d^3][3]. */
+ * [ne][q1d^3][3] ([ne][q1d^2][2] in 2D). */
 fem_status fem_qpoint_coords(const fem_form* form, double* xq, void* stream);
 
 /* ---- Jacobi-preconditioned CG (Sec. 5.2, CGSolver with SetRelTol /
@@ -209,6 +226,7 @@ fem_status fem_qpoint_coords(const fem_form* form, double* xq, void* stream);
  * the recursive residual drifted). precision FEM_SOLVE_MIXED runs FP32 inner
  * Jacobi-PCG to inner_rtol on FP32 copies of D, inside FP64 iterative
  * refinement (FP64 outer residual, norms and updates).
+ * precond FEM_PC_NONE replaces the Jacobi diagonal by ones.
  * Synchronises `stream`. Errors: FEM_ENOCONV, FEM_EBREAKDOWN. */
 typedef struct {
   double rtol;          /* relative tolerance, e.g. 1e-10 */
@@ -219,6 +237,7 @@ typedef struct {
   int max_outer;        /* mixed: cap on refinement steps */
   int check_every;      /* iterations per CUDA-graph launch between host polls */
   int use_graph;        /* capture check_every iterations in a CUDA graph */
+  int precond;          /* FEM_PC_JACOBI (default) or FEM_PC_NONE (plain CG) */
 } fem_solve_opts;
 typedef struct {
   int iterations;       /* total CG iterations (inner iterations for mixed) */

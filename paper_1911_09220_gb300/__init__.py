@@ -19,7 +19,7 @@ from . import _binding as B
 from ._binding import (FemError, FEM_DIFFUSION, FEM_MASS, FEM_F64, FEM_F32, FEM_DF64, FEM_SOLVE_F64,
                        FEM_SOLVE_MIXED, FEM_SOLVE_DF64, FEM_SOLVE_MIXED_RU)
 
-__all__ = ["Mesh", "Space", "Form", "Batch", "FemError", "lib", "supported", "version"]
+__all__ = ["Mesh", "Mesh2D", "Space", "Form", "Batch", "FemError", "lib", "supported", "version"]
 
 
 def lib():
@@ -79,11 +79,30 @@ class Mesh:
                                   self.hexes.shape[0], C.byref(h)))
         self._h = h
         self.nv, self.ne = self.coords.shape[0], self.hexes.shape[0]
+        self.dim = 3
 
     def __del__(self):
         if getattr(self, "_h", None) and B._lib is not None:
             B._lib.fem_mesh_destroy(self._h)
             self._h = None
+
+
+class Mesh2D(Mesh):
+    """Unstructured quadrilateral mesh: vertex coordinates [nv,2] and 4-vertex
+    tuples, counter-clockwise from the local (0,0) corner (Sec. 3.1, d = 2)."""
+
+    def __init__(self, coords, quads):
+        L = B.lib()
+        self.coords = np.ascontiguousarray(coords, dtype=np.float64)
+        self.hexes = np.ascontiguousarray(quads, dtype=np.int32)
+        if self.coords.ndim != 2 or self.coords.shape[1] != 2 or self.hexes.ndim != 2 or self.hexes.shape[1] != 4:
+            raise ValueError("coords must be [nv,2] and quads [ne,4]")
+        h = C.c_void_p()
+        B.check(L.fem_mesh2d_create(self.coords.ctypes.data, self.coords.shape[0], self.hexes.ctypes.data,
+                                    self.hexes.shape[0], C.byref(h)))
+        self._h = h
+        self.nv, self.ne = self.coords.shape[0], self.hexes.shape[0]
+        self.dim = 2
 
 
 class Space:
@@ -100,6 +119,7 @@ class Space:
         pp = C.c_int()
         B.check(L.fem_space_info(h, C.byref(ndof), C.byref(nbdr), C.byref(ne), C.byref(pp)))
         self.ndof, self.nbdr, self.ne, self.p = ndof.value, nbdr.value, ne.value, pp.value
+        self.dim = mesh.dim
 
     def boundary_dofs(self):
         out = np.empty(self.nbdr, dtype=np.int32)
@@ -107,14 +127,14 @@ class Space:
         return out
 
     def element_dofs(self):
-        out = np.empty((self.ne, (self.p + 1) ** 3), dtype=np.int32)
+        out = np.empty((self.ne, (self.p + 1) ** self.dim), dtype=np.int32)
         B.check(B.lib().fem_space_element_dofs(self._h, out.ctypes.data))
         return out
 
     def dof_coords(self, out=None, stream=None):
         import torch
         if out is None:
-            out = torch.empty((self.ndof, 3), dtype=torch.float64, device="cuda")
+            out = torch.empty((self.ndof, self.dim), dtype=torch.float64, device="cuda")
         B.check(B.lib().fem_space_dof_coords(self._h, _ptr(out, torch.float64, "out"), _stream(stream)))
         return out
 
@@ -134,7 +154,7 @@ class Form:
         self.space = space
         self.kind = {"diffusion": FEM_DIFFUSION, "mass": FEM_MASS}[kind] if isinstance(kind, str) else int(kind)
         self.q1d = int(q1d) if q1d is not None else space.p + 2
-        self.nq = self.q1d ** 3
+        self.nq = self.q1d ** space.dim
         self._coef = None if coef is None else coef.contiguous()
         h = C.c_void_p()
         B.check(L.fem_form_create(space._h, self.kind, self.q1d, _ptr(self._coef, torch.float64, "coef"),
@@ -201,7 +221,7 @@ class Form:
     def qpoint_coords(self, out=None, stream=None):
         import torch
         if out is None:
-            out = torch.empty((self.space.ne, self.nq, 3), dtype=torch.float64, device="cuda")
+            out = torch.empty((self.space.ne, self.nq, self.space.dim), dtype=torch.float64, device="cuda")
         B.check(B.lib().fem_qpoint_coords(self._h, _ptr(out, torch.float64, "out"), _stream(stream)))
         return out
 
@@ -212,12 +232,12 @@ class Form:
         return bc
 
     def solve(self, b, x, rtol=1e-10, maxit=20000, precision="f64", inner_rtol=None, max_outer=30,
-              check_every=16, use_graph=True, stream=None, raise_on_error=True):
+              check_every=16, use_graph=True, stream=None, raise_on_error=True, precond="jacobi"):
         """Jacobi-PCG on the constrained operator. precision: "f64", "df64"
         (FP64 CG, double-float operator), "mixed" (FP32 inner CG restarted in
         FP64 refinement; inner_rtol default 1e-4) or "mixed_ru" (FP32 CG with
         FP64 reliable updates; inner_rtol = residual drop between updates,
-        default 1e-2)."""
+        default 1e-2). precond: "jacobi" or "none" (plain CG)."""
         import torch
         o = B.SolveOpts()
         B.lib().fem_solve_opts_default(C.byref(o))
@@ -227,6 +247,7 @@ class Form:
         o.precision = {"f64": FEM_SOLVE_F64, "mixed": FEM_SOLVE_MIXED, "df64": FEM_SOLVE_DF64,
                        "mixed_ru": FEM_SOLVE_MIXED_RU}[precision]
         o.check_every, o.use_graph = check_every, int(bool(use_graph))
+        o.precond = {"jacobi": 0, "none": 1}[precond]
         info = B.SolveInfo()
         st = B.lib().fem_solve(self._h, _ptr(b, torch.float64, "b"), _ptr(x, torch.float64, "x"), C.byref(o),
                                C.byref(info), _stream(stream))

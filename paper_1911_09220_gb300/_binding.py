@@ -31,7 +31,7 @@ class FemError(RuntimeError):
 class SolveOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("maxit", C.c_int), ("precision", C.c_int),
                 ("inner_rtol", C.c_double), ("max_outer", C.c_int), ("check_every", C.c_int),
-                ("use_graph", C.c_int)]
+                ("use_graph", C.c_int), ("precond", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -49,6 +49,7 @@ SIGNATURES = {
     "fem_last_error": (C.c_char_p, []),
     "fem_supported": (I, [I, I]),
     "fem_mesh_create": (I, [P, I64, P, I64, C.POINTER(P)]),
+    "fem_mesh2d_create": (I, [P, I64, P, I64, C.POINTER(P)]),
     "fem_mesh_destroy": (None, [P]),
     "fem_space_create": (I, [P, I, C.POINTER(P)]),
     "fem_space_destroy": (None, [P]),

@@ -25,8 +25,22 @@ extern "C" const char* fem_last_error(void) { return g_last_error.c_str(); }
 extern "C" int fem_supported(int p, int q1d) { return fem_kernels_supported(p, q1d); }
 
 // ----------------------------------------------------------------- mesh ----
+static fem_status mesh_create(const double* coords_host, int64_t nv, const int32_t* hex_host, int64_t ne,
+                              int dim, fem_mesh** out);
+
 extern "C" fem_status fem_mesh_create(const double* coords_host, int64_t nv,
                                       const int32_t* hex_host, int64_t ne, fem_mesh** out) {
+  return mesh_create(coords_host, nv, hex_host, ne, 3, out);
+}
+
+extern "C" fem_status fem_mesh2d_create(const double* coords_host, int64_t nv, const int32_t* quad_host,
+                                        int64_t ne, fem_mesh** out) {
+  return mesh_create(coords_host, nv, quad_host, ne, 2, out);
+}
+
+static fem_status mesh_create(const double* coords_host, int64_t nv, const int32_t* hex_host, int64_t ne,
+                              int dim, fem_mesh** out) {
+  const int nvpe = dim == 3 ? 8 : 4;
   if (!out) return fem_fail(FEM_EINVAL, "fem_mesh_create: out is NULL");
   *out = nullptr;
   if (!coords_host || !hex_host || nv <= 0 || ne <= 0)
@@ -36,8 +50,8 @@ extern "C" fem_status fem_mesh_create(const double* coords_host, int64_t nv,
     return fem_fail(FEM_EUNSUPPORTED, "fem_mesh_create: mesh too large for int32 indices");
   std::vector<uint8_t> used(nv, 0);
   for (int64_t e = 0; e < ne; ++e) {
-    const int32_t* h = hex_host + 8 * e;
-    for (int a = 0; a < 8; ++a) {
+    const int32_t* h = hex_host + nvpe * e;
+    for (int a = 0; a < nvpe; ++a) {
       if (h[a] < 0 || h[a] >= nv)
         return fem_fail(FEM_EINVAL, "fem_mesh_create: element %lld vertex %d index %d out of range",
                         (long long)e, a, h[a]);
@@ -52,17 +66,19 @@ extern "C" fem_status fem_mesh_create(const double* coords_host, int64_t nv,
     if (!used[v])
       return fem_fail(FEM_EINVAL, "fem_mesh_create: vertex %lld belongs to no element", (long long)v);
   fem_mesh* m = new fem_mesh();
+  m->dim = dim;
+  m->nvpe = nvpe;
   m->nv = nv;
   m->ne = ne;
-  m->coords.assign(coords_host, coords_host + 3 * nv);
-  m->hex.assign(hex_host, hex_host + 8 * ne);
-  fem_status st = dev_alloc(&m->d_coords, 3 * nv);
-  if (st == FEM_OK) st = dev_alloc(&m->d_hex, 8 * ne);
+  m->coords.assign(coords_host, coords_host + dim * nv);
+  m->hex.assign(hex_host, hex_host + nvpe * ne);
+  fem_status st = dev_alloc(&m->d_coords, dim * nv);
+  if (st == FEM_OK) st = dev_alloc(&m->d_hex, nvpe * ne);
   if (st == FEM_OK &&
-      cudaMemcpy(m->d_coords, coords_host, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice) != cudaSuccess)
+      cudaMemcpy(m->d_coords, coords_host, sizeof(double) * dim * nv, cudaMemcpyHostToDevice) != cudaSuccess)
     st = fem_fail(FEM_ECUDA, "fem_mesh_create: copy of coordinates failed");
   if (st == FEM_OK &&
-      cudaMemcpy(m->d_hex, hex_host, sizeof(int32_t) * 8 * ne, cudaMemcpyHostToDevice) != cudaSuccess)
+      cudaMemcpy(m->d_hex, hex_host, sizeof(int32_t) * nvpe * ne, cudaMemcpyHostToDevice) != cudaSuccess)
     st = fem_fail(FEM_ECUDA, "fem_mesh_create: copy of connectivity failed");
   if (st != FEM_OK) {
     fem_mesh_destroy(m);
@@ -123,11 +139,15 @@ int64_t first_appearance_ids(std::vector<K>& keys, std::vector<int32_t>& id_of_s
 
 }  // namespace
 
+static fem_status space_finish(fem_space* sp, fem_space** out);
+static fem_status space_create_2d(const fem_mesh* mesh, int p, fem_space** out);
+
 extern "C" fem_status fem_space_create(const fem_mesh* mesh, int p, fem_space** out) {
   if (!out || !mesh) return fem_fail(FEM_EINVAL, "fem_space_create: NULL argument");
   *out = nullptr;
   if (p < 1) return fem_fail(FEM_EINVAL, "fem_space_create: p must be >= 1 (got %d)", p);
   if (p > 8) return fem_fail(FEM_EUNSUPPORTED, "fem_space_create: p = %d > 8 not compiled", p);
+  if (mesh->dim == 2) return space_create_2d(mesh, p, out);
   const int64_t ne = mesh->ne, nv = mesh->nv;
   const int D1 = p + 1, nd = D1 * D1 * D1;
   if ((double)ne * nd >= 2147483647.0)
@@ -278,6 +298,96 @@ extern "C" fem_status fem_space_create(const fem_mesh* mesh, int p, fem_space** 
       if (mark[i]) sp->bdr.push_back((int32_t)i);
   }
 
+  return space_finish(sp, out);
+}
+
+// Quadrilaterals: vertices, then edges by first appearance (local edges
+// (0,1),(1,2),(3,2),(0,3), DOFs from the lower to the higher global
+// vertex), then element interiors (lexicographic); boundary DOFs lie on
+// edges with one adjacent element.
+static fem_status space_create_2d(const fem_mesh* mesh, int p, fem_space** out) {
+  static const int kEdge2[4][2] = {{0, 1}, {1, 2}, {3, 2}, {0, 3}};
+  static const int kCorner2[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+  const int64_t ne = mesh->ne, nv = mesh->nv;
+  const int D1 = p + 1, nd = D1 * D1;
+  if ((double)ne * nd >= 2147483647.0)
+    return fem_fail(FEM_EUNSUPPORTED, "fem_space_create: ne*(p+1)^2 exceeds int32");
+  const int32_t* q4 = mesh->hex.data();
+  std::vector<Key2> ek((size_t)ne * 4);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int le = 0; le < 4; ++le) {
+      uint64_t a = (uint64_t)q4[4 * e + kEdge2[le][0]], b = (uint64_t)q4[4 * e + kEdge2[le][1]];
+      if (a > b) std::swap(a, b);
+      ek[e * 4 + le] = Key2{a * (uint64_t)nv + b, (uint32_t)(e * 4 + le)};
+    }
+  std::vector<int32_t> edge_id;
+  const int64_t n_edges = first_appearance_ids(
+      ek, edge_id, [](const Key2& x, const Key2& y) { return x.a == y.a; },
+      [](const Key2& x, const Key2& y) { return x.a < y.a; });
+  const int64_t pm1 = p - 1;
+  const int64_t off_e = nv, off_i = nv + n_edges * pm1, ndof = off_i + ne * pm1 * pm1;
+  if (ndof >= (int64_t)INT32_MAX) return fem_fail(FEM_EUNSUPPORTED, "fem_space_create: ndof exceeds int32");
+  fem_space* sp = new fem_space();
+  sp->mesh = mesh;
+  sp->p = p;
+  sp->D1 = D1;
+  sp->nd = nd;
+  sp->ne = ne;
+  sp->ndof = ndof;
+  sp->n_edges = n_edges;
+  sp->e2l.assign((size_t)ne * nd, -1);
+  for (int64_t e = 0; e < ne; ++e) {
+    const int32_t* h = q4 + 4 * e;
+    int32_t* row = sp->e2l.data() + (size_t)e * nd;
+    for (int k = 0; k < nd; ++k) {
+      const int L[2] = {k % D1, k / D1};
+      const int onb = (L[0] == 0 || L[0] == p) + (L[1] == 0 || L[1] == p);
+      if (onb == 2) {
+        for (int v = 0; v < 4; ++v)
+          if (kCorner2[v][0] * p == L[0] && kCorner2[v][1] * p == L[1]) row[k] = h[v];
+      } else if (onb == 1) {
+        for (int le = 0; le < 4; ++le) {
+          const int* A = kCorner2[kEdge2[le][0]];
+          const int* B = kCorner2[kEdge2[le][1]];
+          bool on = true;
+          for (int d = 0; d < 2; ++d)
+            if (A[d] == B[d] && A[d] * p != L[d]) on = false;
+          if (!on) continue;
+          int a = kEdge2[le][0], b = kEdge2[le][1];
+          if (h[a] > h[b]) std::swap(a, b);
+          const int dist = std::abs(L[0] - kCorner2[a][0] * p) + std::abs(L[1] - kCorner2[a][1] * p);
+          row[k] = (int32_t)(off_e + (int64_t)edge_id[e * 4 + le] * pm1 + (dist - 1));
+        }
+      } else {
+        row[k] = (int32_t)(off_i + e * pm1 * pm1 + (L[0] - 1) + pm1 * (L[1] - 1));
+      }
+    }
+  }
+  std::vector<int32_t> count(n_edges, 0);
+  for (size_t i = 0; i < edge_id.size(); ++i) count[edge_id[i]]++;
+  std::vector<uint8_t> mark(ndof, 0);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int le = 0; le < 4; ++le) {
+      if (count[edge_id[e * 4 + le]] != 1) continue;
+      const int* A = kCorner2[kEdge2[le][0]];
+      const int* B = kCorner2[kEdge2[le][1]];
+      for (int k = 0; k < nd; ++k) {
+        const int L[2] = {k % D1, k / D1};
+        bool on = true;
+        for (int d = 0; d < 2; ++d)
+          if (A[d] == B[d] && A[d] * p != L[d]) on = false;
+        if (on) mark[sp->e2l[(size_t)e * nd + k]] = 1;
+      }
+    }
+  for (int64_t i = 0; i < ndof; ++i)
+    if (mark[i]) sp->bdr.push_back((int32_t)i);
+  return space_finish(sp, out);
+}
+
+// Inverse map, GLL nodes and device copies (shared by 2D and 3D).
+static fem_status space_finish(fem_space* sp, fem_space** out) {
+  const int64_t ndof = sp->ndof, ne = sp->ne;
+  const int nd = sp->nd, p = sp->p;
   // inverse map: for each DOF, the E-vector slots e*nd+k holding it, in (e,k) order
   std::vector<int32_t> off(ndof + 1, 0), idx((size_t)ne * nd);
   for (size_t s = 0; s < sp->e2l.size(); ++s) off[sp->e2l[s] + 1]++;
@@ -359,13 +469,15 @@ extern "C" fem_status fem_form_create(const fem_space* sp, int kind, int q1d, co
   if (!fem_kernels_supported(sp->p, q1d))
     return fem_fail(FEM_EUNSUPPORTED, "fem_form_create: (p=%d, q1d=%d) not compiled", sp->p, q1d);
   FEM_TRY(fem_apply_tables_init());
+  if (sp->mesh->dim == 2) FEM_TRY(fem_2d_tables_init());
   cudaStream_t s = (cudaStream_t)stream;
   fem_form* f = new fem_form();
   f->space = sp;
   f->kind = kind;
   f->q1d = q1d;
-  f->nq = q1d * q1d * q1d;
-  f->ncomp = (kind == FEM_DIFFUSION) ? 6 : 1;
+  const int dim = sp->mesh->dim;
+  f->nq = dim == 3 ? q1d * q1d * q1d : q1d * q1d;
+  f->ncomp = (kind == FEM_DIFFUSION) ? (dim == 3 ? 6 : 3) : 1;
   std::vector<double> pts, wts, B, G;
   fem_gauss_rule(q1d, pts, wts);
   fem_lagrange_tables(sp->nodes, pts, B, G);

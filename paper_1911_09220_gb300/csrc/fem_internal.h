@@ -46,9 +46,11 @@ void dev_free(T*& p) {
 
 // ---------------------------------------------------------------- handles ---
 struct fem_mesh {
+  int dim = 3;                  // 3: hexahedra, 2: quadrilaterals
+  int nvpe = 8;                 // vertices per element (8 or 4)
   int64_t nv = 0, ne = 0;
-  std::vector<double> coords;   // [nv][3]
-  std::vector<int32_t> hex;     // [ne][8]
+  std::vector<double> coords;   // [nv][dim]
+  std::vector<int32_t> hex;     // [ne][nvpe] element vertex tuples
   double* d_coords = nullptr;
   int32_t* d_hex = nullptr;
 };
@@ -132,3 +134,13 @@ int fem_scatter_blocks(int64_t ndof);
 // unit): filled once per device from form / batch creation.
 fem_status fem_apply_tables_init();
 fem_status fem_batch_tables_init();
+fem_status fem_2d_tables_init();
+// Quadrilateral (2D) counterparts, dispatched on mesh->dim == 2 (k_2d.cu).
+fem_status fem_launch_setup_2d(const fem_form* f, cudaStream_t s);
+fem_status fem_launch_qpoint_coords_2d(const fem_form* f, double* xq, cudaStream_t s);
+fem_status fem_launch_dof_coords_2d(const fem_space* sp, double* out, cudaStream_t s);
+fem_status fem_launch_apply_element_2d(const fem_form* f, int dtype, const void* x, void* ye, cudaStream_t s,
+                                       const int* skip);
+fem_status fem_launch_diag_element_2d(const fem_form* f, double* ye, cudaStream_t s);
+fem_status fem_launch_rhs_element_2d(const fem_form* f, const double* fq, double* ye, cudaStream_t s);
+fem_status fem_launch_grad_2d(const fem_form* f, const double* u, double* g, cudaStream_t s);

@@ -173,6 +173,7 @@ fem_status fem_form_ensure_df64(const fem_form* fc, cudaStream_t s) {
 
 fem_status fem_launch_apply_element(const fem_form* f, int dtype, const void* x, void* ye, cudaStream_t s,
                                     const int* skip) {
+  if (f->space->mesh->dim == 2) return fem_launch_apply_element_2d(f, dtype, x, ye, s, skip);
   const int p = f->space->p, q = f->q1d;
   if (dtype == FEM_F64) {
 #define X(P, Q)                                                                                            \

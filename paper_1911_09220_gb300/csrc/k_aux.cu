@@ -304,6 +304,7 @@ fem_status launch_grad(const fem_form* f, const double* u, double* g, cudaStream
 }  // namespace
 
 fem_status fem_launch_diag_element(const fem_form* f, double* ye, cudaStream_t s) {
+  if (f->space->mesh->dim == 2) return fem_launch_diag_element_2d(f, ye, s);
   const int p = f->space->p, q = f->q1d;
 #define X(P, Q) \
   if (p == P && q == Q) return launch_diag<P, Q>(f, ye, s);
@@ -313,6 +314,7 @@ fem_status fem_launch_diag_element(const fem_form* f, double* ye, cudaStream_t s
 }
 
 fem_status fem_launch_rhs_element(const fem_form* f, const double* fq, double* ye, cudaStream_t s) {
+  if (f->space->mesh->dim == 2) return fem_launch_rhs_element_2d(f, fq, ye, s);
   const int p = f->space->p, q = f->q1d;
 #define X(P, Q) \
   if (p == P && q == Q) return launch_rhs<P, Q>(f, fq, ye, s);
@@ -322,6 +324,7 @@ fem_status fem_launch_rhs_element(const fem_form* f, const double* fq, double* y
 }
 
 fem_status fem_launch_grad(const fem_form* f, const double* u, double* g, cudaStream_t s) {
+  if (f->space->mesh->dim == 2) return fem_launch_grad_2d(f, u, g, s);
   const int p = f->space->p, q = f->q1d;
 #define X(P, Q) \
   if (p == P && q == Q) return launch_grad<P, Q>(f, u, g, s);

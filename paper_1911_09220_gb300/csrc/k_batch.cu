@@ -645,6 +645,10 @@ extern "C" fem_status fem_batch_create(const fem_form* const* forms, int nprob, 
       return fem_fail(FEM_EINVAL, "fem_batch_create: form %d is NULL", i);
     }
     const fem_space* sp = f->space;
+    if (sp->mesh->dim != 3) {
+      delete b;
+      return fem_fail(FEM_EUNSUPPORTED, "fem_batch_create: form %d is on a 2D mesh; batches hold hexahedra", i);
+    }
     if (sp->p > 6) {
       delete b;
       return fem_fail(FEM_EUNSUPPORTED, "fem_batch_create: form %d has p = %d; batches hold p <= 6", i, sp->p);
@@ -795,6 +799,7 @@ extern "C" fem_status fem_batch_solve(fem_batch* b, const double* Bv, double* Xv
   fem_solve_opts_default(&o);
   if (opts) o = *opts;
   if (!(o.rtol > 0) || o.maxit <= 0) return fem_fail(FEM_EINVAL, "fem_batch_solve: rtol > 0 and maxit > 0 required");
+  if (o.precond != FEM_PC_JACOBI) return fem_fail(FEM_EUNSUPPORTED, "fem_batch_solve: Jacobi preconditioner only");
   const bool mixed = o.precision == FEM_SOLVE_MIXED;
   cudaStream_t s = (cudaStream_t)stream;
   for (int i = 0; i < b->nprob; ++i)

@@ -161,6 +161,7 @@ __global__ void k_mark_ess(int64_t n, int64_t ndof, const int32_t* __restrict__ 
 
 fem_status fem_launch_setup(const fem_form* f, cudaStream_t s) {
   const fem_space* sp = f->space;
+  if (sp->mesh->dim == 2) return fem_launch_setup_2d(f, s);
   const int64_t total = sp->ne * f->nq;
   const int grid = grid_for(total, 256);
   k_setup<<<grid, 256, 0, s>>>(sp->ne, f->q1d, f->kind, sp->mesh->d_coords, sp->mesh->d_hex, f->d_qpts,
@@ -171,6 +172,7 @@ fem_status fem_launch_setup(const fem_form* f, cudaStream_t s) {
 
 fem_status fem_launch_qpoint_coords(const fem_form* f, double* xq, cudaStream_t s) {
   const fem_space* sp = f->space;
+  if (sp->mesh->dim == 2) return fem_launch_qpoint_coords_2d(f, xq, s);
   const int64_t total = sp->ne * f->nq;
   k_qpoint_coords<<<grid_for(total, 256), 256, 0, s>>>(sp->ne, f->q1d, sp->mesh->d_coords, sp->mesh->d_hex,
                                                        f->d_qpts, xq);
@@ -179,6 +181,7 @@ fem_status fem_launch_qpoint_coords(const fem_form* f, double* xq, cudaStream_t 
 }
 
 fem_status fem_launch_dof_coords(const fem_space* sp, double* out, cudaStream_t s) {
+  if (sp->mesh->dim == 2) return fem_launch_dof_coords_2d(sp, out, s);
   k_dof_coords<<<grid_for(sp->ndof, 256), 256, 0, s>>>(sp->ndof, sp->D1, sp->mesh->d_coords, sp->mesh->d_hex,
                                                        sp->d_l2e_off, sp->d_l2e_idx, sp->d_nodes, out);
   FEM_LAUNCHED();

@@ -264,6 +264,11 @@ __global__ void k_axpy_scaled(int64_t n, const double* __restrict__ rr, const fl
     x[i] += s * (double)d[i];
 }
 
+__global__ void k_fill(int64_t n, double v, double* __restrict__ a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
 __global__ void k_cast_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
@@ -439,6 +444,7 @@ extern "C" void fem_solve_opts_default(fem_solve_opts* o) {
   o->max_outer = 30;
   o->check_every = 16;
   o->use_graph = 1;
+  o->precond = FEM_PC_JACOBI;
 }
 
 extern "C" fem_status fem_solve(const fem_form* fc, const double* b, double* xio, const fem_solve_opts* opts,
@@ -452,6 +458,8 @@ extern "C" fem_status fem_solve(const fem_form* fc, const double* b, double* xio
   if (o.precision != FEM_SOLVE_F64 && o.precision != FEM_SOLVE_MIXED && o.precision != FEM_SOLVE_DF64 &&
       o.precision != FEM_SOLVE_MIXED_RU)
     return fem_fail(FEM_EINVAL, "fem_solve: unknown precision %d", o.precision);
+  if (o.precond != FEM_PC_JACOBI && o.precond != FEM_PC_NONE)
+    return fem_fail(FEM_EINVAL, "fem_solve: unknown preconditioner %d", o.precond);
   fem_form* f = const_cast<fem_form*>(fc);
   cudaStream_t s = (cudaStream_t)stream;
   const bool ru = o.precision == FEM_SOLVE_MIXED_RU;
@@ -463,7 +471,12 @@ extern "C" fem_status fem_solve(const fem_form* fc, const double* b, double* xio
   if (op64 == FEM_DF64) FEM_TRY(fem_form_ensure_df64(f, s));
   const int64_t n = w.n;
   FEM_CUDA(cudaMemcpyAsync(w.x, xio, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  FEM_TRY(fem_assemble_diagonal(f, w.diag, 1, s));
+  if (o.precond == FEM_PC_NONE) {
+    k_fill<<<w.nb, 256, 0, s>>>(n, 1.0, w.diag);
+    FEM_LAUNCHED();
+  } else {
+    FEM_TRY(fem_assemble_diagonal(f, w.diag, 1, s));
+  }
   fem_solve_info inf;
   std::memset(&inf, 0, sizeof inf);
   double hb[2];
