@@ -37,7 +37,7 @@ constexpr int ne_for(int Q) {
 // mbarrier.
 template <typename T, int D1, int Q, int NE, int NCOMP, bool STAGE>
 struct BlockSmem {
-  static constexpr size_t slabs = (sizeof(T) * NE * ElemSmem<D1, Q>::SE + 15) / 16 * 16;
+  static constexpr size_t slabs = (sizeof(T) * NE * ElemSmem<T, D1, Q>::SE + 15) / 16 * 16;
   static constexpr size_t tile = STAGE ? (sizeof(T) * NE * NCOMP * Q * Q * Q + 16 + 15) / 16 * 16 : 0;
   static constexpr size_t bytes = slabs + tile + (STAGE ? 16 : 0);
 };
@@ -63,7 +63,7 @@ template <typename T, int D1, int Q, int NE, typename TX, bool STAGE>
 __global__ void __launch_bounds__(Q * Q * NE)
 k_diffusion_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
                   const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye, int* __restrict__ err) {
-  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<D1, Q>::SE;
+  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
   using BS = BlockSmem<T, D1, Q, NE, 6, STAGE>;
   if (skip && *skip) return;  // a captured solver iteration after convergence
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -93,7 +93,7 @@ template <typename T, int D1, int Q, int NE, typename TX, bool STAGE>
 __global__ void __launch_bounds__(Q * Q * NE)
 k_mass_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
              const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye, int* __restrict__ err) {
-  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<D1, Q>::SE;
+  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
   using BS = BlockSmem<T, D1, Q, NE, 1, STAGE>;
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -76,7 +76,7 @@ __host__ __device__ constexpr int planes_for(int Q) { return (kBT + Q * Q - 1) /
 template <typename T, int D1, int Q>
 __device__ __noinline__ void run_tile(const BProb& P, int e0, int tile, int nrhs, const int* __restrict__ done,
                                       const T* __restrict__ X, T* __restrict__ YE, T* sm) {
-  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<D1, Q>::SE;
+  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
   const int tid = threadIdx.x;
   const int t = tid % (Q * Q), tz = tid / (Q * Q);
   const int e = e0 + tz;
@@ -423,10 +423,11 @@ __global__ void k_cast_vec(int64_t n, const double* __restrict__ a, float* __res
 
 template <typename T>
 size_t slab_bytes(int p, int q) {
-  const int D1 = p + 1, Q = q;
-  const int XP = D1 | 1, YP = D1 | 1, QP = Q | 1;
-  const int SA = D1 * D1 * XP + 2 * D1 * Q * YP + 3 * D1 * Q * Q, SB = 3 * D1 * Q * Q + 2 * D1 * D1 * QP;
-  return sizeof(T) * (size_t)planes_for(Q) * (size_t)(SA > SB ? SA : SB);
+#define X(P, Q) \
+  if (p == P && q == Q) return sizeof(T) * (size_t)planes_for(Q) * (size_t)ElemSmem<T, P + 1, Q>::SE;
+  FEM_FOR_EACH_PQ_BATCH(X)
+#undef X
+  return 0;
 }
 
 }  // namespace

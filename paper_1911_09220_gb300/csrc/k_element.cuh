@@ -21,12 +21,14 @@
 //       back z: T0, T1, T2[dz][qy][qx] = sum_qz B/G[qz][dz] v           (z^T)
 //   S4  (dz, qx) lines: UA, UB[dz][dy][qx] = sum_qy B/G[qy][dy] T       (y^T)
 //   S5  (dz, dy) lines: Y[dz][dy][dx] = sum_qx G[qx][dx] UA + B[qx][dx] UB (x^T)
-// Rows that threads read along are padded to an odd length so that lines of
-// neighbouring threads fall in different shared-memory banks.
+// Each stage's outputs are stored in its own thread order (consecutive words
+// per store) with row strides searched at compile time against the next
+// stage's read pattern (ElemSmem below), so that neither side of a stage
+// boundary replays for bank conflicts.
 //
 // Every thread of the block must call these functions the same number of
 // times (they contain __syncthreads); a plane without an element passes
-// valid = false and still owns an in-bounds slab of ElemSmem<D1,Q>::SE values.
+// valid = false and still owns an in-bounds slab of ElemSmem<T,D1,Q>::SE values.
 #pragma once
 
 #include <stdint.h>
@@ -219,19 +221,67 @@ __device__ __forceinline__ void gather_x(int t, bool valid, const int32_t* __res
   }
 }
 
-template <int D1, int Q>
+// ------------------------------------------------ shared-memory strides ----
+// Every intermediate tensor of the stages is stored in the order its writer
+// threads produce it (writer r stores word row * S + r: consecutive words,
+// no bank conflict), and its row stride S is chosen at compile time to
+// minimise the bank conflicts of its reader threads. Reader r of n reads word
+// (r % A) * m_lo + (r / A) * m_hi, with S in one of the two places. The cost
+// of a candidate S splits the readers of one element into bank groups (32
+// threads for 4-byte words; 16 for 8-byte words, which a warp accesses in two
+// halves) and sums, over the groups, the largest number of threads whose
+// words fall in one bank (distinct words, since every reader reads its own).
+__host__ __device__ constexpr int bank_cost(int n, int A, int m_lo, int m_hi, int wbytes) {
+  const int G = wbytes == 8 ? 16 : 32;
+  int cost = 0;
+  for (int g0 = 0; g0 < n; g0 += G) {
+    int cnt[32] = {};
+    int worst = 0;
+    for (int r = g0; r < n && r < g0 + G; ++r) {
+      const int w = (r % A) * m_lo + (r / A) * m_hi;
+      const int b = w % G;
+      cnt[b] += 1;
+      if (cnt[b] > worst) worst = cnt[b];
+    }
+    cost += worst;
+  }
+  return cost;
+}
+
+// Smallest stride >= lo of least reader cost (candidates lo .. lo + 31).
+__host__ __device__ constexpr int best_stride(int lo, int n, int A, bool stride_lo, int m_other, int wbytes) {
+  int best = lo, best_cost = 1 << 30;
+  for (int s = lo; s < lo + 32; ++s) {
+    const int c = stride_lo ? bank_cost(n, A, s, m_other, wbytes) : bank_cost(n, A, m_other, s, wbytes);
+    if (c < best_cost) {
+      best_cost = c;
+      best = s;
+    }
+  }
+  return best;
+}
+
+// Per-element shared-memory plan (in units of T):
+//   phase A  region 0: X [z][y][XP], dead after S1, then BB, GB, BG [qy][RC]
+//            over (z, qx); region 1 (offset R0): BX, GX [qx][RB] over (z, y)
+//   phase B  T0, T1, T2 [dz][RT] over (qy, qx);  UA, UB [dy][RU] over (dz, qx)
+template <typename T, int D1, int Q>
 struct ElemSmem {
-  static constexpr int XP = D1 | 1;  // padded x rows of X
-  static constexpr int YP = D1 | 1;  // padded y rows of BX, GX
-  static constexpr int QP = Q | 1;   // padded qx rows of UA, UB
-  static constexpr int SA = D1 * D1 * XP + 2 * D1 * Q * YP + 3 * D1 * Q * Q;
-  static constexpr int SB = 3 * D1 * Q * Q + 2 * D1 * D1 * QP;
+  static constexpr int W = (int)sizeof(T);
+  static constexpr int XP = D1 | 1;  // odd x rows: S1 reads rows with stride XP
+  static constexpr int RB = best_stride(D1 * D1, D1 * Q, Q, true, D1, W);  // S2 reader (z, qx)
+  static constexpr int RC = best_stride(D1 * Q, Q * Q, Q, false, 1, W);    // S3 reader (qy, qx)
+  static constexpr int RT = best_stride(Q * Q, D1 * Q, Q, false, 1, W);    // S4 reader (dz, qx)
+  static constexpr int RU = best_stride(D1 * Q, D1 * D1, D1, true, Q, W);  // S5 reader (dz, dy)
+  static constexpr int R0 = D1 * D1 * XP > 3 * Q * RC ? D1 * D1 * XP : 3 * Q * RC;
+  static constexpr int SA = R0 + 2 * Q * RB;
+  static constexpr int SB = 3 * D1 * RT + 2 * D1 * RU;
   static constexpr int SE = SA > SB ? SA : SB;  // per element, in T
 };
 
 // map: the element's DOF list (e2l + e*(p+1)^3); De: its D block
-// (D + e*q^3*6, point-major [q][6]); out: its E-vector slice. Dereferenced
-// only when valid.
+// (D + e*q^3*6, point-major [q][6]); out: its E-vector slice. Dereferenced only when
+// valid.
 // T: compute type (double, float or df64); TX: type of x and out.
 // DS: De points into a shared-memory tile staged by the caller, who passes
 // its barrier as bar (waited on before the tile is read) and an error word.
@@ -240,20 +290,19 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
                                                   const T* __restrict__ De, T* s, const TX* __restrict__ x,
                                                   TX* __restrict__ out, uint64_t* bar = nullptr,
                                                   int* err = nullptr) {
-  using L = ElemSmem<D1, Q>;
-  constexpr int QQ = Q * Q, XP = L::XP, YP = L::YP, QP = L::QP;
+  using L = ElemSmem<T, D1, Q>;
+  constexpr int QQ = Q * Q, XP = L::XP, RB = L::RB, RC = L::RC, RT = L::RT, RU = L::RU;
   constexpr int BF = eo_off(D1, Q, 0), GF = eo_off(D1, Q, 1), BT = eo_off(D1, Q, 2), GT = eo_off(D1, Q, 3);
   constexpr int cD = (D1 + 1) / 2, hD = D1 / 2 > 0 ? D1 / 2 : 1;
-  T* sX = s;                                // [z][y][XP]
-  T* sBX = sX + D1 * D1 * XP;               // [z][qx][YP]
-  T* sGX = sBX + D1 * Q * YP;
-  T* sBB = sGX + D1 * Q * YP;               // [z][qy][qx]
-  T* sGB = sBB + D1 * QQ;
-  T* sBG = sGB + D1 * QQ;
+  T* sX = s;                                // [z][y][XP] (region 0 until S1 ends)
+  T* sBX = s + L::R0;                       // [qx][RB], column z*D1 + y
+  T* sGX = sBX + Q * RB;
+  T* sBB = s;                               // [qy][RC], column z*Q + qx (region 0 from S2)
+  T* sGB = sBB + Q * RC;
+  T* sBG = sGB + Q * RC;
   gather_x<T, D1, Q, TX>(t, valid, map, x, sX, XP);
   __syncthreads();
   if (t < D1 * D1) {  // S1: line (z, y) along x
-    const int z = t / D1, y = t % D1;
     T xr[D1], e[cD], o[hD], bx[Q], gx[Q];
 #pragma unroll
     for (int d = 0; d < D1; ++d) xr[d] = sX[t * XP + d];
@@ -262,8 +311,8 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
     eo_apply<T, Q, D1, -1, GF>(e, o, gx);
 #pragma unroll
     for (int qx = 0; qx < Q; ++qx) {
-      sBX[(z * Q + qx) * YP + y] = bx[qx];
-      sGX[(z * Q + qx) * YP + y] = gx[qx];
+      sBX[qx * RB + t] = bx[qx];
+      sGX[qx * RB + t] = gx[qx];
     }
   }
   __syncthreads();
@@ -272,8 +321,8 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
     T br[D1], gr[D1], e[cD], o[hD], bb[Q], bg[Q], gb[Q];
 #pragma unroll
     for (int d = 0; d < D1; ++d) {
-      br[d] = sBX[t * YP + d];
-      gr[d] = sGX[t * YP + d];
+      br[d] = sBX[qx * RB + z * D1 + d];
+      gr[d] = sGX[qx * RB + z * D1 + d];
     }
     eo_split<T, D1>(br, e, o);
     eo_apply<T, Q, D1, 1, BF>(e, o, bb);
@@ -281,21 +330,21 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
     eo_line<T, Q, D1, 1, BF>(gr, gb);
 #pragma unroll
     for (int qy = 0; qy < Q; ++qy) {
-      const int o2 = (z * Q + qy) * Q + qx;
-      sBB[o2] = bb[qy];
-      sGB[o2] = gb[qy];
-      sBG[o2] = bg[qy];
+      sBB[qy * RC + t] = bb[qy];
+      sGB[qy * RC + t] = gb[qy];
+      sBG[qy * RC + t] = bg[qy];
     }
   }
   __syncthreads();
   T t0[D1], t1[D1], t2[D1];
   if (t < QQ) {  // S3: line (qy, qx) along z, D at every point, back along z
+    const int qy = t / Q, qx = t % Q;
     T rbb[D1], rgb[D1], rbg[D1], g0[Q], g1[Q], g2[Q];
 #pragma unroll
     for (int z = 0; z < D1; ++z) {
-      rbb[z] = sBB[z * QQ + t];
-      rgb[z] = sGB[z * QQ + t];
-      rbg[z] = sBG[z * QQ + t];
+      rbb[z] = sBB[qy * RC + z * Q + qx];
+      rgb[z] = sGB[qy * RC + z * Q + qx];
+      rbg[z] = sBG[qy * RC + z * Q + qx];
     }
     eo_line<T, Q, D1, 1, BF>(rgb, g0);
     eo_line<T, Q, D1, 1, BF>(rbg, g1);
@@ -322,17 +371,17 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
     eo_line<T, D1, Q, -1, GT>(g2, t2);
   }
   __syncthreads();  // phase-A arrays are dead from here on
-  T* sT0 = s;                               // [dz][qy][qx]
-  T* sT1 = sT0 + D1 * QQ;
-  T* sT2 = sT1 + D1 * QQ;
-  T* sUA = sT2 + D1 * QQ;                   // [dz][dy][QP]
-  T* sUB = sUA + D1 * D1 * QP;
+  T* sT0 = s;                               // [dz][RT], column qy*Q + qx
+  T* sT1 = sT0 + D1 * RT;
+  T* sT2 = sT1 + D1 * RT;
+  T* sUA = sT2 + D1 * RT;                   // [dy][RU], column dz*Q + qx
+  T* sUB = sUA + D1 * RU;
   if (t < QQ) {
 #pragma unroll
     for (int d = 0; d < D1; ++d) {
-      sT0[d * QQ + t] = t0[d];
-      sT1[d * QQ + t] = t1[d];
-      sT2[d * QQ + t] = t2[d];
+      sT0[d * RT + t] = t0[d];
+      sT1[d * RT + t] = t1[d];
+      sT2[d * RT + t] = t2[d];
     }
   }
   __syncthreads();
@@ -341,7 +390,7 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
     T a0[Q], a1[Q], a2[Q], ua[D1], u1[D1], u2[D1];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const int o2 = (dz * Q + q) * Q + qx;
+      const int o2 = dz * RT + q * Q + qx;
       a0[q] = sT0[o2];
       a1[q] = sT1[o2];
       a2[q] = sT2[o2];
@@ -351,17 +400,18 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
     eo_line<T, D1, Q, 1, BT>(a2, u2);
 #pragma unroll
     for (int dy = 0; dy < D1; ++dy) {
-      sUA[(dz * D1 + dy) * QP + qx] = ua[dy];
-      sUB[(dz * D1 + dy) * QP + qx] = fe_norm(u1[dy] + u2[dy]);
+      sUA[dy * RU + t] = ua[dy];
+      sUB[dy * RU + t] = fe_norm(u1[dy] + u2[dy]);
     }
   }
   __syncthreads();
   if (valid && t < D1 * D1) {  // S5: line (dz, dy) along qx
+    const int dz = t / D1, dy = t % D1;
     T ua[Q], ub[Q], y1[D1], y2[D1];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      ua[q] = sUA[t * QP + q];
-      ub[q] = sUB[t * QP + q];
+      ua[q] = sUA[dy * RU + dz * Q + q];
+      ub[q] = sUB[dy * RU + dz * Q + q];
     }
     eo_line<T, D1, Q, -1, GT>(ua, y1);
     eo_line<T, D1, Q, 1, BT>(ub, y2);
@@ -376,39 +426,39 @@ template <typename T, int D1, int Q, typename TX = T, bool DS = false>
 __device__ __forceinline__ void mass_element(int t, bool valid, const int32_t* __restrict__ map,
                                              const T* __restrict__ De, T* s, const TX* __restrict__ x,
                                              TX* __restrict__ out, uint64_t* bar = nullptr, int* err = nullptr) {
-  using L = ElemSmem<D1, Q>;
-  constexpr int QQ = Q * Q, XP = L::XP, YP = L::YP, QP = L::QP;
+  using L = ElemSmem<T, D1, Q>;
+  constexpr int QQ = Q * Q, XP = L::XP, RB = L::RB, RC = L::RC, RT = L::RT, RU = L::RU;
   constexpr int BF = eo_off(D1, Q, 0), BT = eo_off(D1, Q, 2);
-  T* sX = s;
-  T* sBX = sX + D1 * D1 * XP;
-  T* sBB = sBX + D1 * Q * YP;
+  T* sX = s;                   // region 0 until S1 ends
+  T* sBX = s + L::R0;          // [qx][RB]
+  T* sBB = s;                  // [qy][RC], region 0 from S2
   gather_x<T, D1, Q, TX>(t, valid, map, x, sX, XP);
   __syncthreads();
   if (t < D1 * D1) {
-    const int z = t / D1, y = t % D1;
     T xr[D1], bx[Q];
 #pragma unroll
     for (int d = 0; d < D1; ++d) xr[d] = sX[t * XP + d];
     eo_line<T, Q, D1, 1, BF>(xr, bx);
 #pragma unroll
-    for (int qx = 0; qx < Q; ++qx) sBX[(z * Q + qx) * YP + y] = bx[qx];
+    for (int qx = 0; qx < Q; ++qx) sBX[qx * RB + t] = bx[qx];
   }
   __syncthreads();
   if (t < D1 * Q) {
     const int z = t / Q, qx = t % Q;
     T br[D1], bb[Q];
 #pragma unroll
-    for (int d = 0; d < D1; ++d) br[d] = sBX[t * YP + d];
+    for (int d = 0; d < D1; ++d) br[d] = sBX[qx * RB + z * D1 + d];
     eo_line<T, Q, D1, 1, BF>(br, bb);
 #pragma unroll
-    for (int qy = 0; qy < Q; ++qy) sBB[(z * Q + qy) * Q + qx] = bb[qy];
+    for (int qy = 0; qy < Q; ++qy) sBB[qy * RC + t] = bb[qy];
   }
   __syncthreads();
   T t0[D1];
   if (t < QQ) {
+    const int qy = t / Q, qx = t % Q;
     T rbb[D1], u[Q];
 #pragma unroll
-    for (int z = 0; z < D1; ++z) rbb[z] = sBB[z * QQ + t];
+    for (int z = 0; z < D1; ++z) rbb[z] = sBB[qy * RC + z * Q + qx];
     eo_line<T, Q, D1, 1, BF>(rbb, u);
     if (DS) stage_wait(bar, err);
 #pragma unroll
@@ -416,27 +466,28 @@ __device__ __forceinline__ void mass_element(int t, bool valid, const int32_t* _
     eo_line<T, D1, Q, 1, BT>(u, t0);
   }
   __syncthreads();
-  T* sT0 = s;
-  T* sUA = sT0 + D1 * QQ;
+  T* sT0 = s;                  // [dz][RT]
+  T* sUA = sT0 + D1 * RT;      // [dy][RU]
   if (t < QQ) {
 #pragma unroll
-    for (int d = 0; d < D1; ++d) sT0[d * QQ + t] = t0[d];
+    for (int d = 0; d < D1; ++d) sT0[d * RT + t] = t0[d];
   }
   __syncthreads();
   if (t < D1 * Q) {
     const int dz = t / Q, qx = t % Q;
     T a0[Q], ua[D1];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) a0[q] = sT0[(dz * Q + q) * Q + qx];
+    for (int q = 0; q < Q; ++q) a0[q] = sT0[dz * RT + q * Q + qx];
     eo_line<T, D1, Q, 1, BT>(a0, ua);
 #pragma unroll
-    for (int dy = 0; dy < D1; ++dy) sUA[(dz * D1 + dy) * QP + qx] = ua[dy];
+    for (int dy = 0; dy < D1; ++dy) sUA[dy * RU + t] = ua[dy];
   }
   __syncthreads();
   if (valid && t < D1 * D1) {
+    const int dz = t / D1, dy = t % D1;
     T ua[Q], y[D1];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) ua[q] = sUA[t * QP + q];
+    for (int q = 0; q < Q; ++q) ua[q] = sUA[dy * RU + dz * Q + q];
     eo_line<T, D1, Q, 1, BT>(ua, y);
 #pragma unroll
     for (int dx = 0; dx < D1; ++dx) fe_store(&out[t * D1 + dx], y[dx]);
