@@ -26,7 +26,11 @@ matrix with the same quadrature):
 * essential-BC elimination, load vector, Jacobi-PCG and dense Cholesky
   (`solve`, Sec. 2 and Sec. 5.1);
 * the compliance gradient dJ/dkappa_e = -u_e^T Khat_e u_e (`gradient`);
-* the same definitions on quadrilaterals in 2D (`twod`).
+* the same definitions on quadrilaterals in 2D (`twod`);
+* p-multigrid: level hierarchy, nodal-interpolation transfers, coarse
+  essential DOFs, Chebyshev-Jacobi smoothing, the V-cycle and flexible CG
+  (`multigrid`; the paper names matrix-free p-multigrid, Sec. 5.2, without
+  an algorithm: the module header states the reading).
 
 Parity status: every function is pinned by `tests/test_oracle_*.py` against
 closed forms, invariants or brute force, except the mixed-precision error,
@@ -34,4 +38,4 @@ which has no oracle of its own (parity unpinned beyond the FP64 outer
 residual; the error against this FP64 oracle is reported per result).
 """
 
-from . import rules, lagrange, numbering, element, assemble, solve, gradient, twod  # noqa: F401
+from . import rules, lagrange, numbering, element, assemble, solve, gradient, twod, multigrid  # noqa: F401
