@@ -463,6 +463,60 @@ def run_paper2d(args):
     return 0
 
 
+def run_mg(args):
+    """p-multigrid workload: the apply workload's problem (p, N; lognormal
+    kappa, sin sin sin right-hand side, homogeneous Dirichlet conditions),
+    solved to 1e-10 by flexible CG with one V-cycle per iteration (FP64 and
+    FP32 V-cycles), beside Jacobi-PCG in FP64 and mixed precision. One JSON
+    line."""
+    import torch
+    from paper_1911_09220_gb300 import build as fbuild
+    fbuild.build()
+    import paper_1911_09220_gb300 as F
+    p, N = args.p, args.N
+    c, h, kappa, _ = make_problem(p, N)
+    space = F.Space(F.Mesh(c, h), p)
+    form = F.Form(space, "diffusion", p + 2, coef=torch.as_tensor(kappa, device="cuda"))
+    form.set_essential(torch.as_tensor(space.boundary_dofs(), device="cuda"))
+    b = torch.empty(space.ndof, dtype=torch.float64, device="cuda")
+    _sin_rhs(form, b)
+    bc = torch.empty_like(b)
+    form.lift_rhs(b, torch.zeros_like(b), bc)
+    out = {"workload": f"p-multigrid FCG, p={p}, q={p + 2}, {N}^3 hexes perturbed 0.15h, lognormal kappa, rtol 1e-10",
+           "p": p, "N": N, "ndof": space.ndof}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, r
+
+    for prec in ("f32", "f64"):
+        ts, mg = timed(lambda: F.Multigrid(form, precision=prec, coarse_its=args.mg_coarse_its))
+        res = {"setup_s": ts, "levels": mg.info()}
+        z = torch.empty_like(b)
+        res["vcycle_ms"] = time_events(lambda: mg.vcycle(bc, z), 5, 2)
+        best = None
+        for _ in range(2):
+            u = torch.zeros_like(b)
+            t, info = timed(lambda: mg.solve(bc, u, rtol=1e-10, check_every=4, raise_on_error=False))
+            if best is None or t < best[0]:
+                best = (t, info)
+        res.update({"seconds": best[0], "iterations": best[1]["iterations"], "relres": best[1]["relres"],
+                    "converged": best[1]["converged"]})
+        out["mg_" + prec] = res
+        del mg
+    if not args.no_solve:
+        for prec in ("mixed", "f64"):
+            u = torch.zeros_like(b)
+            t, info = timed(lambda: form.solve(bc, u, rtol=1e-10, maxit=args.solve_maxit, precision=prec,
+                                               raise_on_error=False))
+            out["pcg_" + prec] = {"seconds": t, "iterations": info["iterations"], "relres": info["relres"]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_grad(args):
     """Differentiation workload: 64^3 hexes, 0.1h, p = 2, kappa = 0.01 + rho^3,
     rho ~ U[0.2, 1], f = 1, homogeneous Dirichlet: compliance solve and the
@@ -514,12 +568,13 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--solve-maxit", type=int, default=20000)
-    ap.add_argument("--workload", default="apply", choices=["apply", "sweep", "batch", "grad", "paper2d"])
+    ap.add_argument("--workload", default="apply", choices=["apply", "sweep", "batch", "grad", "paper2d", "mg"])
     ap.add_argument("--sweep-size", default="4e6", choices=["4e6", "2e7"])
     ap.add_argument("--orders", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--nprob", type=int, default=256)
     ap.add_argument("--nrhs", type=int, default=8)
     ap.add_argument("--batch-f64-solve", action="store_true")
+    ap.add_argument("--mg-coarse-its", type=int, default=20)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -529,6 +584,8 @@ def main():
         return run_batch(args)
     if args.workload == "paper2d":
         return run_paper2d(args)
+    if args.workload == "mg":
+        return run_mg(args)
     if args.workload == "grad":
         return run_grad(args)
 

@@ -308,6 +308,71 @@ fem_status fem_batch_tune(fem_batch* batch, int dtype, const char* cache_path, v
 /* Current element tiles: tiles_host [18], entry 2p + (q - p - 1). */
 fem_status fem_batch_tiles(const fem_batch* batch, int* tiles_host);
 
+/* ---- p-multigrid preconditioner (Sec. 5.2 names matrix-free p-multigrid
+ * for PA operators as a research direction without fixing an algorithm; the
+ * algorithm below is this library's) --------------------------------------
+ * Levels p, p/2, ..., 1 on the fine form's mesh and coefficient, each a PA
+ * form of the same kind with q_l = p_l + (q - p) points. A coarse DOF is
+ * essential iff every fine DOF of the same mesh entity is. Transfers: P =
+ * nodal interpolation of the coarse function at the fine GLL nodes (each
+ * fine DOF takes its value from the first element holding it), masked to
+ * free DOFs on both sides; restriction = P^T. Smoother: cheb_order steps of
+ * Jacobi-preconditioned Chebyshev iteration on [cheb_lo, 1] * cheb_hi *
+ * lambda, lambda = D-Rayleigh quotient after power_its power iterations on
+ * D^-1 A_c from v_i = frac(i * 2654435761 / 2^32) - 1/2. Coarsest level:
+ * coarse_its Jacobi-PCG iterations from zero. V-cycle: pre-smoothing from
+ * zero, restricted residual, recursion, prolongated correction,
+ * post-smoothing. 3D (hexahedral) forms only. */
+typedef struct fem_mg fem_mg;
+typedef struct {
+  int cheb_order;       /* Chebyshev steps per pre- and post-smoothing (2) */
+  double cheb_lo;       /* lower end of the smoothing interval / upper end (0.25) */
+  double cheb_hi;       /* upper end / estimated lambda_max of D^-1 A_c (1.1) */
+  int power_its;        /* power iterations per smoothed level (20) */
+  int coarse_its;       /* Jacobi-PCG iterations on the coarsest level (20) */
+  int precision;        /* FEM_F64 or FEM_F32: arithmetic of the V-cycle */
+} fem_mg_opts;
+void fem_mg_opts_default(fem_mg_opts* opts);
+/* Builds the hierarchy for `fine` (fem_form_set_essential must have been
+ * called on it; the handle keeps a pointer to it: keep it alive and do not
+ * change its coefficient or essential DOFs while the handle exists). The
+ * coarse spaces and forms, diagonals, FP32 copies (precision FEM_F32) and
+ * lambda estimates are made here, synchronously on `stream`. Errors:
+ * FEM_EINVAL (bad options, no essential list), FEM_EUNSUPPORTED (2D mesh),
+ * FEM_ENOMEM. */
+fem_status fem_mg_create(const fem_form* fine, const fem_mg_opts* opts, void* stream,
+                         fem_mg** out);
+void fem_mg_destroy(fem_mg* mg);
+/* Level count and, per level l (fine first), order, lambda estimate (0 on
+ * the coarsest level) and DOF count; each host array may be NULL or holds
+ * at least nlevels entries. */
+fem_status fem_mg_info(const fem_mg* mg, int* nlevels, int* orders_host,
+                       double* lambdas_host, int64_t* ndofs_host);
+/* One V-cycle: z = M^-1 r. r, z: device float64 [ndof] of the fine space;
+ * entries of r on essential DOFs are ignored (taken as 0), z is 0 there.
+ * Uses the fine form's E-vector scratch: do not run another operation of
+ * that form concurrently. */
+fem_status fem_mg_vcycle(fem_mg* mg, const double* r, double* z, void* stream);
+/* The form of level l (0 = the fine form); owned by the handle (level 0 by
+ * the caller). Its essential DOFs are the level's. NULL if l is out of
+ * range. */
+const fem_form* fem_mg_level_form(const fem_mg* mg, int level);
+/* Transfers between level l (finer) and l + 1, FP64: zf = P~ zc (prolong)
+ * and rc = P~^T rf (restrict), with P~ = (I - E_l) P (I - E_{l+1}). zc, rc:
+ * device float64 [ndof of level l+1]; zf, rf: [ndof of level l]. Uses the
+ * E-vector scratch of both levels' forms. Errors: FEM_EINVAL (l out of
+ * range). */
+fem_status fem_mg_prolong(fem_mg* mg, int level, const double* zc, double* zf, void* stream);
+fem_status fem_mg_restrict(fem_mg* mg, int level, const double* rf, double* rc, void* stream);
+/* Flexible CG (FP64; beta = z.(r - r_old) / z_old.r_old) on the fine
+ * constrained operator, preconditioned by one V-cycle per iteration. x and b
+ * as for fem_solve; opts: rtol, maxit, max_outer (restarts when the true
+ * residual disagrees with the recursive one), check_every, use_graph (the
+ * other fields are ignored). Synchronises `stream`. Errors: FEM_ENOCONV,
+ * FEM_EBREAKDOWN. */
+fem_status fem_mg_solve(fem_mg* mg, const double* b, double* x, const fem_solve_opts* opts,
+                        fem_solve_info* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

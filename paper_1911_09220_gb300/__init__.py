@@ -19,7 +19,7 @@ from . import _binding as B
 from ._binding import (FemError, FEM_DIFFUSION, FEM_MASS, FEM_F64, FEM_F32, FEM_DF64, FEM_SOLVE_F64,
                        FEM_SOLVE_MIXED, FEM_SOLVE_DF64, FEM_SOLVE_MIXED_RU)
 
-__all__ = ["Mesh", "Mesh2D", "Space", "Form", "Batch", "FemError", "lib", "supported", "version"]
+__all__ = ["Mesh", "Mesh2D", "Space", "Form", "Batch", "Multigrid", "FemError", "lib", "supported", "version"]
 
 
 def lib():
@@ -340,3 +340,88 @@ class Batch:
         if getattr(self, "_h", None) and B._lib is not None:
             B._lib.fem_batch_destroy(self._h)
             self._h = None
+
+
+class Multigrid:
+    """p-multigrid preconditioner of a form (levels p, p/2, ..., 1; Chebyshev-
+    Jacobi smoothing; coarsest level by Jacobi-PCG) and flexible CG with it.
+    precision: "f64" or "f32" (arithmetic of the V-cycle; the outer iteration
+    is FP64). set_essential must have been called on the form."""
+
+    def __init__(self, form, cheb_order=2, cheb_lo=0.25, cheb_hi=1.1, power_its=20, coarse_its=20,
+                 precision="f64", stream=None):
+        L = B.lib()
+        self.form = form
+        o = B.MgOpts()
+        L.fem_mg_opts_default(C.byref(o))
+        o.cheb_order, o.cheb_lo, o.cheb_hi = int(cheb_order), float(cheb_lo), float(cheb_hi)
+        o.power_its, o.coarse_its = int(power_its), int(coarse_its)
+        o.precision = {"f64": FEM_F64, "f32": FEM_F32}[precision]
+        h = C.c_void_p()
+        B.check(L.fem_mg_create(form._h, C.byref(o), _stream(stream), C.byref(h)))
+        self._h = h
+
+    def info(self):
+        n = C.c_int()
+        B.check(B.lib().fem_mg_info(self._h, C.byref(n), None, None, None))
+        orders = np.zeros(n.value, dtype=np.int32)
+        lams = np.zeros(n.value, dtype=np.float64)
+        ndofs = np.zeros(n.value, dtype=np.int64)
+        B.check(B.lib().fem_mg_info(self._h, None, orders.ctypes.data, lams.ctypes.data, ndofs.ctypes.data))
+        return {"orders": orders.tolist(), "lambdas": lams.tolist(), "ndofs": ndofs.tolist()}
+
+    def level_form(self, level):
+        """A non-owning view of level `level`'s form (apply, diagonal, ...)."""
+        h = B.lib().fem_mg_level_form(self._h, int(level))
+        if not h:
+            raise IndexError(level)
+        v = Form.__new__(_FormView)
+        v._h, v._owner, v.space, v.ess = C.c_void_p(h), self, None, None
+        return v
+
+    def prolong(self, level, zc, zf, stream=None):
+        import torch
+        B.check(B.lib().fem_mg_prolong(self._h, int(level), _ptr(zc, torch.float64, "zc"), _ptr(zf, torch.float64, "zf"),
+                                       _stream(stream)))
+        return zf
+
+    def restrict(self, level, rf, rc, stream=None):
+        import torch
+        B.check(B.lib().fem_mg_restrict(self._h, int(level), _ptr(rf, torch.float64, "rf"),
+                                        _ptr(rc, torch.float64, "rc"), _stream(stream)))
+        return rc
+
+    def vcycle(self, r, z, stream=None):
+        import torch
+        B.check(B.lib().fem_mg_vcycle(self._h, _ptr(r, torch.float64, "r"), _ptr(z, torch.float64, "z"),
+                                      _stream(stream)))
+        return z
+
+    def solve(self, b, x, rtol=1e-10, maxit=500, max_outer=30, check_every=4, use_graph=True, stream=None,
+              raise_on_error=True):
+        import torch
+        o = B.SolveOpts()
+        B.lib().fem_solve_opts_default(C.byref(o))
+        o.rtol, o.maxit, o.max_outer = rtol, maxit, max_outer
+        o.check_every, o.use_graph = check_every, int(bool(use_graph))
+        info = B.SolveInfo()
+        st = B.lib().fem_mg_solve(self._h, _ptr(b, torch.float64, "b"), _ptr(x, torch.float64, "x"), C.byref(o),
+                                  C.byref(info), _stream(stream))
+        out = {"status": st, "iterations": info.iterations, "outer": info.outer,
+               "converged": bool(info.converged), "relres": info.relres, "bnorm": info.bnorm}
+        if st != B.FEM_OK and raise_on_error:
+            raise FemError(st, B.lib().fem_last_error().decode())
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None) and B._lib is not None:
+            B._lib.fem_mg_destroy(self._h)
+            self._h = None
+
+
+class _FormView(Form):
+    """A form owned by another handle (a multigrid level): same methods,
+    nothing destroyed on collection."""
+
+    def __del__(self):
+        pass

@@ -34,6 +34,11 @@ class SolveOpts(C.Structure):
                 ("use_graph", C.c_int), ("precond", C.c_int)]
 
 
+class MgOpts(C.Structure):
+    _fields_ = [("cheb_order", C.c_int), ("cheb_lo", C.c_double), ("cheb_hi", C.c_double), ("power_its", C.c_int),
+                ("coarse_its", C.c_int), ("precision", C.c_int)]
+
+
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int), ("outer", C.c_int), ("converged", C.c_int),
                 ("relres", C.c_double), ("bnorm", C.c_double)]
@@ -80,6 +85,15 @@ SIGNATURES = {
     "fem_batch_solve": (I, [P, P, P, C.POINTER(SolveOpts), P, P, P]),
     "fem_batch_tune": (I, [P, I, C.c_char_p, P]),
     "fem_batch_tiles": (I, [P, P]),
+    "fem_mg_opts_default": (None, [C.POINTER(MgOpts)]),
+    "fem_mg_create": (I, [P, C.POINTER(MgOpts), P, C.POINTER(P)]),
+    "fem_mg_destroy": (None, [P]),
+    "fem_mg_info": (I, [P, P, P, P, P]),
+    "fem_mg_vcycle": (I, [P, P, P, P]),
+    "fem_mg_level_form": (P, [P, I]),
+    "fem_mg_prolong": (I, [P, I, P, P, P]),
+    "fem_mg_restrict": (I, [P, I, P, P, P]),
+    "fem_mg_solve": (I, [P, P, P, C.POINTER(SolveOpts), C.POINTER(SolveInfo), P]),
 }
 
 _lib = None

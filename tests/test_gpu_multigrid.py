@@ -1,0 +1,181 @@
+"""Parity of the p-multigrid preconditioner and flexible CG of the CUDA
+library (fem_mg_*) with the oracle (oracle.multigrid) on the same seeded
+inputs: level orders and sizes, lambda estimates, one V-cycle (FP64 and
+FP32 arithmetic; whole-boundary and one-face essential sets; p = 1..8,
+shuffled meshes, ragged element counts), the solve (true residual by the
+oracle's CSR, iteration count against the oracle's FCG), determinism and
+error reporting.
+
+Tolerances: the FP64 V-cycle runs ~4K + 20 operator applications and a
+20-step CG whose coefficients are ratios of dot products; rounding-order
+differences of ~1e-16 per operation grow to at most ~1e-12 relative in the
+max norm on these sizes, so 1e-10 is required. The FP32 V-cycle is
+compared at 1e-4 (single precision, amplified by the same ratios)."""
+
+import numpy as np
+import pytest
+
+from fem_inputs import lognormal, x_uniform
+from oracle import assemble, multigrid as omg, solve as osolve
+
+from gpu_util import cuda, make_mesh, relerr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1911_09220_gb300 import build
+    build.build()
+
+
+def _setup(p, N=3, drop=0, shuffle=True, face_only=False, seed=5, **kw):
+    import paper_1911_09220_gb300 as F
+    c, h = make_mesh(N, perturb=0.15, seed=seed, shuffle=shuffle, drop=drop)
+    kap = lognormal(seed + 1, h.shape[0])
+    fine = assemble.Problem(c, h, p, p + 2, kappa=kap)
+    if face_only:
+        X = fine.dof_coords()
+        ess = np.nonzero(np.abs(X[:, 0]) < 1e-12)[0]
+    else:
+        ess = fine.num["boundary_dofs"]
+    mesh = F.Mesh(c, h)
+    space = F.Space(mesh, p)
+    form = F.Form(space, "diffusion", p + 2, coef=cuda(kap))
+    form.set_essential(ess)
+    okw = {k: v for k, v in kw.items() if k != "precision"}
+    M = omg.PMG(c, h, p, p + 2, kap, ess, fine_prob=fine, **okw)
+    G = F.Multigrid(form, **kw)
+    return M, G, form, fine, ess, (mesh, space)
+
+
+@pytest.mark.parametrize("p,N,drop", [(2, 4, 3), (3, 3, 1), (4, 3, 2), (5, 2, 1), (8, 2, 0), (1, 4, 5)])
+def test_levels_and_lambdas(p, N, drop):
+    M, G, *_ = _setup(p, N, drop)
+    info = G.info()
+    assert info["orders"] == omg.level_orders(p)
+    assert info["ndofs"] == [lv.n for lv in M.levels]
+    for l, lv in enumerate(M.levels[:-1]):
+        assert abs(info["lambdas"][l] - lv.lam) <= 1e-10 * lv.lam
+
+
+@pytest.mark.parametrize("face_only", [False, True])
+@pytest.mark.parametrize("p,N,drop", [(2, 4, 3), (4, 3, 2), (7, 2, 0), (8, 2, 1)])
+def test_level_operators_and_transfers(p, N, drop, face_only):
+    """Every level's constrained operator and diagonal (coarse essential
+    DOFs included) and both transfers against the oracle's matrices."""
+    import torch
+    M, G, form, fine, ess, keep = _setup(p, N, drop, face_only=face_only)
+    for l, lv in enumerate(M.levels):
+        f = G.level_form(l)
+        x = x_uniform(40 + l, lv.n)
+        y = torch.empty(lv.n, dtype=torch.float64, device="cuda")
+        f.apply(cuda(x), y, constrained=True)
+        assert relerr(y.cpu().numpy(), lv.A @ x) <= 1e-12
+        d = torch.empty_like(y)
+        f.diagonal(d, constrained=True)
+        assert relerr(d.cpu().numpy(), lv.D) <= 1e-12
+        if l + 1 < len(M.levels):
+            nc = M.levels[l + 1].n
+            zc = x_uniform(50 + l, nc)
+            zf = torch.empty(lv.n, dtype=torch.float64, device="cuda")
+            G.prolong(l, cuda(zc), zf)
+            assert relerr(zf.cpu().numpy(), lv.P @ zc) <= 1e-13
+            rc = torch.empty(nc, dtype=torch.float64, device="cuda")
+            G.restrict(l, cuda(x), rc)
+            assert relerr(rc.cpu().numpy(), lv.P.T @ x) <= 1e-13
+    with pytest.raises(IndexError):
+        G.level_form(len(M.levels))
+
+
+@pytest.mark.parametrize("face_only", [False, True])
+@pytest.mark.parametrize("p,N,drop", [(2, 4, 3), (3, 3, 1), (4, 3, 2), (5, 2, 1), (6, 2, 1), (7, 2, 0), (8, 2, 1),
+                                      (1, 4, 5)])
+def test_vcycle_parity_fp64(p, N, drop, face_only):
+    import torch
+    M, G, form, fine, ess, keep = _setup(p, N, drop, face_only=face_only)
+    r = x_uniform(10 + p, fine.ndof)
+    r[ess] = 0.0
+    z = torch.empty(fine.ndof, dtype=torch.float64, device="cuda")
+    G.vcycle(cuda(r), z)
+    ref = M.vcycle(r)
+    assert relerr(z.cpu().numpy(), ref) <= 1e-10
+    # entries of r on essential DOFs are ignored
+    r2 = r.copy()
+    r2[ess] = 7.0
+    z2 = torch.empty_like(z)
+    G.vcycle(cuda(r2), z2)
+    assert torch.equal(z, z2)
+
+
+@pytest.mark.parametrize("p,N", [(2, 4), (4, 3), (8, 2)])
+def test_vcycle_parity_fp32(p, N):
+    import torch
+    M, G, form, fine, ess, keep = _setup(p, N, precision="f32")
+    r = x_uniform(20 + p, fine.ndof)
+    r[ess] = 0.0
+    z = torch.empty(fine.ndof, dtype=torch.float64, device="cuda")
+    G.vcycle(cuda(r), z)
+    assert relerr(z.cpu().numpy(), M.vcycle(r)) <= 1e-4
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("p,N,face_only", [(2, 5, False), (4, 3, False), (4, 3, True), (8, 2, False), (3, 4, True)])
+def test_solve(p, N, face_only, precision):
+    import torch
+    M, G, form, fine, ess, keep = _setup(p, N, face_only=face_only, precision=precision)
+    bvec = x_uniform(30 + p, fine.ndof)
+    bc = torch.empty(fine.ndof, dtype=torch.float64, device="cuda")
+    form.lift_rhs(cuda(bvec), torch.zeros_like(bc), bc)
+    x = torch.zeros_like(bc)
+    info = G.solve(bc, x, rtol=1e-10)
+    assert info["converged"]
+    u = x.cpu().numpy()
+    Ac = M.levels[0].A
+    bco = osolve.constrain_rhs(fine.K, bvec, ess)
+    assert np.linalg.norm(bco - Ac @ u) / np.linalg.norm(bco) <= 1.01e-10
+    xo, ito, relo = M.fcg(bco, rtol=1e-10)
+    if precision == "f64":
+        assert abs(info["iterations"] - ito) <= 1, (info, ito)
+    else:
+        assert info["iterations"] <= ito + 3, (info, ito)
+    # far fewer iterations than Jacobi-PCG
+    _, ij = osolve.pcg(Ac, bco, rtol=1e-10)
+    assert info["iterations"] * 4 < ij["iterations"]
+
+
+def test_solve_deterministic_and_graph_free_path():
+    import torch
+    M, G, form, fine, ess, keep = _setup(4, 3)
+    b = torch.empty(fine.ndof, dtype=torch.float64, device="cuda")
+    form.lift_rhs(cuda(x_uniform(3, fine.ndof)), torch.zeros_like(b), b)
+    xs = []
+    for graph in (True, True, False):
+        x = torch.zeros_like(b)
+        info = G.solve(b, x, use_graph=graph, check_every=3)
+        xs.append((x, info["iterations"]))
+    assert torch.equal(xs[0][0], xs[1][0]) and xs[0][1] == xs[1][1]
+    assert torch.equal(xs[0][0], xs[2][0]) and xs[0][1] == xs[2][1]
+
+
+def test_errors():
+    import paper_1911_09220_gb300 as F
+    from fem_inputs import quad_lattice
+    c, h = make_mesh(2)
+    form = F.Form(F.Space(F.Mesh(c, h), 2), "diffusion", 4)
+    with pytest.raises(F.FemError) as ei:
+        F.Multigrid(form)                      # no essential list yet
+    assert ei.value.status == 1
+    form.set_essential(np.array([], dtype=np.int32))
+    with pytest.raises(F.FemError) as ei:
+        F.Multigrid(form, cheb_lo=1.5)
+    assert ei.value.status == 1
+    c2, q2 = quad_lattice(3)
+    f2 = F.Form(F.Space(F.Mesh2D(c2, q2), 2), "diffusion", 4)
+    f2.set_essential(np.array([0], dtype=np.int32))
+    with pytest.raises(F.FemError) as ei:
+        F.Multigrid(f2)
+    assert ei.value.status == 7
