@@ -329,7 +329,7 @@ typedef struct {
   double cheb_lo;       /* lower end of the smoothing interval / upper end (0.25) */
   double cheb_hi;       /* upper end / estimated lambda_max of D^-1 A_c (1.1) */
   int power_its;        /* power iterations per smoothed level (20) */
-  int coarse_its;       /* Jacobi-PCG iterations on the coarsest level (20) */
+  int coarse_its;       /* Jacobi-PCG iterations on the coarsest level (30) */
   int precision;        /* FEM_F64 or FEM_F32: arithmetic of the V-cycle */
 } fem_mg_opts;
 void fem_mg_opts_default(fem_mg_opts* opts);
@@ -367,9 +367,11 @@ fem_status fem_mg_restrict(fem_mg* mg, int level, const double* rf, double* rc, 
 /* Flexible CG (FP64; beta = z.(r - r_old) / z_old.r_old) on the fine
  * constrained operator, preconditioned by one V-cycle per iteration. x and b
  * as for fem_solve; opts: rtol, maxit, max_outer (restarts when the true
- * residual disagrees with the recursive one), check_every, use_graph (the
- * other fields are ignored). Synchronises `stream`. Errors: FEM_ENOCONV,
- * FEM_EBREAKDOWN. */
+ * residual disagrees with the recursive one), check_every, use_graph, and
+ * precision FEM_SOLVE_F64 or FEM_SOLVE_DF64 (arithmetic of the outer
+ * operator apply; the final true residual is always FP64); the other fields
+ * are ignored. Synchronises `stream`. Errors: FEM_EINVAL (other precision),
+ * FEM_ENOCONV, FEM_EBREAKDOWN. */
 fem_status fem_mg_solve(fem_mg* mg, const double* b, double* x, const fem_solve_opts* opts,
                         fem_solve_info* info, void* stream);
 

@@ -125,7 +125,7 @@ class PMG:
     ess: fine essential DOF ids."""
 
     def __init__(self, coords, hexes, p, q, kappa, ess, cheb_order=2, alpha=0.25, beta=1.1, power_its=20,
-                 coarse_its=20, fine_prob=None):
+                 coarse_its=30, fine_prob=None):
         self.K, self.alpha, self.beta = cheb_order, alpha, beta
         self.coarse_its = coarse_its
         orders = level_orders(p)

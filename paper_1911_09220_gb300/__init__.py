@@ -348,7 +348,7 @@ class Multigrid:
     precision: "f64" or "f32" (arithmetic of the V-cycle; the outer iteration
     is FP64). set_essential must have been called on the form."""
 
-    def __init__(self, form, cheb_order=2, cheb_lo=0.25, cheb_hi=1.1, power_its=20, coarse_its=20,
+    def __init__(self, form, cheb_order=2, cheb_lo=0.25, cheb_hi=1.1, power_its=20, coarse_its=30,
                  precision="f64", stream=None):
         L = B.lib()
         self.form = form
@@ -398,11 +398,16 @@ class Multigrid:
         return z
 
     def solve(self, b, x, rtol=1e-10, maxit=500, max_outer=30, check_every=4, use_graph=True, stream=None,
-              raise_on_error=True):
+              raise_on_error=True, arith="f64"):
+        """Flexible CG with one V-cycle per iteration; arith: "f64" or "df64"
+        (double-float) for the outer operator apply."""
         import torch
         o = B.SolveOpts()
         B.lib().fem_solve_opts_default(C.byref(o))
         o.rtol, o.maxit, o.max_outer = rtol, maxit, max_outer
+        if arith not in ("f64", "df64"):
+            raise ValueError(f"arith must be 'f64' or 'df64', not {arith!r}")
+        o.precision = FEM_SOLVE_F64 if arith == "f64" else FEM_SOLVE_DF64
         o.check_every, o.use_graph = check_every, int(bool(use_graph))
         info = B.SolveInfo()
         st = B.lib().fem_mg_solve(self._h, _ptr(b, torch.float64, "b"), _ptr(x, torch.float64, "x"), C.byref(o),

@@ -47,11 +47,6 @@ struct MgScalars {
 };
 enum { MS_RUN = 0, MS_CONV = 1, MS_NOCONV = 2, MS_BREAK = 3 };
 
-struct CcScalars {  // coarsest-level CG
-  double rz, alpha, beta;
-  int it, done, m, pad;
-};
-
 __device__ double sum_part(const double* part, int n, double* red) {
   double v = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
@@ -219,12 +214,23 @@ k_mg_interp(int ne, const int32_t* __restrict__ map, const uint8_t* __restrict__
 }
 
 // ------------------------------------------------------ coarsest-level CG
+// m Jacobi-PCG iterations from zero, four launches per iteration (element,
+// scatter with p.q partials, update, p update) and no single-block kernel:
+// every block sums the partials it needs itself, in the same fixed order, so
+// all blocks hold the same alpha and beta. The r.z partials alternate between
+// two buffers by iteration parity (the launch's iteration k is a kernel
+// argument), so no buffer is written while another block may read it. `stop`
+// is set by block 0 when p.q <= 0 (the iteration ends there, as in the
+// oracle) and read by the later launches.
 template <typename T>
 __global__ void k_cc_init(int64_t n, const T* __restrict__ rin, const T* __restrict__ D, T* __restrict__ r,
-                          T* __restrict__ z, T* __restrict__ p, T* __restrict__ x, double* __restrict__ part,
-                          const int* __restrict__ skip) {
+                          T* __restrict__ z, T* __restrict__ p, T* __restrict__ x, double* __restrict__ part_rz,
+                          int* __restrict__ stop, const int* __restrict__ skip) {
   __shared__ double red[32];
-  if (*skip) return;
+  if (*skip) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *stop = 1;
+    return;
+  }
   double rz = 0;
   GRID_LOOP(i, n) {
     const T ri = rin[i];
@@ -236,70 +242,58 @@ __global__ void k_cc_init(int64_t n, const T* __restrict__ rin, const T* __restr
     rz += (double)ri * (double)zi;
   }
   const double s = block_sum(rz, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (threadIdx.x == 0) {
+    part_rz[blockIdx.x] = s;
+    if (blockIdx.x == 0) *stop = 0;
+  }
 }
 
-__global__ void k_cc_scal(CcScalars* cc, const double* __restrict__ part, int nb, int m, const int* __restrict__ skip) {
+// x += a p, r -= a q, z = r / D, partials of the new r.z into part_new;
+// a = rz / pq with rz = sum(part_rz), pq = sum(part_pq).
+template <typename T>
+__global__ void k_cc_update(int64_t n, int nb, const double* __restrict__ part_pq, const double* __restrict__ part_rz,
+                            double* __restrict__ part_new, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
+                            const T* __restrict__ p, const T* __restrict__ q, const T* __restrict__ D,
+                            int* __restrict__ stop) {
   __shared__ double red[32];
-  if (*skip) {
-    if (threadIdx.x == 0) cc->done = 1;
+  __shared__ double sh[2];
+  if (*stop) return;
+  const double pq = sum_part(part_pq, nb, red);
+  if (threadIdx.x == 0) sh[0] = pq;
+  const double rz = sum_part(part_rz, nb, red);
+  if (threadIdx.x == 0) sh[1] = rz;
+  __syncthreads();
+  if (!(sh[0] > 0.0)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *stop = 1;
     return;
   }
-  const double rz = sum_part(part, nb, red);
-  if (threadIdx.x == 0) {
-    cc->rz = rz;
-    cc->it = 0;
-    cc->m = m;
-    cc->done = m <= 0 ? 1 : 0;
-  }
-}
-
-__global__ void k_cc_alpha(CcScalars* cc, const double* __restrict__ part, int nb) {
-  __shared__ double red[32];
-  if (cc->done) return;
-  const double pq = sum_part(part, nb, red);
-  if (threadIdx.x == 0) {
-    if (!(pq > 0.0)) cc->done = 1;
-    else cc->alpha = cc->rz / pq;
-  }
-}
-
-template <typename T>
-__global__ void k_cc_update(int64_t n, const CcScalars* __restrict__ cc, T* __restrict__ x, T* __restrict__ r,
-                            T* __restrict__ z, const T* __restrict__ p, const T* __restrict__ q,
-                            const T* __restrict__ D, double* __restrict__ part) {
-  __shared__ double red[32];
-  if (cc->done) return;
-  const T a = (T)cc->alpha;
-  double rz = 0;
+  const T a = (T)(sh[1] / sh[0]);
+  double acc = 0;
   GRID_LOOP(i, n) {
     x[i] += a * p[i];
     const T ri = r[i] - a * q[i];
     r[i] = ri;
     const T zi = ri / D[i];
     z[i] = zi;
-    rz += (double)ri * (double)zi;
+    acc += (double)ri * (double)zi;
   }
-  const double s = block_sum(rz, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part_new[blockIdx.x] = s;
 }
 
-__global__ void k_cc_beta(CcScalars* cc, const double* __restrict__ part, int nb) {
-  __shared__ double red[32];
-  if (cc->done) return;
-  const double rz = sum_part(part, nb, red);
-  if (threadIdx.x == 0) {
-    cc->it += 1;
-    cc->beta = rz / cc->rz;
-    cc->rz = rz;
-    if (cc->it >= cc->m) cc->done = 1;
-  }
-}
-
+// p = z + (rz_new / rz_old) p
 template <typename T>
-__global__ void k_cc_p(int64_t n, const CcScalars* __restrict__ cc, const T* __restrict__ z, T* __restrict__ p) {
-  if (cc->done) return;
-  const T b = (T)cc->beta;
+__global__ void k_cc_p(int64_t n, int nb, const double* __restrict__ part_old, const double* __restrict__ part_new,
+                       const T* __restrict__ z, T* __restrict__ p, const int* __restrict__ stop) {
+  __shared__ double red[32];
+  __shared__ double sh[2];
+  if (*stop) return;
+  const double ro = sum_part(part_old, nb, red);
+  if (threadIdx.x == 0) sh[0] = ro;
+  const double rn = sum_part(part_new, nb, red);
+  if (threadIdx.x == 0) sh[1] = rn;
+  __syncthreads();
+  const T b = (T)(sh[1] / sh[0]);
   GRID_LOOP(i, n) p[i] = z[i] + b * p[i];
 }
 
@@ -529,7 +523,7 @@ struct fem_mg {
   void* zero = nullptr;         // zeros (T) of the largest coarse level
   void* cc_vec = nullptr;       // coarsest CG: r, z, p, q (T)
   double* part = nullptr;       // 3 * nb partials
-  CcScalars* cc = nullptr;
+  int* d_stop = nullptr;        // coarsest CG: stop word
   MgScalars* sc = nullptr;      // outer FCG scalars
   double* w64 = nullptr;        // FCG: x, r, rold, z, p, q, t
   int* h = nullptr;             // pinned host words
@@ -576,24 +570,27 @@ fem_status launch_interp(int D1f, int D1c, bool prolong, int ne, const int32_t* 
   return fem_fail(FEM_EUNSUPPORTED, "multigrid: no transfer for orders %d -> %d", D1f - 1, D1c - 1);
 }
 
+// Blocks of the coarsest level's vector kernels: at most two per SM, so
+// that every block's own sums over the partials stay short.
+int cc_blocks(int64_t n) { return std::min(grid_for(n, 256), 2 * fem_sm_count()); }
+
 template <typename T>
 fem_status coarse_solve(fem_mg* m, const MgLevel& C, const int* skip, cudaStream_t s) {
   const int64_t n = C.n;
-  const int nb = vblocks(n);
+  const int nb = cc_blocks(n);
   T* cv = reinterpret_cast<T*>(m->cc_vec);
   T *r = cv, *z = cv + n, *p = cv + 2 * n, *q = cv + 3 * n;
   const T* D = std::is_same<T, float>::value ? (const T*)C.diag32 : (const T*)C.diag64;
   T* x = lvec<T>(C, 1);
-  k_cc_init<T><<<nb, 256, 0, s>>>(n, lvec<T>(C, 0), D, r, z, p, x, m->part, skip);
-  k_cc_scal<<<1, kRed, 0, s>>>(m->cc, m->part, nb, m->o.coarse_its, skip);
+  double* pq = m->part;
+  double* rzp[2] = {m->part + nb, m->part + 2 * nb};
+  int* stop = m->d_stop;
+  k_cc_init<T><<<nb, 256, 0, s>>>(n, lvec<T>(C, 0), D, r, z, p, x, rzp[0], stop, skip);
   FEM_LAUNCHED();
-  const int* cskip = &m->cc->done;
-  for (int it = 0; it < m->o.coarse_its; ++it) {
-    FEM_TRY(level_apply<T>(C, p, q, cskip, s, m->part, nb));
-    k_cc_alpha<<<1, kRed, 0, s>>>(m->cc, m->part, nb);
-    k_cc_update<T><<<nb, 256, 0, s>>>(n, m->cc, x, r, z, p, q, D, m->part);
-    k_cc_beta<<<1, kRed, 0, s>>>(m->cc, m->part, nb);
-    k_cc_p<T><<<nb, 256, 0, s>>>(n, m->cc, z, p);
+  for (int k = 0; k < m->o.coarse_its; ++k) {
+    FEM_TRY(level_apply<T>(C, p, q, stop, s, pq, nb));
+    k_cc_update<T><<<nb, 256, 0, s>>>(n, nb, pq, rzp[k & 1], rzp[(k + 1) & 1], x, r, z, p, q, D, stop);
+    k_cc_p<T><<<nb, 256, 0, s>>>(n, nb, rzp[k & 1], rzp[(k + 1) & 1], z, p, stop);
     FEM_LAUNCHED();
   }
   return FEM_OK;
@@ -790,7 +787,7 @@ extern "C" void fem_mg_opts_default(fem_mg_opts* o) {
   o->cheb_lo = 0.25;
   o->cheb_hi = 1.1;
   o->power_its = 20;
-  o->coarse_its = 20;
+  o->coarse_its = 30;
   o->precision = FEM_F64;
 }
 
@@ -808,7 +805,7 @@ extern "C" void fem_mg_destroy(fem_mg* m) {
   if (m->zero) cudaFree(m->zero);
   if (m->cc_vec) cudaFree(m->cc_vec);
   dev_free(m->part);
-  if (m->cc) cudaFree(m->cc);
+  dev_free(m->d_stop);
   if (m->sc) cudaFree(m->sc);
   dev_free(m->w64);
   dev_free(m->d_never);
@@ -893,10 +890,10 @@ extern "C" fem_status fem_mg_create(const fem_form* fine, const fem_mg_opts* opt
   const int64_t n0 = m->lv[0].n;
   m->nb = vblocks(n0);
   if ((st = dev_alloc(&m->part, (size_t)3 * m->nb + 8)) != FEM_OK) return fail(st);
-  if (cudaMalloc((void**)&m->cc, sizeof(CcScalars)) != cudaSuccess ||
-      cudaMalloc((void**)&m->sc, sizeof(MgScalars)) != cudaSuccess)
+  if ((st = dev_alloc(&m->d_stop, 1)) != FEM_OK) return fail(st);
+  if (cudaMalloc((void**)&m->sc, sizeof(MgScalars)) != cudaSuccess)
     return fail(fem_fail(FEM_ENOMEM, "fem_mg_create: scalars"));
-  FEM_CUDA(cudaMemset(m->cc, 0, sizeof(CcScalars)));
+  FEM_CUDA(cudaMemset(m->d_stop, 0, sizeof(int)));
   FEM_CUDA(cudaMemset(m->sc, 0, sizeof(MgScalars)));
   if ((st = dev_alloc(&m->w64, (size_t)7 * n0)) != FEM_OK) return fail(st);
   if ((st = dev_alloc(&m->d_never, 1)) != FEM_OK) return fail(st);
@@ -985,13 +982,14 @@ extern "C" fem_status fem_mg_vcycle(fem_mg* m, const double* r, double* z, void*
 
 namespace {
 
-fem_status fcg_iteration(fem_mg* m, double* x, double* r, double* rold, double* z, double* p, double* q,
+// dtype: arithmetic of the outer operator apply (FEM_F64 or FEM_DF64).
+fem_status fcg_iteration(fem_mg* m, int dtype, double* x, double* r, double* rold, double* z, double* p, double* q,
                          cudaStream_t s) {
   const MgLevel& L = m->lv[0];
   const int64_t n = L.n;
   const int nb = m->nb;
   const int* skip = &m->sc->done;
-  FEM_TRY(fem_launch_apply_element(L.f, FEM_F64, p, L.f->d_ye, s, skip));
+  FEM_TRY(fem_launch_apply_element(L.f, dtype, p, L.f->d_ye, s, skip));
   FEM_TRY(fem_launch_scatter(L.f, FEM_F64, L.f->d_ye, q, L.f->d_ess_mask, p, m->part, nb, s, skip));
   k_fg_alpha<<<1, kRed, 0, s>>>(m->sc, m->part, nb);
   k_fg_update<<<nb, 256, 0, s>>>(n, m->sc, x, r, rold, p, q, m->part);
@@ -1027,7 +1025,11 @@ extern "C" fem_status fem_mg_solve(fem_mg* m, const double* b, double* xio, cons
   fem_solve_opts_default(&o);
   if (opts) o = *opts;
   if (!(o.rtol > 0) || o.maxit <= 0) return fem_fail(FEM_EINVAL, "fem_mg_solve: rtol > 0 and maxit > 0 required");
+  if (o.precision != FEM_SOLVE_F64 && o.precision != FEM_SOLVE_DF64)
+    return fem_fail(FEM_EINVAL, "fem_mg_solve: precision must be FEM_SOLVE_F64 or FEM_SOLVE_DF64");
+  const int dtype = o.precision == FEM_SOLVE_DF64 ? FEM_DF64 : FEM_F64;
   cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == FEM_DF64) FEM_TRY(fem_form_ensure_df64(m->lv[0].f, s));
   const MgLevel& L = m->lv[0];
   const int64_t n = L.n;
   const int nb = m->nb;
@@ -1088,7 +1090,7 @@ extern "C" fem_status fem_mg_solve(fem_mg* m, const double* b, double* xio, cons
       if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         st = fem_fail(FEM_ECUDA, "fem_mg_solve: capture failed to begin");
       } else {
-        for (int i = 0; i < k && st == FEM_OK; ++i) st = fcg_iteration(m, x, r, rold, z, p, q, cs);
+        for (int i = 0; i < k && st == FEM_OK; ++i) st = fcg_iteration(m, dtype, x, r, rold, z, p, q, cs);
         const cudaError_t e = cudaStreamEndCapture(cs, &g);
         if (st == FEM_OK && e != cudaSuccess) st = fem_fail(FEM_ECUDA, "fem_mg_solve: end capture failed");
       }
@@ -1108,7 +1110,7 @@ extern "C" fem_status fem_mg_solve(fem_mg* m, const double* b, double* xio, cons
       if (exec) {
         if (cudaGraphLaunch(exec, s) != cudaSuccess) st = fem_fail(FEM_ECUDA, "fem_mg_solve: graph launch failed");
       } else {
-        for (int i = 0; i < k && st == FEM_OK; ++i) st = fcg_iteration(m, x, r, rold, z, p, q, s);
+        for (int i = 0; i < k && st == FEM_OK; ++i) st = fcg_iteration(m, dtype, x, r, rold, z, p, q, s);
       }
       if (st == FEM_OK) st = read_words(m, &m->sc->it, sizeof words, words, s);
       if (st == FEM_OK && words[1]) break;

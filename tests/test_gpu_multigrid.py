@@ -147,6 +147,26 @@ def test_solve(p, N, face_only, precision):
     assert info["iterations"] * 4 < ij["iterations"]
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_solve_double_float_outer(precision):
+    """arith='df64': the outer operator in double-float; same stopping rule
+    on the FP64 true residual, iteration count within one of FP64."""
+    import torch
+    M, G, form, fine, ess, keep = _setup(4, 3, precision=precision)
+    bvec = x_uniform(31, fine.ndof)
+    bc = torch.empty(fine.ndof, dtype=torch.float64, device="cuda")
+    form.lift_rhs(cuda(bvec), torch.zeros_like(bc), bc)
+    x64, xdf = torch.zeros_like(bc), torch.zeros_like(bc)
+    i64 = G.solve(bc, x64, rtol=1e-10)
+    idf = G.solve(bc, xdf, rtol=1e-10, arith="df64")
+    assert idf["converged"] and abs(idf["iterations"] - i64["iterations"]) <= 1
+    bco = osolve.constrain_rhs(fine.K, bvec, ess)
+    u = xdf.cpu().numpy()
+    assert np.linalg.norm(bco - M.levels[0].A @ u) / np.linalg.norm(bco) <= 1.01e-10
+    with pytest.raises(ValueError):
+        G.solve(bc, xdf, arith="mixed")
+
+
 def test_solve_deterministic_and_graph_free_path():
     import torch
     M, G, form, fine, ess, keep = _setup(4, 3)
