@@ -4,13 +4,12 @@
 #pragma once
 
 // Elements per block for a (Q x Q) thread plane: Q^2 * NE fills whole (or
-// nearly whole) warps (inactive lanes still occupy an issued FP64
-// instruction). The choice per element type and Q comes from measuring both
-// candidates of every order on GB300 (p = 1..8, q = p + 2, ~4e6 DOFs): the
-// FP64 kernels keep the larger blocks (more warps hide the FP64 pipe's
-// latency), the FP32 kernels run faster with smaller blocks for Q >= 6 (more
-// independent blocks in flight on their memory latency), and double-float
-// prefers the smaller block at Q = 3, 5, 8, 9.
+// nearly whole) warps, and the stages with fewer lines pack the lines of all
+// NE elements onto full warps. The choice per element type and Q comes from
+// measuring both candidates of every order on GB300 (p = 1..8, q = p + 2,
+// ~4e6 DOFs, block-packed stages): FP64 takes the larger block except at
+// Q = 5, 10; FP32 the smaller one from Q = 5 on (more independent blocks in
+// flight on its memory latency); double-float the smaller one at Q = 3, 5, 8.
 constexpr int ne_large(int Q) {
   return Q <= 3 ? 32 : Q == 4 ? 16 : Q == 5 ? 5 : Q == 6 ? 8 : Q == 7 ? 5 : Q == 8 ? 4 : 3;
 }
@@ -27,9 +26,9 @@ constexpr int ne_for(int Q) {
 #elif defined(FEM_NE_TABLE) && FEM_NE_TABLE == 2
   return ne_small(Q);
 #endif
-  if (std::is_same<T, float>::value) return Q >= 6 ? ne_small(Q) : ne_large(Q);
-  if (std::is_same<T, double>::value) return Q == 10 ? ne_small(Q) : ne_large(Q);
-  return (Q == 3 || Q == 5 || Q == 8 || Q == 9) ? ne_small(Q) : ne_large(Q);  // double-float
+  if (std::is_same<T, float>::value) return Q >= 5 ? ne_small(Q) : ne_large(Q);
+  if (std::is_same<T, double>::value) return (Q == 5 || Q == 10) ? ne_small(Q) : ne_large(Q);
+  return (Q == 3 || Q == 5 || Q == 8) ? ne_small(Q) : ne_large(Q);  // double-float
 }
 
 // Shared-memory plan of a block: NE element slabs, then (STAGE) the staged D
@@ -63,29 +62,25 @@ template <typename T, int D1, int Q, int NE, typename TX, bool STAGE>
 __global__ void __launch_bounds__(Q * Q * NE)
 k_diffusion_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
                   const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye, int* __restrict__ err) {
-  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
+  constexpr int NQ = Q * Q * Q;
   using BS = BlockSmem<T, D1, Q, NE, 6, STAGE>;
   if (skip && *skip) return;  // a captured solver iteration after convergence
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  const int t = threadIdx.x + Q * threadIdx.y, tz = threadIdx.z;
+  const int tid = threadIdx.x + Q * (threadIdx.y + Q * threadIdx.z);
   const int e0 = blockIdx.x * NE;
   const int nel = min(NE, ne - e0);
-  const int e = e0 + tz;
-  const bool valid = e < ne;
-  const size_t ev = valid ? (size_t)e : 0;
   if constexpr (STAGE) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + BS::slabs + BS::tile);
-    const bool issuer = t == 0 && tz == 0;
+    const bool issuer = tid == 0;
     if (issuer) stage_init(bar);
     __syncthreads();
     const T* tileD = stage_tile<T, 6, NQ>(smem_raw + BS::slabs, bar, Dq, e0, nel, issuer);
-    diffusion_element<T, D1, Q, TX, true>(t, valid, e2l + ev * ND, tileD + (size_t)tz * 6 * NQ, sm + tz * SE, x,
-                                          ye + ev * ND, bar, err);
+    diffusion_block<T, D1, Q, NE, TX, true>(tid, e0, nel, e2l, tileD, sm, x, ye, bar, err);
   } else {
-    if (t == 0 && tz == 0)  // D of the block's elements: read in stage S3, fetch into L2 now
+    if (tid == 0)  // D of the block's elements: read in stage S3, fetch into L2 now
       l2_prefetch_range(Dq + (size_t)e0 * 6 * NQ, sizeof(T) * (size_t)nel * 6 * NQ);
-    diffusion_element<T, D1, Q, TX>(t, valid, e2l + ev * ND, Dq + ev * 6 * NQ, sm + tz * SE, x, ye + ev * ND);
+    diffusion_block<T, D1, Q, NE, TX>(tid, e0, nel, e2l, Dq, sm, x, ye);
   }
 }
 
@@ -93,28 +88,24 @@ template <typename T, int D1, int Q, int NE, typename TX, bool STAGE>
 __global__ void __launch_bounds__(Q * Q * NE)
 k_mass_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
              const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye, int* __restrict__ err) {
-  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
+  constexpr int NQ = Q * Q * Q;
   using BS = BlockSmem<T, D1, Q, NE, 1, STAGE>;
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  const int t = threadIdx.x + Q * threadIdx.y, tz = threadIdx.z;
+  const int tid = threadIdx.x + Q * (threadIdx.y + Q * threadIdx.z);
   const int e0 = blockIdx.x * NE;
   const int nel = min(NE, ne - e0);
-  const int e = e0 + tz;
-  const bool valid = e < ne;
-  const size_t ev = valid ? (size_t)e : 0;
   if constexpr (STAGE) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + BS::slabs + BS::tile);
-    const bool issuer = t == 0 && tz == 0;
+    const bool issuer = tid == 0;
     if (issuer) stage_init(bar);
     __syncthreads();
     const T* tileD = stage_tile<T, 1, NQ>(smem_raw + BS::slabs, bar, Dq, e0, nel, issuer);
-    mass_element<T, D1, Q, TX, true>(t, valid, e2l + ev * ND, tileD + (size_t)tz * NQ, sm + tz * SE, x,
-                                     ye + ev * ND, bar, err);
+    mass_block<T, D1, Q, NE, TX, true>(tid, e0, nel, e2l, tileD, sm, x, ye, bar, err);
   } else {
-    if (t == 0 && tz == 0) l2_prefetch_range(Dq + (size_t)e0 * NQ, sizeof(T) * (size_t)nel * NQ);
-    mass_element<T, D1, Q, TX>(t, valid, e2l + ev * ND, Dq + ev * NQ, sm + tz * SE, x, ye + ev * ND);
+    if (tid == 0) l2_prefetch_range(Dq + (size_t)e0 * NQ, sizeof(T) * (size_t)nel * NQ);
+    mass_block<T, D1, Q, NE, TX>(tid, e0, nel, e2l, Dq, sm, x, ye);
   }
 }
 

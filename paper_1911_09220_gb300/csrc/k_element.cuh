@@ -279,72 +279,81 @@ struct ElemSmem {
   static constexpr int SE = SA > SB ? SA : SB;  // per element, in T
 };
 
-// map: the element's DOF list (e2l + e*(p+1)^3); De: its D block
-// (D + e*q^3*6, point-major [q][6]); out: its E-vector slice. Dereferenced only when
-// valid.
-// T: compute type (double, float or df64); TX: type of x and out.
-// DS: De points into a shared-memory tile staged by the caller, who passes
-// its barrier as bar (waited on before the tile is read) and an error word.
-template <typename T, int D1, int Q, typename TX = T, bool DS = false>
-__device__ __forceinline__ void diffusion_element(int t, bool valid, const int32_t* __restrict__ map,
-                                                  const T* __restrict__ De, T* s, const TX* __restrict__ x,
-                                                  TX* __restrict__ out, uint64_t* bar = nullptr,
-                                                  int* err = nullptr) {
+// ------------------------------------------------------ stage bodies ----
+// One line of one stage on the slab s of one element (ElemSmem layout). The
+// drivers below decide which thread runs which line of which element.
+template <typename T, int D1, int Q>
+struct Lines {
   using L = ElemSmem<T, D1, Q>;
-  constexpr int QQ = Q * Q, XP = L::XP, RB = L::RB, RC = L::RC, RT = L::RT, RU = L::RU;
-  constexpr int BF = eo_off(D1, Q, 0), GF = eo_off(D1, Q, 1), BT = eo_off(D1, Q, 2), GT = eo_off(D1, Q, 3);
-  constexpr int cD = (D1 + 1) / 2, hD = D1 / 2 > 0 ? D1 / 2 : 1;
-  T* sX = s;                                // [z][y][XP] (region 0 until S1 ends)
-  T* sBX = s + L::R0;                       // [qx][RB], column z*D1 + y
-  T* sGX = sBX + Q * RB;
-  T* sBB = s;                               // [qy][RC], column z*Q + qx (region 0 from S2)
-  T* sGB = sBB + Q * RC;
-  T* sBG = sGB + Q * RC;
-  gather_x<T, D1, Q, TX>(t, valid, map, x, sX, XP);
-  __syncthreads();
-  if (t < D1 * D1) {  // S1: line (z, y) along x
+  static constexpr int QQ = Q * Q, XP = L::XP, RB = L::RB, RC = L::RC, RT = L::RT, RU = L::RU;
+  static constexpr int BF = eo_off(D1, Q, 0), GF = eo_off(D1, Q, 1), BT = eo_off(D1, Q, 2), GT = eo_off(D1, Q, 3);
+  static constexpr int cD = (D1 + 1) / 2, hD = D1 / 2 > 0 ? D1 / 2 : 1;
+  // phase A: X (region 0 until S1 ends), BB/GB/BG (region 0 from S2), BX/GX (region 1)
+  __device__ static T* X(T* s) { return s; }
+  __device__ static T* BX(T* s) { return s + L::R0; }
+  __device__ static T* GX(T* s) { return s + L::R0 + Q * RB; }
+  __device__ static T* BB(T* s) { return s; }
+  __device__ static T* GB(T* s) { return s + Q * RC; }
+  __device__ static T* BG(T* s) { return s + 2 * Q * RC; }
+  // phase B
+  __device__ static T* T0(T* s) { return s; }
+  __device__ static T* T1(T* s) { return s + D1 * RT; }
+  __device__ static T* T2(T* s) { return s + 2 * D1 * RT; }
+  __device__ static T* UA(T* s) { return s + 3 * D1 * RT; }
+  __device__ static T* UB(T* s) { return s + 3 * D1 * RT + D1 * RU; }
+
+  // ---- diffusion
+  // S1: line t = (z, y) along x -> BX, GX [qx][RB], column t
+  __device__ static void d1(int t, T* s) {
     T xr[D1], e[cD], o[hD], bx[Q], gx[Q];
+    const T* sx = X(s) + t * XP;
 #pragma unroll
-    for (int d = 0; d < D1; ++d) xr[d] = sX[t * XP + d];
+    for (int d = 0; d < D1; ++d) xr[d] = sx[d];
     eo_split<T, D1>(xr, e, o);
     eo_apply<T, Q, D1, 1, BF>(e, o, bx);
     eo_apply<T, Q, D1, -1, GF>(e, o, gx);
+    T *sb = BX(s), *sg = GX(s);
 #pragma unroll
     for (int qx = 0; qx < Q; ++qx) {
-      sBX[qx * RB + t] = bx[qx];
-      sGX[qx * RB + t] = gx[qx];
+      sb[qx * RB + t] = bx[qx];
+      sg[qx * RB + t] = gx[qx];
     }
   }
-  __syncthreads();
-  if (t < D1 * Q) {  // S2: line (z, qx) along y
+  // S2: line t = (z, qx) along y -> BB, GB, BG [qy][RC], column t
+  __device__ static void d2(int t, T* s) {
     const int z = t / Q, qx = t % Q;
     T br[D1], gr[D1], e[cD], o[hD], bb[Q], bg[Q], gb[Q];
+    const T *sb = BX(s) + qx * RB + z * D1, *sg = GX(s) + qx * RB + z * D1;
 #pragma unroll
     for (int d = 0; d < D1; ++d) {
-      br[d] = sBX[qx * RB + z * D1 + d];
-      gr[d] = sGX[qx * RB + z * D1 + d];
+      br[d] = sb[d];
+      gr[d] = sg[d];
     }
     eo_split<T, D1>(br, e, o);
     eo_apply<T, Q, D1, 1, BF>(e, o, bb);
     eo_apply<T, Q, D1, -1, GF>(e, o, bg);
     eo_line<T, Q, D1, 1, BF>(gr, gb);
+    T *o0 = BB(s), *o1 = GB(s), *o2 = BG(s);
 #pragma unroll
     for (int qy = 0; qy < Q; ++qy) {
-      sBB[qy * RC + t] = bb[qy];
-      sGB[qy * RC + t] = gb[qy];
-      sBG[qy * RC + t] = bg[qy];
+      o0[qy * RC + t] = bb[qy];
+      o1[qy * RC + t] = gb[qy];
+      o2[qy * RC + t] = bg[qy];
     }
   }
-  __syncthreads();
-  T t0[D1], t1[D1], t2[D1];
-  if (t < QQ) {  // S3: line (qy, qx) along z, D at every point, back along z
+  // S3: line t = (qy, qx) along z, D at every point, back along z; results
+  // stay in registers until phase A is dead
+  template <bool DS>
+  __device__ static void d3(int t, bool valid, const T* __restrict__ De, T* s, T* t0, T* t1, T* t2, uint64_t* bar,
+                            int* err) {
     const int qy = t / Q, qx = t % Q;
     T rbb[D1], rgb[D1], rbg[D1], g0[Q], g1[Q], g2[Q];
+    const T *sbb = BB(s) + qy * RC + qx, *sgb = GB(s) + qy * RC + qx, *sbg = BG(s) + qy * RC + qx;
 #pragma unroll
     for (int z = 0; z < D1; ++z) {
-      rbb[z] = sBB[qy * RC + z * Q + qx];
-      rgb[z] = sGB[qy * RC + z * Q + qx];
-      rbg[z] = sBG[qy * RC + z * Q + qx];
+      rbb[z] = sbb[z * Q];
+      rgb[z] = sgb[z * Q];
+      rbg[z] = sbg[z * Q];
     }
     eo_line<T, Q, D1, 1, BF>(rgb, g0);
     eo_line<T, Q, D1, 1, BF>(rbg, g1);
@@ -370,127 +379,232 @@ __device__ __forceinline__ void diffusion_element(int t, bool valid, const int32
     eo_line<T, D1, Q, 1, BT>(g1, t1);
     eo_line<T, D1, Q, -1, GT>(g2, t2);
   }
-  __syncthreads();  // phase-A arrays are dead from here on
-  T* sT0 = s;                               // [dz][RT], column qy*Q + qx
-  T* sT1 = sT0 + D1 * RT;
-  T* sT2 = sT1 + D1 * RT;
-  T* sUA = sT2 + D1 * RT;                   // [dy][RU], column dz*Q + qx
-  T* sUB = sUA + D1 * RU;
-  if (t < QQ) {
+  __device__ static void d3_store(int t, T* s, const T* t0, const T* t1, const T* t2) {
+    T *a = T0(s), *b = T1(s), *c = T2(s);
 #pragma unroll
     for (int d = 0; d < D1; ++d) {
-      sT0[d * RT + t] = t0[d];
-      sT1[d * RT + t] = t1[d];
-      sT2[d * RT + t] = t2[d];
+      a[d * RT + t] = t0[d];
+      b[d * RT + t] = t1[d];
+      c[d * RT + t] = t2[d];
     }
   }
-  __syncthreads();
-  if (t < D1 * Q) {  // S4: line (dz, qx) along qy
+  // S4: line t = (dz, qx) along qy -> UA, UB [dy][RU], column t
+  __device__ static void d4(int t, T* s) {
     const int dz = t / Q, qx = t % Q;
     T a0[Q], a1[Q], a2[Q], ua[D1], u1[D1], u2[D1];
+    const T *s0 = T0(s) + dz * RT + qx, *s1 = T1(s) + dz * RT + qx, *s2 = T2(s) + dz * RT + qx;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const int o2 = dz * RT + q * Q + qx;
-      a0[q] = sT0[o2];
-      a1[q] = sT1[o2];
-      a2[q] = sT2[o2];
+      a0[q] = s0[q * Q];
+      a1[q] = s1[q * Q];
+      a2[q] = s2[q * Q];
     }
     eo_line<T, D1, Q, 1, BT>(a0, ua);
     eo_line<T, D1, Q, -1, GT>(a1, u1);
     eo_line<T, D1, Q, 1, BT>(a2, u2);
+    T *oa = UA(s), *ob = UB(s);
 #pragma unroll
     for (int dy = 0; dy < D1; ++dy) {
-      sUA[dy * RU + t] = ua[dy];
-      sUB[dy * RU + t] = fe_norm(u1[dy] + u2[dy]);
+      oa[dy * RU + t] = ua[dy];
+      ob[dy * RU + t] = fe_norm(u1[dy] + u2[dy]);
     }
   }
-  __syncthreads();
-  if (valid && t < D1 * D1) {  // S5: line (dz, dy) along qx
+  // S5: line t = (dz, dy) along qx -> out[t * D1 + dx]
+  template <typename TX>
+  __device__ static void d5(int t, T* s, TX* __restrict__ out) {
     const int dz = t / D1, dy = t % D1;
     T ua[Q], ub[Q], y1[D1], y2[D1];
+    const T *sa = UA(s) + dy * RU + dz * Q, *sb = UB(s) + dy * RU + dz * Q;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      ua[q] = sUA[dy * RU + dz * Q + q];
-      ub[q] = sUB[dy * RU + dz * Q + q];
+      ua[q] = sa[q];
+      ub[q] = sb[q];
     }
     eo_line<T, D1, Q, -1, GT>(ua, y1);
     eo_line<T, D1, Q, 1, BT>(ub, y2);
 #pragma unroll
     for (int dx = 0; dx < D1; ++dx) fe_store(&out[t * D1 + dx], y1[dx] + y2[dx]);
   }
-}
 
-// Mass: the same lines with B only and one scalar D per point
-// (Sec. 4.4, M_E = B^T D_E B). De: the element's D block (D + e*q^3).
-template <typename T, int D1, int Q, typename TX = T, bool DS = false>
-__device__ __forceinline__ void mass_element(int t, bool valid, const int32_t* __restrict__ map,
-                                             const T* __restrict__ De, T* s, const TX* __restrict__ x,
-                                             TX* __restrict__ out, uint64_t* bar = nullptr, int* err = nullptr) {
-  using L = ElemSmem<T, D1, Q>;
-  constexpr int QQ = Q * Q, XP = L::XP, RB = L::RB, RC = L::RC, RT = L::RT, RU = L::RU;
-  constexpr int BF = eo_off(D1, Q, 0), BT = eo_off(D1, Q, 2);
-  T* sX = s;                   // region 0 until S1 ends
-  T* sBX = s + L::R0;          // [qx][RB]
-  T* sBB = s;                  // [qy][RC], region 0 from S2
-  gather_x<T, D1, Q, TX>(t, valid, map, x, sX, XP);
-  __syncthreads();
-  if (t < D1 * D1) {
+  // ---- mass (B only, one D per point)
+  __device__ static void m1(int t, T* s) {
     T xr[D1], bx[Q];
+    const T* sx = X(s) + t * XP;
 #pragma unroll
-    for (int d = 0; d < D1; ++d) xr[d] = sX[t * XP + d];
+    for (int d = 0; d < D1; ++d) xr[d] = sx[d];
     eo_line<T, Q, D1, 1, BF>(xr, bx);
+    T* sb = BX(s);
 #pragma unroll
-    for (int qx = 0; qx < Q; ++qx) sBX[qx * RB + t] = bx[qx];
+    for (int qx = 0; qx < Q; ++qx) sb[qx * RB + t] = bx[qx];
   }
-  __syncthreads();
-  if (t < D1 * Q) {
+  __device__ static void m2(int t, T* s) {
     const int z = t / Q, qx = t % Q;
     T br[D1], bb[Q];
+    const T* sb = BX(s) + qx * RB + z * D1;
 #pragma unroll
-    for (int d = 0; d < D1; ++d) br[d] = sBX[qx * RB + z * D1 + d];
+    for (int d = 0; d < D1; ++d) br[d] = sb[d];
     eo_line<T, Q, D1, 1, BF>(br, bb);
+    T* o = BB(s);
 #pragma unroll
-    for (int qy = 0; qy < Q; ++qy) sBB[qy * RC + t] = bb[qy];
+    for (int qy = 0; qy < Q; ++qy) o[qy * RC + t] = bb[qy];
   }
-  __syncthreads();
-  T t0[D1];
-  if (t < QQ) {
+  template <bool DS>
+  __device__ static void m3(int t, bool valid, const T* __restrict__ De, T* s, T* t0, uint64_t* bar, int* err) {
     const int qy = t / Q, qx = t % Q;
     T rbb[D1], u[Q];
+    const T* sbb = BB(s) + qy * RC + qx;
 #pragma unroll
-    for (int z = 0; z < D1; ++z) rbb[z] = sBB[qy * RC + z * Q + qx];
+    for (int z = 0; z < D1; ++z) rbb[z] = sbb[z * Q];
     eo_line<T, Q, D1, 1, BF>(rbb, u);
     if (DS) stage_wait(bar, err);
 #pragma unroll
     for (int qz = 0; qz < Q; ++qz) u[qz] = valid ? fe_norm(d_load<DS>(De + t + qz * QQ) * u[qz]) : T(0);
     eo_line<T, D1, Q, 1, BT>(u, t0);
   }
-  __syncthreads();
-  T* sT0 = s;                  // [dz][RT]
-  T* sUA = sT0 + D1 * RT;      // [dy][RU]
-  if (t < QQ) {
+  __device__ static void m3_store(int t, T* s, const T* t0) {
+    T* a = T0(s);
 #pragma unroll
-    for (int d = 0; d < D1; ++d) sT0[d * RT + t] = t0[d];
+    for (int d = 0; d < D1; ++d) a[d * RT + t] = t0[d];
   }
-  __syncthreads();
-  if (t < D1 * Q) {
+  __device__ static void m4(int t, T* s) {
     const int dz = t / Q, qx = t % Q;
     T a0[Q], ua[D1];
+    const T* s0 = T0(s) + dz * RT + qx;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) a0[q] = sT0[dz * RT + q * Q + qx];
+    for (int q = 0; q < Q; ++q) a0[q] = s0[q * Q];
     eo_line<T, D1, Q, 1, BT>(a0, ua);
+    T* oa = UA(s);
 #pragma unroll
-    for (int dy = 0; dy < D1; ++dy) sUA[dy * RU + t] = ua[dy];
+    for (int dy = 0; dy < D1; ++dy) oa[dy * RU + t] = ua[dy];
   }
-  __syncthreads();
-  if (valid && t < D1 * D1) {
+  template <typename TX>
+  __device__ static void m5(int t, T* s, TX* __restrict__ out) {
     const int dz = t / D1, dy = t % D1;
     T ua[Q], y[D1];
+    const T* sa = UA(s) + dy * RU + dz * Q;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) ua[q] = sUA[dy * RU + dz * Q + q];
+    for (int q = 0; q < Q; ++q) ua[q] = sa[q];
     eo_line<T, D1, Q, 1, BT>(ua, y);
 #pragma unroll
     for (int dx = 0; dx < D1; ++dx) fe_store(&out[t * D1 + dx], y[dx]);
+  }
+};
+
+// ------------------------------------------------------------- drivers ----
+// Per element: a plane of Q*Q threads (index t) runs every stage of its own
+// element (map, De, out: that element's DOF list, D block and E-vector
+// slice, dereferenced only when valid). Used by the persistent batched
+// kernel.
+template <typename T, int D1, int Q, typename TX = T, bool DS = false>
+__device__ __forceinline__ void diffusion_element(int t, bool valid, const int32_t* __restrict__ map,
+                                                  const T* __restrict__ De, T* s, const TX* __restrict__ x,
+                                                  TX* __restrict__ out, uint64_t* bar = nullptr,
+                                                  int* err = nullptr) {
+  using Ln = Lines<T, D1, Q>;
+  constexpr int QQ = Q * Q;
+  gather_x<T, D1, Q, TX>(t, valid, map, x, Ln::X(s), Ln::XP);
+  __syncthreads();
+  if (t < D1 * D1) Ln::d1(t, s);
+  __syncthreads();
+  if (t < D1 * Q) Ln::d2(t, s);
+  __syncthreads();
+  T t0[D1], t1[D1], t2[D1];
+  if (t < QQ) Ln::template d3<DS>(t, valid, De, s, t0, t1, t2, bar, err);
+  __syncthreads();  // phase-A arrays are dead from here on
+  if (t < QQ) Ln::d3_store(t, s, t0, t1, t2);
+  __syncthreads();
+  if (t < D1 * Q) Ln::d4(t, s);
+  __syncthreads();
+  if (valid && t < D1 * D1) Ln::template d5<TX>(t, s, out);
+}
+
+template <typename T, int D1, int Q, typename TX = T, bool DS = false>
+__device__ __forceinline__ void mass_element(int t, bool valid, const int32_t* __restrict__ map,
+                                             const T* __restrict__ De, T* s, const TX* __restrict__ x,
+                                             TX* __restrict__ out, uint64_t* bar = nullptr, int* err = nullptr) {
+  using Ln = Lines<T, D1, Q>;
+  constexpr int QQ = Q * Q;
+  gather_x<T, D1, Q, TX>(t, valid, map, x, Ln::X(s), Ln::XP);
+  __syncthreads();
+  if (t < D1 * D1) Ln::m1(t, s);
+  __syncthreads();
+  if (t < D1 * Q) Ln::m2(t, s);
+  __syncthreads();
+  T t0[D1];
+  if (t < QQ) Ln::template m3<DS>(t, valid, De, s, t0, bar, err);
+  __syncthreads();
+  if (t < QQ) Ln::m3_store(t, s, t0);
+  __syncthreads();
+  if (t < D1 * Q) Ln::m4(t, s);
+  __syncthreads();
+  if (valid && t < D1 * D1) Ln::template m5<TX>(t, s, out);
+}
+
+// Per block of NE elements (e0 .. e0 + nel - 1): the gather and stage S3
+// (which have Q*Q lines per element) keep one plane per element, thread tid
+// = el * Q*Q + t; the stages with fewer lines (S1, S5: D1^2; S2, S4: D1*Q)
+// pack the lines of all the block's elements onto the lowest thread ids, so
+// warps are full and the arithmetic pipe issues no instructions for idle
+// lanes. Element e's DOF list is e2l + e*D1^3, its D block Dq + e*NC*Q^3
+// (NC = 6 diffusion, 1 mass), its E-vector slice ye + e*D1^3; its slab
+// sm + el*SE.
+template <typename T, int D1, int Q, int NE, typename TX = T, bool DS = false>
+__device__ __forceinline__ void diffusion_block(int tid, int e0, int nel, const int32_t* __restrict__ e2l,
+                                                const T* __restrict__ Dq, T* sm, const TX* __restrict__ x,
+                                                TX* __restrict__ ye, uint64_t* bar = nullptr, int* err = nullptr) {
+  using Ln = Lines<T, D1, Q>;
+  constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
+  constexpr int N1 = D1 * D1, N2 = D1 * Q;
+  const int el = tid / QQ, t = tid % QQ;
+  const bool valid = el < nel;
+  const size_t ev = valid ? (size_t)(e0 + el) : 0;
+  gather_x<T, D1, Q, TX>(t, valid, e2l + ev * ND, x, Ln::X(sm + el * SE), Ln::XP);
+  __syncthreads();
+  if (tid < NE * N1) Ln::d1(tid % N1, sm + (tid / N1) * SE);
+  __syncthreads();
+  if (tid < NE * N2) Ln::d2(tid % N2, sm + (tid / N2) * SE);
+  __syncthreads();
+  T t0[D1], t1[D1], t2[D1];
+  const T* De = DS ? Dq + (size_t)el * 6 * NQ : Dq + ev * 6 * NQ;
+  Ln::template d3<DS>(t, valid, De, sm + el * SE, t0, t1, t2, bar, err);
+  __syncthreads();
+  Ln::d3_store(t, sm + el * SE, t0, t1, t2);
+  __syncthreads();
+  if (tid < NE * N2) Ln::d4(tid % N2, sm + (tid / N2) * SE);
+  __syncthreads();
+  if (tid < NE * N1) {
+    const int el5 = tid / N1;
+    if (el5 < nel) Ln::template d5<TX>(tid % N1, sm + el5 * SE, ye + (size_t)(e0 + el5) * ND);
+  }
+}
+
+template <typename T, int D1, int Q, int NE, typename TX = T, bool DS = false>
+__device__ __forceinline__ void mass_block(int tid, int e0, int nel, const int32_t* __restrict__ e2l,
+                                           const T* __restrict__ Dq, T* sm, const TX* __restrict__ x,
+                                           TX* __restrict__ ye, uint64_t* bar = nullptr, int* err = nullptr) {
+  using Ln = Lines<T, D1, Q>;
+  constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
+  constexpr int N1 = D1 * D1, N2 = D1 * Q;
+  const int el = tid / QQ, t = tid % QQ;
+  const bool valid = el < nel;
+  const size_t ev = valid ? (size_t)(e0 + el) : 0;
+  gather_x<T, D1, Q, TX>(t, valid, e2l + ev * ND, x, Ln::X(sm + el * SE), Ln::XP);
+  __syncthreads();
+  if (tid < NE * N1) Ln::m1(tid % N1, sm + (tid / N1) * SE);
+  __syncthreads();
+  if (tid < NE * N2) Ln::m2(tid % N2, sm + (tid / N2) * SE);
+  __syncthreads();
+  T t0[D1];
+  const T* De = DS ? Dq + (size_t)el * NQ : Dq + ev * NQ;
+  Ln::template m3<DS>(t, valid, De, sm + el * SE, t0, bar, err);
+  __syncthreads();
+  Ln::m3_store(t, sm + el * SE, t0);
+  __syncthreads();
+  if (tid < NE * N2) Ln::m4(tid % N2, sm + (tid / N2) * SE);
+  __syncthreads();
+  if (tid < NE * N1) {
+    const int el5 = tid / N1;
+    if (el5 < nel) Ln::template m5<TX>(tid % N1, sm + el5 * SE, ye + (size_t)(e0 + el5) * ND);
   }
 }
 
