@@ -150,22 +150,27 @@ __global__ void __launch_bounds__(Q * NE) k_apply_2d(const int* __restrict__ ski
   using L = Smem2<D1, Q>;
   constexpr int XP = L::XP, YP = L::YP, QP = L::QP, ND = D1 * D1, NQ = Q * Q;
   constexpr int BF = eo_off(D1, Q, 0), GF = eo_off(D1, Q, 1), BT = eo_off(D1, Q, 2), GT = eo_off(D1, Q, 3);
+  // slab offsets: X [y][XP], BX, GX [qx][YP], T0, T1 [dy][QP]
+  constexpr int OBX = D1 * XP, OGX = OBX + Q * YP, OT0 = OGX + Q * YP, OT1 = OT0 + D1 * QP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int t = threadIdx.x, el = threadIdx.y;
-  const int64_t e = (int64_t)blockIdx.x * NE + el;
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int t = threadIdx.x, el = threadIdx.y, tid = t + Q * el;
+  const int64_t e0 = (int64_t)blockIdx.x * NE, e = e0 + el;
+  const int nel = (int)min((int64_t)NE, ne - e0);
   const bool valid = e < ne;
-  T* s = reinterpret_cast<T*>(smem_raw) + el * L::SE;
-  T* sX = s;                   // [y][XP]
-  T* sBX = sX + D1 * XP;       // [qx][YP]
-  T* sGX = sBX + Q * YP;
-  T* sT0 = sGX + Q * YP;       // [dy][QP]
-  T* sT1 = sT0 + D1 * QP;
   if (valid) {
+    T* sX = sm + el * L::SE;
     const int32_t* map = e2l + e * ND;
     for (int k = t; k < ND; k += Q) sX[(k / D1) * XP + k % D1] = fe_from<T>(__ldg(x + __ldg(map + k)));
   }
   __syncthreads();
-  if (t < D1) {  // S1: line y along x
+  // S1 and S3 have D1 lines per element: the lines of all nel elements are
+  // packed onto the lowest thread ids (full warps); S2 has Q lines per
+  // element and keeps one row of Q threads per element.
+  if (tid < nel * D1) {  // S1: line y along x
+    T* s = sm + (tid / D1) * L::SE;
+    const int t = tid % D1;
+    T *sX = s, *sBX = s + OBX, *sGX = s + OGX;
     T xr[D1], bx[Q], gx[Q];
 #pragma unroll
     for (int d = 0; d < D1; ++d) xr[d] = sX[t * XP + d];
@@ -188,6 +193,8 @@ __global__ void __launch_bounds__(Q * NE) k_apply_2d(const int* __restrict__ ski
   __syncthreads();
   {  // S2: line qx along y, D at every point, back along y (t < Q always)
     const int qx = t;
+    T* s = sm + el * L::SE;
+    T *sBX = s + OBX, *sGX = s + OGX, *sT0 = s + OT0, *sT1 = s + OT1;
     T br[D1], t0[D1];
 #pragma unroll
     for (int d = 0; d < D1; ++d) br[d] = sBX[qx * YP + d];
@@ -229,11 +236,14 @@ __global__ void __launch_bounds__(Q * NE) k_apply_2d(const int* __restrict__ ski
     }
   }
   __syncthreads();
-  if (valid && t < D1) {  // S3: line dy along qx
+  if (tid < nel * D1) {  // S3: line dy along qx
+    const int el3 = tid / D1, t = tid % D1;
+    T* s = sm + el3 * L::SE;
+    const T *sT0 = s + OT0, *sT1 = s + OT1;
     T a0[Q], y1[D1];
 #pragma unroll
     for (int q = 0; q < Q; ++q) a0[q] = sT0[t * QP + q];
-    TX* out = ye + e * ND + t * D1;
+    TX* out = ye + (e0 + el3) * ND + t * D1;
     if constexpr (DIFF) {
       T a1[Q], y2[D1];
 #pragma unroll

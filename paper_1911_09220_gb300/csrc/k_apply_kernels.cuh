@@ -76,11 +76,11 @@ k_diffusion_apply(const int* __restrict__ skip, int ne, const int32_t* __restric
     if (issuer) stage_init(bar);
     __syncthreads();
     const T* tileD = stage_tile<T, 6, NQ>(smem_raw + BS::slabs, bar, Dq, e0, nel, issuer);
-    diffusion_block<T, D1, Q, NE, TX, true>(tid, e0, nel, e2l, tileD, sm, x, ye, bar, err);
+    diffusion_block<T, D1, Q, TX, true>(tid, e0, nel, e2l, tileD, sm, x, ye, bar, err);
   } else {
     if (tid == 0)  // D of the block's elements: read in stage S3, fetch into L2 now
       l2_prefetch_range(Dq + (size_t)e0 * 6 * NQ, sizeof(T) * (size_t)nel * 6 * NQ);
-    diffusion_block<T, D1, Q, NE, TX>(tid, e0, nel, e2l, Dq, sm, x, ye);
+    diffusion_block<T, D1, Q, TX>(tid, e0, nel, e2l, Dq, sm, x, ye);
   }
 }
 
@@ -102,10 +102,10 @@ k_mass_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e
     if (issuer) stage_init(bar);
     __syncthreads();
     const T* tileD = stage_tile<T, 1, NQ>(smem_raw + BS::slabs, bar, Dq, e0, nel, issuer);
-    mass_block<T, D1, Q, NE, TX, true>(tid, e0, nel, e2l, tileD, sm, x, ye, bar, err);
+    mass_block<T, D1, Q, TX, true>(tid, e0, nel, e2l, tileD, sm, x, ye, bar, err);
   } else {
     if (tid == 0) l2_prefetch_range(Dq + (size_t)e0 * NQ, sizeof(T) * (size_t)nel * NQ);
-    mass_block<T, D1, Q, NE, TX>(tid, e0, nel, e2l, Dq, sm, x, ye);
+    mass_block<T, D1, Q, TX>(tid, e0, nel, e2l, Dq, sm, x, ye);
   }
 }
 

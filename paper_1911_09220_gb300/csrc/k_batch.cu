@@ -76,22 +76,18 @@ __host__ __device__ constexpr int planes_for(int Q) { return (kBT + Q * Q - 1) /
 template <typename T, int D1, int Q>
 __device__ __noinline__ void run_tile(const BProb& P, int e0, int tile, int nrhs, const int* __restrict__ done,
                                       const T* __restrict__ X, T* __restrict__ YE, T* sm) {
-  constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
+  constexpr int ND = D1 * D1 * D1;
   const int tid = threadIdx.x;
-  const int t = tid % (Q * Q), tz = tid / (Q * Q);
-  const int e = e0 + tz;
-  const bool valid = tz < tile && e < P.ne;
-  const size_t ev = valid ? (size_t)e : 0;
+  const int nel = min(tile, P.ne - e0);  // tile <= floor(256 / Q^2): whole planes
   const T* D = D_of<T>(P);
-  T* slab = sm + tz * SE;
   for (int r = 0; r < nrhs; ++r) {
     if (done && done[P.sys0 + r]) continue;  // uniform over the block
     const T* x = X + P.xoff + (int64_t)r * P.ndof;
-    T* ye = YE + P.yeoff + ((int64_t)r * P.ne + ev) * ND;
+    T* ye = YE + P.yeoff + (int64_t)r * P.ne * ND;
     if (P.kind == FEM_DIFFUSION)
-      diffusion_element<T, D1, Q>(t, valid, P.e2l + ev * ND, D + ev * 6 * NQ, slab, x, ye);
+      diffusion_block<T, D1, Q>(tid, e0, nel, P.e2l, D, sm, x, ye);
     else
-      mass_element<T, D1, Q>(t, valid, P.e2l + ev * ND, D + ev * NQ, slab, x, ye);
+      mass_block<T, D1, Q>(tid, e0, nel, P.e2l, D, sm, x, ye);
   }
 }
 

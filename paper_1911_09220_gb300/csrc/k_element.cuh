@@ -5,8 +5,9 @@
 // evaluator applied one direction at a time (Sec. 4.4: B_ki = B1d_{k1 i1}
 // B1d_{k2 i2} B1d_{k3 i3}, O(p^{d+1}) operations per element).
 //
-// One element is handled by a plane of Q*Q threads (index t). Every
-// contraction stage gives each active thread one *line* of its input tensor:
+// Every contraction stage gives each active thread one *line* of its input
+// tensor (the drivers at the end of this file decide which thread runs
+// which line of which element):
 // the thread reads the line (K values) from shared memory into registers and
 // produces every output of that line (M values), so each loaded value feeds
 // many FMAs. Each line goes through the even-odd (folded) form of its 1D
@@ -26,9 +27,9 @@
 // stage's read pattern (ElemSmem below), so that neither side of a stage
 // boundary replays for bank conflicts.
 //
-// Every thread of the block must call these functions the same number of
-// times (they contain __syncthreads); a plane without an element passes
-// valid = false and still owns an in-bounds slab of ElemSmem<T,D1,Q>::SE values.
+// Every thread of the block must call the drivers the same number of times
+// (they contain __syncthreads); a plane without an element passes valid =
+// false and still owns an in-bounds slab of ElemSmem<T,D1,Q>::SE values.
 #pragma once
 
 #include <stdint.h>
@@ -491,64 +492,18 @@ struct Lines {
 };
 
 // ------------------------------------------------------------- drivers ----
-// Per element: a plane of Q*Q threads (index t) runs every stage of its own
-// element (map, De, out: that element's DOF list, D block and E-vector
-// slice, dereferenced only when valid). Used by the persistent batched
-// kernel.
+// A block works on elements e0 .. e0 + nel - 1. The gather and stage S3
+// (Q*Q lines per element) keep one plane of Q*Q threads per element, thread
+// tid = el * Q*Q + t (threads of planes el >= nel take part with valid =
+// false; the block needs a slab for every plane it has); the stages with
+// fewer lines (S1, S5: D1^2; S2, S4: D1*Q) pack the lines of the nel
+// elements onto the lowest thread ids, so warps are full and the arithmetic
+// pipe issues no instructions for idle lanes. Element e's DOF list is
+// e2l + e*D1^3, its D block Dq + e*NC*Q^3 (NC = 6 diffusion, 1 mass; with
+// DS, Dq is the block's staged tile and element el's block starts at
+// el*NC*Q^3), its E-vector slice ye + e*D1^3; its slab sm + el*SE. Every
+// thread of the block must call the driver (it contains __syncthreads).
 template <typename T, int D1, int Q, typename TX = T, bool DS = false>
-__device__ __forceinline__ void diffusion_element(int t, bool valid, const int32_t* __restrict__ map,
-                                                  const T* __restrict__ De, T* s, const TX* __restrict__ x,
-                                                  TX* __restrict__ out, uint64_t* bar = nullptr,
-                                                  int* err = nullptr) {
-  using Ln = Lines<T, D1, Q>;
-  constexpr int QQ = Q * Q;
-  gather_x<T, D1, Q, TX>(t, valid, map, x, Ln::X(s), Ln::XP);
-  __syncthreads();
-  if (t < D1 * D1) Ln::d1(t, s);
-  __syncthreads();
-  if (t < D1 * Q) Ln::d2(t, s);
-  __syncthreads();
-  T t0[D1], t1[D1], t2[D1];
-  if (t < QQ) Ln::template d3<DS>(t, valid, De, s, t0, t1, t2, bar, err);
-  __syncthreads();  // phase-A arrays are dead from here on
-  if (t < QQ) Ln::d3_store(t, s, t0, t1, t2);
-  __syncthreads();
-  if (t < D1 * Q) Ln::d4(t, s);
-  __syncthreads();
-  if (valid && t < D1 * D1) Ln::template d5<TX>(t, s, out);
-}
-
-template <typename T, int D1, int Q, typename TX = T, bool DS = false>
-__device__ __forceinline__ void mass_element(int t, bool valid, const int32_t* __restrict__ map,
-                                             const T* __restrict__ De, T* s, const TX* __restrict__ x,
-                                             TX* __restrict__ out, uint64_t* bar = nullptr, int* err = nullptr) {
-  using Ln = Lines<T, D1, Q>;
-  constexpr int QQ = Q * Q;
-  gather_x<T, D1, Q, TX>(t, valid, map, x, Ln::X(s), Ln::XP);
-  __syncthreads();
-  if (t < D1 * D1) Ln::m1(t, s);
-  __syncthreads();
-  if (t < D1 * Q) Ln::m2(t, s);
-  __syncthreads();
-  T t0[D1];
-  if (t < QQ) Ln::template m3<DS>(t, valid, De, s, t0, bar, err);
-  __syncthreads();
-  if (t < QQ) Ln::m3_store(t, s, t0);
-  __syncthreads();
-  if (t < D1 * Q) Ln::m4(t, s);
-  __syncthreads();
-  if (valid && t < D1 * D1) Ln::template m5<TX>(t, s, out);
-}
-
-// Per block of NE elements (e0 .. e0 + nel - 1): the gather and stage S3
-// (which have Q*Q lines per element) keep one plane per element, thread tid
-// = el * Q*Q + t; the stages with fewer lines (S1, S5: D1^2; S2, S4: D1*Q)
-// pack the lines of all the block's elements onto the lowest thread ids, so
-// warps are full and the arithmetic pipe issues no instructions for idle
-// lanes. Element e's DOF list is e2l + e*D1^3, its D block Dq + e*NC*Q^3
-// (NC = 6 diffusion, 1 mass), its E-vector slice ye + e*D1^3; its slab
-// sm + el*SE.
-template <typename T, int D1, int Q, int NE, typename TX = T, bool DS = false>
 __device__ __forceinline__ void diffusion_block(int tid, int e0, int nel, const int32_t* __restrict__ e2l,
                                                 const T* __restrict__ Dq, T* sm, const TX* __restrict__ x,
                                                 TX* __restrict__ ye, uint64_t* bar = nullptr, int* err = nullptr) {
@@ -560,9 +515,9 @@ __device__ __forceinline__ void diffusion_block(int tid, int e0, int nel, const 
   const size_t ev = valid ? (size_t)(e0 + el) : 0;
   gather_x<T, D1, Q, TX>(t, valid, e2l + ev * ND, x, Ln::X(sm + el * SE), Ln::XP);
   __syncthreads();
-  if (tid < NE * N1) Ln::d1(tid % N1, sm + (tid / N1) * SE);
+  if (tid < nel * N1) Ln::d1(tid % N1, sm + (tid / N1) * SE);
   __syncthreads();
-  if (tid < NE * N2) Ln::d2(tid % N2, sm + (tid / N2) * SE);
+  if (tid < nel * N2) Ln::d2(tid % N2, sm + (tid / N2) * SE);
   __syncthreads();
   T t0[D1], t1[D1], t2[D1];
   const T* De = DS ? Dq + (size_t)el * 6 * NQ : Dq + ev * 6 * NQ;
@@ -570,15 +525,12 @@ __device__ __forceinline__ void diffusion_block(int tid, int e0, int nel, const 
   __syncthreads();
   Ln::d3_store(t, sm + el * SE, t0, t1, t2);
   __syncthreads();
-  if (tid < NE * N2) Ln::d4(tid % N2, sm + (tid / N2) * SE);
+  if (tid < nel * N2) Ln::d4(tid % N2, sm + (tid / N2) * SE);
   __syncthreads();
-  if (tid < NE * N1) {
-    const int el5 = tid / N1;
-    if (el5 < nel) Ln::template d5<TX>(tid % N1, sm + el5 * SE, ye + (size_t)(e0 + el5) * ND);
-  }
+  if (tid < nel * N1) Ln::template d5<TX>(tid % N1, sm + (tid / N1) * SE, ye + (size_t)(e0 + tid / N1) * ND);
 }
 
-template <typename T, int D1, int Q, int NE, typename TX = T, bool DS = false>
+template <typename T, int D1, int Q, typename TX = T, bool DS = false>
 __device__ __forceinline__ void mass_block(int tid, int e0, int nel, const int32_t* __restrict__ e2l,
                                            const T* __restrict__ Dq, T* sm, const TX* __restrict__ x,
                                            TX* __restrict__ ye, uint64_t* bar = nullptr, int* err = nullptr) {
@@ -590,9 +542,9 @@ __device__ __forceinline__ void mass_block(int tid, int e0, int nel, const int32
   const size_t ev = valid ? (size_t)(e0 + el) : 0;
   gather_x<T, D1, Q, TX>(t, valid, e2l + ev * ND, x, Ln::X(sm + el * SE), Ln::XP);
   __syncthreads();
-  if (tid < NE * N1) Ln::m1(tid % N1, sm + (tid / N1) * SE);
+  if (tid < nel * N1) Ln::m1(tid % N1, sm + (tid / N1) * SE);
   __syncthreads();
-  if (tid < NE * N2) Ln::m2(tid % N2, sm + (tid / N2) * SE);
+  if (tid < nel * N2) Ln::m2(tid % N2, sm + (tid / N2) * SE);
   __syncthreads();
   T t0[D1];
   const T* De = DS ? Dq + (size_t)el * NQ : Dq + ev * NQ;
@@ -600,12 +552,9 @@ __device__ __forceinline__ void mass_block(int tid, int e0, int nel, const int32
   __syncthreads();
   Ln::m3_store(t, sm + el * SE, t0);
   __syncthreads();
-  if (tid < NE * N2) Ln::m4(tid % N2, sm + (tid / N2) * SE);
+  if (tid < nel * N2) Ln::m4(tid % N2, sm + (tid / N2) * SE);
   __syncthreads();
-  if (tid < NE * N1) {
-    const int el5 = tid / N1;
-    if (el5 < nel) Ln::template m5<TX>(tid % N1, sm + el5 * SE, ye + (size_t)(e0 + el5) * ND);
-  }
+  if (tid < nel * N1) Ln::template m5<TX>(tid % N1, sm + (tid / N1) * SE, ye + (size_t)(e0 + tid / N1) * ND);
 }
 
 // Hint the L2 to fetch a contiguous byte range with one bulk prefetch
