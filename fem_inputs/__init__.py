@@ -17,16 +17,20 @@ partial-assembly discussion of Sec. 4.4):
 * optional shuffling of vertex and element numbering and a random proper
   rotation of each element's local vertex order (exercises shared-entity
   orientation handling);
+* curved meshes: per-element nodal coordinates at an equispaced lattice,
+  the multilinear vertex map followed by a smooth bulge that fixes the
+  domain boundary (the library and the oracle read them as the element's
+  order-k nodal geometry);
 * per-element coefficient kappa_e with log(kappa_e) ~ N(0, 1);
 * input vectors x ~ U[-1, 1].
 """
 
 from .rng import splitmix64, uniform01, uniform, normal, permutation
-from .mesh import hex_lattice, CUBE_ROTATIONS, lattice_dofs, submesh, quad_lattice
+from .mesh import hex_lattice, CUBE_ROTATIONS, lattice_dofs, submesh, quad_lattice, curved_nodes
 from .fields import lognormal, x_uniform, rho_uniform
 
 __all__ = [
     "splitmix64", "uniform01", "uniform", "normal", "permutation",
-    "hex_lattice", "CUBE_ROTATIONS", "lattice_dofs", "submesh", "quad_lattice",
+    "hex_lattice", "CUBE_ROTATIONS", "lattice_dofs", "submesh", "quad_lattice", "curved_nodes",
     "lognormal", "x_uniform", "rho_uniform",
 ]

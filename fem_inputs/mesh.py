@@ -151,3 +151,40 @@ def quad_lattice(N, perturb=0.0, seed=1, shuffle=False, shuffle_seed=None):
         cyc = np.array([[0, 1, 2, 3], [1, 2, 3, 0], [2, 3, 0, 1], [3, 0, 1, 2]], dtype=np.int64)
         quads = np.take_along_axis(quads, cyc[rot], axis=1)
     return np.ascontiguousarray(coords), np.ascontiguousarray(quads.astype(np.int32))
+
+
+def _bulge(x, amp):
+    """Smooth interior displacement of the unit cube / square, zero on its
+    boundary: x + amp * prod_d sin(pi x_d) * (1, ..., 1)."""
+    s = np.prod(np.sin(np.pi * x), axis=-1, keepdims=True)
+    return x + amp * s
+
+
+def curved_nodes(coords, cells, k, amp=0.05):
+    """Per-element nodal coordinates of a curved mesh: every element's
+    (k+1)^dim equispaced reference lattice (first index fastest, in the
+    element's own local vertex frame), mapped through the element's
+    multilinear vertex map and then through a smooth bulge that fixes the
+    domain boundary. Neighbours compute identical points on shared faces, so
+    the nodal field is continuous. cells: [E,8] hexes (local vertices
+    (0,0,0) (1,0,0) (1,1,0) (0,1,0) then z = 1) or [E,4] quads. Returns
+    [E, (k+1)^dim, dim]."""
+    coords = np.asarray(coords, dtype=np.float64)
+    cells = np.asarray(cells, dtype=np.int64)
+    dim = coords.shape[1]
+    t = np.arange(k + 1) / k
+    if dim == 3:
+        c3, c2, c1 = np.meshgrid(t, t, t, indexing="ij")
+        xi = np.stack([c1.ravel(), c2.ravel(), c3.ravel()], axis=1)
+        corners = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0],
+                            [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]])
+    else:
+        c2, c1 = np.meshgrid(t, t, indexing="ij")
+        xi = np.stack([c1.ravel(), c2.ravel()], axis=1)
+        corners = np.array([[0, 0], [1, 0], [1, 1], [0, 1]])
+    W = np.ones((xi.shape[0], corners.shape[0]))
+    for v in range(corners.shape[0]):
+        for d in range(dim):
+            W[:, v] *= np.where(corners[v, d] == 1, xi[:, d], 1.0 - xi[:, d])
+    X = np.einsum("kv,evr->ekr", W, coords[cells])
+    return _bulge(X, amp)

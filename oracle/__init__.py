@@ -27,6 +27,8 @@ matrix with the same quadrature):
   (`solve`, Sec. 2 and Sec. 5.1);
 * the compliance gradient dJ/dkappa_e = -u_e^T Khat_e u_e (`gradient`);
 * the same definitions on quadrilaterals in 2D (`twod`);
+* curved elements: the order-k nodal geometry of Sec. 3.1 in place of the
+  trilinear map (`curved`);
 * p-multigrid: level hierarchy, nodal-interpolation transfers, coarse
   essential DOFs, Chebyshev-Jacobi smoothing, the V-cycle and flexible CG
   (`multigrid`; the paper names matrix-free p-multigrid, Sec. 5.2, without
@@ -38,4 +40,4 @@ which has no oracle of its own (parity unpinned beyond the FP64 outer
 residual; the error against this FP64 oracle is reported per result).
 """
 
-from . import rules, lagrange, numbering, element, assemble, solve, gradient, twod, multigrid  # noqa: F401
+from . import rules, lagrange, numbering, element, assemble, solve, gradient, twod, multigrid, curved  # noqa: F401
