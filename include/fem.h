@@ -114,6 +114,16 @@ fem_status fem_mesh_create(const double* coords_host, int64_t nv,
  * fem_mesh_create. */
 fem_status fem_mesh2d_create(const double* coords_host, int64_t nv,
                              const int32_t* quad_host, int64_t ne, fem_mesh** out);
+/* High-order (curved) geometry, Sec. 3.1 "nodes": element e is mapped by
+ * x(xhat) = sum_i X_{e,i} w_i(xhat) with the (k+1)^3 order-k GLL Lagrange
+ * functions w_i (lexicographic, x fastest, in the element's local vertex
+ * frame). nodes_host: [ne][(k+1)^3][3] float64, copied; 1 <= k <= 8, or
+ * k = 0 to return to the trilinear vertex map. Forms created afterwards use
+ * it in their setup (D), load vector and coordinates; an existing form picks
+ * it up at its next fem_form_set_coef. The vertex coordinates still define
+ * the topology. Errors: FEM_EINVAL (order, non-finite coordinates),
+ * FEM_EUNSUPPORTED (2D mesh). */
+fem_status fem_mesh_set_nodes(fem_mesh* mesh, int k, const double* nodes_host);
 void fem_mesh_destroy(fem_mesh* mesh);
 
 /* ---- H1 space of order p (Sec. 3.4 "Finite Element Spaces") ----------------

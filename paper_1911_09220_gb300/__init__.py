@@ -80,6 +80,21 @@ class Mesh:
         self._h = h
         self.nv, self.ne = self.coords.shape[0], self.hexes.shape[0]
         self.dim = 3
+        self.geo_nodes, self.geo_order = None, 0
+
+    def set_nodes(self, nodes, k):
+        """Curved geometry: element nodal coordinates [ne, (k+1)^3, 3] at the
+        order-k GLL lattice (x fastest, element's local frame); k = 0 returns
+        to the vertex map. Set before creating forms (or call set_coef)."""
+        if k == 0:
+            B.check(B.lib().fem_mesh_set_nodes(self._h, 0, None))
+            self.geo_nodes, self.geo_order = None, 0
+            return
+        n = np.ascontiguousarray(nodes, dtype=np.float64)
+        if n.shape != (self.ne, (k + 1) ** 3, 3):
+            raise ValueError(f"nodes must be [{self.ne}, {(k + 1) ** 3}, 3]")
+        B.check(B.lib().fem_mesh_set_nodes(self._h, int(k), n.ctypes.data))
+        self.geo_nodes, self.geo_order = n, int(k)
 
     def __del__(self):
         if getattr(self, "_h", None) and B._lib is not None:

@@ -55,6 +55,7 @@ SIGNATURES = {
     "fem_supported": (I, [I, I]),
     "fem_mesh_create": (I, [P, I64, P, I64, C.POINTER(P)]),
     "fem_mesh2d_create": (I, [P, I64, P, I64, C.POINTER(P)]),
+    "fem_mesh_set_nodes": (I, [P, I, P]),
     "fem_mesh_destroy": (None, [P]),
     "fem_space_create": (I, [P, I, C.POINTER(P)]),
     "fem_space_destroy": (None, [P]),

@@ -1,6 +1,7 @@
 // Host side of the C ABI: errors, mesh ingest, the H1 space (global numbering,
 // element restriction table and its inverse, boundary DOFs) and form setup.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -92,7 +93,33 @@ extern "C" void fem_mesh_destroy(fem_mesh* m) {
   if (!m) return;
   dev_free(m->d_coords);
   dev_free(m->d_hex);
+  dev_free(m->d_gnodes);
   delete m;
+}
+
+extern "C" fem_status fem_mesh_set_nodes(fem_mesh* m, int k, const double* nodes_host) {
+  if (!m) return fem_fail(FEM_EINVAL, "fem_mesh_set_nodes: NULL mesh");
+  if (m->dim != 3) return fem_fail(FEM_EUNSUPPORTED, "fem_mesh_set_nodes: hexahedral meshes only");
+  if (k == 0) {  // back to the vertex (trilinear) geometry
+    dev_free(m->d_gnodes);
+    m->geo_k = 0;
+    return FEM_OK;
+  }
+  if (k < 1 || k > 8) return fem_fail(FEM_EINVAL, "fem_mesh_set_nodes: order %d not in 1..8", k);
+  if (!nodes_host) return fem_fail(FEM_EINVAL, "fem_mesh_set_nodes: NULL nodes");
+  const size_t n = (size_t)m->ne * (k + 1) * (k + 1) * (k + 1) * 3;
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(nodes_host[i])) return fem_fail(FEM_EINVAL, "fem_mesh_set_nodes: non-finite coordinate");
+  double* d = nullptr;
+  FEM_TRY(dev_alloc(&d, n));
+  if (cudaMemcpy(d, nodes_host, sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+    dev_free(d);
+    return fem_fail(FEM_ECUDA, "fem_mesh_set_nodes: copy failed");
+  }
+  dev_free(m->d_gnodes);
+  m->d_gnodes = d;
+  m->geo_k = k;
+  return FEM_OK;
 }
 
 // ---------------------------------------------------------------- space ----
@@ -429,6 +456,7 @@ extern "C" void fem_space_destroy(fem_space* sp) {
   dev_free(sp->d_l2e_off);
   dev_free(sp->d_l2e_idx);
   dev_free(sp->d_nodes);
+  dev_free(sp->d_gBn);
   delete sp;
 }
 
@@ -526,6 +554,24 @@ extern "C" fem_status fem_form_create(const fem_space* sp, int kind, int q1d, co
   return FEM_OK;
 }
 
+fem_status fem_form_geo_tables(const fem_form* fc) {
+  fem_form* f = const_cast<fem_form*>(fc);
+  const fem_mesh* m = f->space->mesh;
+  if (m->geo_k <= 0 || f->geo_k == m->geo_k) return FEM_OK;
+  std::vector<double> nk, pts, wts, B, G;
+  fem_gll_nodes(m->geo_k, nk);
+  fem_gauss_rule(f->q1d, pts, wts);
+  fem_lagrange_tables(nk, pts, B, G);  // [q1d][k+1]
+  dev_free(f->d_gB);
+  dev_free(f->d_gG);
+  FEM_TRY(dev_alloc(&f->d_gB, B.size()));
+  FEM_TRY(dev_alloc(&f->d_gG, G.size()));
+  FEM_CUDA(cudaMemcpy(f->d_gB, B.data(), sizeof(double) * B.size(), cudaMemcpyHostToDevice));
+  FEM_CUDA(cudaMemcpy(f->d_gG, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice));
+  f->geo_k = m->geo_k;
+  return FEM_OK;
+}
+
 extern "C" fem_status fem_form_set_coef(fem_form* f, const double* coef, void* stream) {
   if (!f) return fem_fail(FEM_EINVAL, "fem_form_set_coef: NULL form");
   cudaStream_t s = (cudaStream_t)stream;
@@ -561,6 +607,8 @@ extern "C" void fem_form_destroy(fem_form* f) {
   dev_free(f->d_Bdf);
   dev_free(f->d_Gdf);
   dev_free(f->d_Ddf);
+  dev_free(f->d_gB);
+  dev_free(f->d_gG);
   dev_free(f->d_qpts);
   dev_free(f->d_qwts);
   if (f->d_ye) cudaFree(f->d_ye);

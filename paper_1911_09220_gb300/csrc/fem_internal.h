@@ -53,6 +53,9 @@ struct fem_mesh {
   std::vector<int32_t> hex;     // [ne][nvpe] element vertex tuples
   double* d_coords = nullptr;
   int32_t* d_hex = nullptr;
+  // optional order-k nodal geometry (Sec. 3.1 "nodes"): [ne][(k+1)^3][3]
+  int geo_k = 0;
+  double* d_gnodes = nullptr;
 };
 
 struct fem_space {
@@ -67,6 +70,8 @@ struct fem_space {
   int32_t* d_l2e_off = nullptr; // [ndof+1]
   int32_t* d_l2e_idx = nullptr; // [ne*nd], e*nd + k
   double* d_nodes = nullptr;
+  double* d_gBn = nullptr;      // order-k geometry basis at this space's GLL nodes [D1][k+1]
+  int gBn_k = 0;
 };
 
 struct fem_form {
@@ -98,6 +103,10 @@ struct fem_form {
   double* d_red = nullptr;         // reduction partials / scalars
   size_t red_len = 0;
   int* h_pinned = nullptr;         // pinned host status words
+  // order-k geometry basis at this form's Gauss points, [q1d][k+1] (curved meshes)
+  double* d_gB = nullptr;
+  double* d_gG = nullptr;
+  int geo_k = 0;
 };
 
 // ---------------------------------------------------------------- basis -----
@@ -144,3 +153,6 @@ fem_status fem_launch_apply_element_2d(const fem_form* f, int dtype, const void*
 fem_status fem_launch_diag_element_2d(const fem_form* f, double* ye, cudaStream_t s);
 fem_status fem_launch_rhs_element_2d(const fem_form* f, const double* fq, double* ye, cudaStream_t s);
 fem_status fem_launch_grad_2d(const fem_form* f, const double* u, double* g, cudaStream_t s);
+// Make the form's geometry tables match its mesh's nodal order (no-op for
+// vertex-only meshes); synchronous.
+fem_status fem_form_geo_tables(const fem_form* f);

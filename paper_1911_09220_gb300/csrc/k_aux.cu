@@ -3,6 +3,7 @@
 // apply kernels, followed by the atomic-free inverse-map scatter.
 #include "fem_internal.h"
 #include "k_common.cuh"
+#include "k_geom.cuh"
 
 namespace {
 
@@ -109,7 +110,7 @@ template <int D1, int Q, int NE>
 __global__ void __launch_bounds__(Q * Q * NE)
 k_rhs(int ne, const double* __restrict__ coords, const int32_t* __restrict__ hex,
       const double* __restrict__ qpts, const double* __restrict__ qwts, const double* __restrict__ Bg,
-      const double* __restrict__ fq, double* __restrict__ ye) {
+      const double* __restrict__ fq, double* __restrict__ ye, NodalGeo ng) {
   constexpr int ND = D1 * D1 * D1, NQ = Q * Q * Q;
   constexpr int SE = D1 * Q * Q + D1 * D1 * Q + 24;
   __shared__ double sB[Q * D1];
@@ -131,8 +132,17 @@ k_rhs(int ne, const double* __restrict__ coords, const int32_t* __restrict__ hex
 #pragma unroll
   for (int d = 0; d < D1; ++d) t[d] = 0.0;
   if (valid) {
+    NodalGeo g = ng;  // ng.K > 0: curved mesh, det J from the nodal map
+    if (g.K > 0) g.load(e);
     for (int qz = 0; qz < Q; ++qz) {
-      const double dj = hex_detj(sX, qpts[tx], qpts[ty], qpts[qz]);
+      double dj;
+      if (g.K > 0) {
+        double J[3][3];
+        g.jacobian(tx, ty, qz, J);
+        dj = det3(J);
+      } else {
+        dj = hex_detj(sX, qpts[tx], qpts[ty], qpts[qz]);
+      }
       const double v = qwts[tx] * qwts[ty] * qwts[qz] * dj * fq[(size_t)e * NQ + (qz * Q + ty) * Q + tx];
 #pragma unroll
       for (int d = 0; d < D1; ++d) t[d] += sB[qz * D1 + d] * v;
@@ -283,8 +293,14 @@ fem_status launch_rhs(const fem_form* f, const double* fq, double* ye, cudaStrea
   const size_t bytes = sizeof(double) * NE * (D1 * Q * Q + D1 * D1 * Q + 24);
   auto k = k_rhs<D1, Q, NE>;
   FEM_TRY(set_smem(k, bytes));
-  k<<<(ne + NE - 1) / NE, dim3(Q, Q, NE), bytes, s>>>(ne, f->space->mesh->d_coords, f->space->mesh->d_hex,
-                                                      f->d_qpts, f->d_qwts, f->d_B, fq, ye);
+  const fem_mesh* m = f->space->mesh;
+  NodalGeo ng{nullptr, nullptr, nullptr, 0, nullptr};
+  if (m->geo_k > 0) {
+    FEM_TRY(fem_form_geo_tables(f));
+    ng = NodalGeo{m->d_gnodes, f->d_gB, f->d_gG, m->geo_k + 1, nullptr};
+  }
+  k<<<(ne + NE - 1) / NE, dim3(Q, Q, NE), bytes, s>>>(ne, m->d_coords, m->d_hex, f->d_qpts, f->d_qwts, f->d_B, fq,
+                                                      ye, ng);
   FEM_LAUNCHED();
   return FEM_OK;
 }
