@@ -518,6 +518,55 @@ def run_mg(args):
     return 0
 
 
+def run_curved(args):
+    """Curved-geometry workload: the apply workload's mesh (p, N) with order-k
+    nodal geometry (k = 2, 4; boundary-preserving bulge of amplitude 0.05):
+    setup (D) time against the vertex geometry, FP64 apply, and the
+    p-multigrid solve to 1e-10 on the curved mesh. One JSON line."""
+    import torch
+    from paper_1911_09220_gb300 import build as fbuild
+    fbuild.build()
+    import paper_1911_09220_gb300 as F
+    from fem_inputs import curved_nodes
+    p, N = args.p, args.N
+    c, h, kappa, xgen = make_problem(p, N)
+    kap = torch.as_tensor(kappa, device="cuda")
+    out = {"workload": f"curved geometry, p={p}, q={p + 2}, {N}^3 hexes, nodal order k = 2, 4", "p": p, "N": N}
+    for k in (0, 2, 4):
+        mesh = F.Mesh(c, h)
+        t0 = time.perf_counter()
+        if k:
+            mesh.set_nodes(curved_nodes(c, h, k, amp=0.05), k)
+        t_nodes = time.perf_counter() - t0
+        space = F.Space(mesh, p)
+        form = F.Form(space, "diffusion", p + 2, coef=kap)
+        t_setup = time_events(lambda: form.set_coef(kap), 3, 1)
+        x = torch.as_tensor(xgen(space.ndof), device="cuda")
+        y = torch.empty_like(x)
+        t_apply = time_events(lambda: form.apply(x, y), args.steps, 3)
+        res = {"nodes_host_s": t_nodes, "setup_ms": t_setup, "apply_f64_ms": t_apply, "ndof": space.ndof}
+        if not args.no_solve:
+            form.set_essential(torch.as_tensor(space.boundary_dofs(), device="cuda"))
+            b = torch.empty_like(x)
+            _sin_rhs(form, b)
+            bc = torch.empty_like(b)
+            form.lift_rhs(b, torch.zeros_like(b), bc)
+            mg = F.Multigrid(form, precision="f32")
+            u = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = mg.solve(bc, u, rtol=1e-10, check_every=4, raise_on_error=False, arith="df64")
+            torch.cuda.synchronize()
+            res["pmg_solve"] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
+                                "converged": info["converged"], "relres": info["relres"]}
+            del mg
+        out["k%d" % k if k else "vertex"] = res
+        del form, space, mesh, x, y
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_grad(args):
     """Differentiation workload: 64^3 hexes, 0.1h, p = 2, kappa = 0.01 + rho^3,
     rho ~ U[0.2, 1], f = 1, homogeneous Dirichlet: compliance solve and the
@@ -569,7 +618,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--solve-maxit", type=int, default=20000)
-    ap.add_argument("--workload", default="apply", choices=["apply", "sweep", "batch", "grad", "paper2d", "mg"])
+    ap.add_argument("--workload", default="apply", choices=["apply", "sweep", "batch", "grad", "paper2d", "mg", "curved"])
     ap.add_argument("--sweep-size", default="4e6", choices=["4e6", "2e7"])
     ap.add_argument("--orders", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--nprob", type=int, default=256)
@@ -587,6 +636,8 @@ def main():
         return run_paper2d(args)
     if args.workload == "mg":
         return run_mg(args)
+    if args.workload == "curved":
+        return run_curved(args)
     if args.workload == "grad":
         return run_grad(args)
 
