@@ -29,6 +29,7 @@ matrix with the same quadrature):
 * the same definitions on quadrilaterals in 2D (`twod`);
 * curved elements: the order-k nodal geometry of Sec. 3.1 in place of the
   trilinear map (`curved`);
+* the convection operator (beta . grad u, v) (`convection`);
 * p-multigrid: level hierarchy, nodal-interpolation transfers, coarse
   essential DOFs, Chebyshev-Jacobi smoothing, the V-cycle and flexible CG
   (`multigrid`; the paper names matrix-free p-multigrid, Sec. 5.2, without
@@ -40,4 +41,5 @@ which has no oracle of its own (parity unpinned beyond the FP64 outer
 residual; the error against this FP64 oracle is reported per result).
 """
 
-from . import rules, lagrange, numbering, element, assemble, solve, gradient, twod, multigrid, curved  # noqa: F401
+from . import (rules, lagrange, numbering, element, assemble, solve, gradient, twod, multigrid, curved,  # noqa: F401
+               convection)
