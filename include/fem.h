@@ -67,7 +67,7 @@ enum {
   FEM_EUNSUPPORTED = 7   /* (p, q1d) or size outside the compiled set */
 };
 
-enum { FEM_MASS = 0, FEM_DIFFUSION = 1 };       /* bilinear form kind */
+enum { FEM_MASS = 0, FEM_DIFFUSION = 1, FEM_CONVECTION = 2 };  /* bilinear form kind */
 /* Vector / compute type. FEM_DF64: float64 vectors, element arithmetic in
  * double-float (pairs of floats, 48-bit significand, on the FP32 pipe) with a
  * double-float copy of D made on first use; the operator agrees with the FP64
@@ -165,6 +165,21 @@ fem_status fem_space_dof_coords(const fem_space* space, double* out, void* strea
 fem_status fem_form_create(const fem_space* space, int kind, int q1d,
                            const double* coef, void* stream, fem_form** out);
 void fem_form_destroy(fem_form* form);
+/* Convection form (beta . grad u, v) (Sec. 5.3 lists convection among the
+ * partially assembled integrators): PA stores, per element and quadrature
+ * point, D_q = coef_e w_q det J_q J_q^-1 beta_q = coef_e w_q adj(J_q) beta_q
+ * (3 components, point-major [ne][q1d^3][3]); the apply runs the forward
+ * gradient stages of the diffusion operator and the backward stages of the
+ * mass operator: y = B^T (D . Ghat) x. beta_q: device float64
+ * [ne][q1d^3][3], the physical velocity at the form's quadrature points
+ * (fem_qpoint_coords gives their positions), copied; coef as for
+ * fem_form_create. The operator is not symmetric: fem_assemble_diagonal,
+ * fem_solve, fem_mg_create and fem_batch_create reject it. Hexahedral
+ * meshes only (FEM_EUNSUPPORTED on 2D). */
+fem_status fem_form_create_convection(const fem_space* space, int q1d, const double* beta_q,
+                                      const double* coef, void* stream, fem_form** out);
+/* Replace the velocity of a convection form (recomputes D). */
+fem_status fem_form_set_velocity(fem_form* form, const double* beta_q, void* stream);
 /* Replace the per-element coefficient (recomputes D). */
 fem_status fem_form_set_coef(fem_form* form, const double* coef, void* stream);
 /* Essential DOF list (device int32 [n], any order, no duplicates needed):

@@ -177,6 +177,33 @@ class Form:
         self._h = h
         self.ess = None
 
+    @classmethod
+    def convection(cls, space, beta, q1d=None, coef=None, stream=None):
+        """Convection form (beta . grad u, v): beta [ne, q1d^3, 3] (device
+        float64), the physical velocity at the form's quadrature points."""
+        import torch
+        L = B.lib()
+        self = cls.__new__(cls)
+        self.space = space
+        self.kind = B.FEM_CONVECTION
+        self.q1d = int(q1d) if q1d is not None else space.p + 2
+        self.nq = self.q1d ** space.dim
+        self._coef = None if coef is None else coef.contiguous()
+        self._beta = beta.contiguous()
+        if tuple(self._beta.shape) != (space.ne, self.nq, 3):
+            raise ValueError(f"beta must be [{space.ne}, {self.nq}, 3]")
+        h = C.c_void_p()
+        B.check(L.fem_form_create_convection(space._h, self.q1d, _ptr(self._beta, torch.float64, "beta"),
+                                             _ptr(self._coef, torch.float64, "coef"), _stream(stream), C.byref(h)))
+        self._h = h
+        self.ess = None
+        return self
+
+    def set_velocity(self, beta, stream=None):
+        import torch
+        self._beta = beta.contiguous()
+        B.check(B.lib().fem_form_set_velocity(self._h, _ptr(self._beta, torch.float64, "beta"), _stream(stream)))
+
     # ---- configuration
     def set_coef(self, coef, stream=None):
         import torch

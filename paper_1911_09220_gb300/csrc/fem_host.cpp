@@ -488,12 +488,30 @@ extern "C" fem_status fem_space_dof_coords(const fem_space* sp, double* out, voi
 }
 
 // ----------------------------------------------------------------- form ----
+static fem_status form_create(const fem_space* sp, int kind, int q1d, const double* coef, const double* beta,
+                              void* stream, fem_form** out);
+
 extern "C" fem_status fem_form_create(const fem_space* sp, int kind, int q1d, const double* coef,
                                       void* stream, fem_form** out) {
   if (!sp || !out) return fem_fail(FEM_EINVAL, "fem_form_create: NULL argument");
   *out = nullptr;
+  if (kind == FEM_CONVECTION)
+    return fem_fail(FEM_EINVAL, "fem_form_create: convection forms need a velocity (fem_form_create_convection)");
   if (kind != FEM_MASS && kind != FEM_DIFFUSION)
     return fem_fail(FEM_EINVAL, "fem_form_create: unknown kind %d", kind);
+  return form_create(sp, kind, q1d, coef, nullptr, stream, out);
+}
+
+extern "C" fem_status fem_form_create_convection(const fem_space* sp, int q1d, const double* beta_q,
+                                                 const double* coef, void* stream, fem_form** out) {
+  if (!sp || !out || !beta_q) return fem_fail(FEM_EINVAL, "fem_form_create_convection: NULL argument");
+  *out = nullptr;
+  if (sp->mesh->dim != 3) return fem_fail(FEM_EUNSUPPORTED, "fem_form_create_convection: hexahedral meshes only");
+  return form_create(sp, FEM_CONVECTION, q1d, coef, beta_q, stream, out);
+}
+
+static fem_status form_create(const fem_space* sp, int kind, int q1d, const double* coef, const double* beta,
+                              void* stream, fem_form** out) {
   if (!fem_kernels_supported(sp->p, q1d))
     return fem_fail(FEM_EUNSUPPORTED, "fem_form_create: (p=%d, q1d=%d) not compiled", sp->p, q1d);
   FEM_TRY(fem_apply_tables_init());
@@ -505,7 +523,7 @@ extern "C" fem_status fem_form_create(const fem_space* sp, int kind, int q1d, co
   f->q1d = q1d;
   const int dim = sp->mesh->dim;
   f->nq = dim == 3 ? q1d * q1d * q1d : q1d * q1d;
-  f->ncomp = (kind == FEM_DIFFUSION) ? (dim == 3 ? 6 : 3) : 1;
+  f->ncomp = (kind == FEM_DIFFUSION) ? (dim == 3 ? 6 : 3) : kind == FEM_CONVECTION ? 3 : 1;
   std::vector<double> pts, wts, B, G;
   fem_gauss_rule(q1d, pts, wts);
   fem_lagrange_tables(sp->nodes, pts, B, G);
@@ -540,6 +558,12 @@ extern "C" fem_status fem_form_create(const fem_space* sp, int kind, int q1d, co
   if (st == FEM_OK) st = dev_alloc(&f->d_flag, 4);
   if (st == FEM_OK && cudaMallocHost((void**)&f->h_pinned, 64) != cudaSuccess)
     st = fem_fail(FEM_ENOMEM, "fem_form_create: pinned host allocation failed");
+  if (st == FEM_OK && beta) {
+    const size_t nb = (size_t)sp->ne * f->nq * 3;
+    st = dev_alloc(&f->d_beta, nb);
+    if (st == FEM_OK && cudaMemcpyAsync(f->d_beta, beta, sizeof(double) * nb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      st = fem_fail(FEM_ECUDA, "fem_form_create: velocity copy failed");
+  }
   if (st != FEM_OK) {
     fem_form_destroy(f);
     return st;
@@ -572,6 +596,8 @@ fem_status fem_form_geo_tables(const fem_form* fc) {
   return FEM_OK;
 }
 
+static fem_status form_setup(fem_form* f, cudaStream_t s);
+
 extern "C" fem_status fem_form_set_coef(fem_form* f, const double* coef, void* stream) {
   if (!f) return fem_fail(FEM_EINVAL, "fem_form_set_coef: NULL form");
   cudaStream_t s = (cudaStream_t)stream;
@@ -583,6 +609,10 @@ extern "C" fem_status fem_form_set_coef(fem_form* f, const double* coef, void* s
     FEM_CUDA(cudaMemcpyAsync(f->d_coef, ones.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaStreamSynchronize(s));
   }
+  return form_setup(f, s);
+}
+
+static fem_status form_setup(fem_form* f, cudaStream_t s) {
   FEM_CUDA(cudaMemsetAsync(f->d_flag, 0, sizeof(int) * 4, s));
   FEM_TRY(fem_launch_setup(f, s));
   FEM_CUDA(cudaMemcpyAsync(f->h_pinned, f->d_flag, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
@@ -593,6 +623,15 @@ extern "C" fem_status fem_form_set_coef(fem_form* f, const double* coef, void* s
     return fem_fail(FEM_EINVERTED, "fem_form: det J <= 0 at a quadrature point of element %d",
                     f->h_pinned[1]);
   return FEM_OK;
+}
+
+extern "C" fem_status fem_form_set_velocity(fem_form* f, const double* beta, void* stream) {
+  if (!f || !beta) return fem_fail(FEM_EINVAL, "fem_form_set_velocity: NULL argument");
+  if (f->kind != FEM_CONVECTION) return fem_fail(FEM_EINVAL, "fem_form_set_velocity: not a convection form");
+  cudaStream_t s = (cudaStream_t)stream;
+  FEM_CUDA(cudaMemcpyAsync(f->d_beta, beta, sizeof(double) * (size_t)f->space->ne * f->nq * 3,
+                           cudaMemcpyDeviceToDevice, s));
+  return form_setup(f, s);
 }
 
 extern "C" void fem_form_destroy(fem_form* f) {
@@ -609,6 +648,7 @@ extern "C" void fem_form_destroy(fem_form* f) {
   dev_free(f->d_Ddf);
   dev_free(f->d_gB);
   dev_free(f->d_gG);
+  dev_free(f->d_beta);
   dev_free(f->d_qpts);
   dev_free(f->d_qwts);
   if (f->d_ye) cudaFree(f->d_ye);

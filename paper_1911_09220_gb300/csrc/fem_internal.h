@@ -103,6 +103,7 @@ struct fem_form {
   double* d_red = nullptr;         // reduction partials / scalars
   size_t red_len = 0;
   int* h_pinned = nullptr;         // pinned host status words
+  double* d_beta = nullptr;        // convection: velocity [ne][nq][3]
   // order-k geometry basis at this form's Gauss points, [q1d][k+1] (curved meshes)
   double* d_gB = nullptr;
   double* d_gG = nullptr;

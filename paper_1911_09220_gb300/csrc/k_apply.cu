@@ -38,7 +38,12 @@ fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G
   (void)B;
   (void)G;
   int* err = f->d_flag + 3;
-  if (f->kind == FEM_DIFFUSION) {
+  if (f->kind == FEM_CONVECTION) {
+    const size_t bytes = BlockSmem<T, D1, Q, NE, 3, false>::bytes;
+    auto kern = k_convection_apply<T, D1, Q, NE, TX>;
+    FEM_TRY(prepare_smem(kern, bytes));
+    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, x, ye);
+  } else if (f->kind == FEM_DIFFUSION) {
     const size_t bytes = BlockSmem<T, D1, Q, NE, 6, ST>::bytes;
     auto kern = k_diffusion_apply<T, D1, Q, NE, TX, ST>;
     FEM_TRY(prepare_smem(kern, bytes));

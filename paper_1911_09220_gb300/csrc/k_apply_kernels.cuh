@@ -109,3 +109,17 @@ k_mass_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e
   }
 }
 
+template <typename T, int D1, int Q, int NE, typename TX>
+__global__ void __launch_bounds__(Q * Q * NE)
+k_convection_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
+                   const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye) {
+  constexpr int NQ = Q * Q * Q;
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x + Q * (threadIdx.y + Q * threadIdx.z);
+  const int e0 = blockIdx.x * NE;
+  const int nel = min(NE, ne - e0);
+  if (tid == 0) l2_prefetch_range(Dq + (size_t)e0 * 3 * NQ, sizeof(T) * (size_t)nel * 3 * NQ);
+  convection_block<T, D1, Q, TX>(tid, e0, nel, e2l, Dq, sm, x, ye);
+}

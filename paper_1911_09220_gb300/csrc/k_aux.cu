@@ -351,6 +351,7 @@ fem_status fem_launch_grad(const fem_form* f, const double* u, double* g, cudaSt
 
 extern "C" fem_status fem_assemble_diagonal(const fem_form* f, double* diag, int constrained, void* stream) {
   if (!f || !diag) return fem_fail(FEM_EINVAL, "fem_assemble_diagonal: NULL argument");
+  if (f->kind == FEM_CONVECTION) return fem_fail(FEM_EUNSUPPORTED, "fem_assemble_diagonal: convection form");
   if (constrained && !f->d_ess_mask)
     return fem_fail(FEM_EINVAL, "fem_assemble_diagonal: constrained diagonal needs fem_form_set_essential");
   cudaStream_t s = (cudaStream_t)stream;

@@ -427,6 +427,36 @@ struct Lines {
     for (int dx = 0; dx < D1; ++dx) fe_store(&out[t * D1 + dx], y1[dx] + y2[dx]);
   }
 
+  // ---- convection: the diffusion forward stages (d1, d2), then one value
+  // per point v = D_q . gradhat (D_q = w adj(J) beta, point-major [q][3]),
+  // then the mass backward stages (m3_store, m4, m5)
+  template <bool DS>
+  __device__ static void c3(int t, bool valid, const T* __restrict__ De, T* s, T* t0) {
+    const int qy = t / Q, qx = t % Q;
+    T rbb[D1], rgb[D1], rbg[D1], g0[Q], g1[Q], g2[Q];
+    const T *sbb = BB(s) + qy * RC + qx, *sgb = GB(s) + qy * RC + qx, *sbg = BG(s) + qy * RC + qx;
+#pragma unroll
+    for (int z = 0; z < D1; ++z) {
+      rbb[z] = sbb[z * Q];
+      rgb[z] = sgb[z * Q];
+      rbg[z] = sbg[z * Q];
+    }
+    eo_line<T, Q, D1, 1, BF>(rgb, g0);
+    eo_line<T, Q, D1, 1, BF>(rbg, g1);
+    eo_line<T, Q, D1, -1, GF>(rbb, g2);
+    const T* Dp = De + (size_t)t * 3;
+#pragma unroll
+    for (int qz = 0; qz < Q; ++qz) {
+      T v = 0;
+      if (valid) {
+        const T* d = Dp + (size_t)qz * QQ * 3;
+        v = fe_norm(d_load<DS>(d) * g0[qz] + d_load<DS>(d + 1) * g1[qz] + d_load<DS>(d + 2) * g2[qz]);
+      }
+      g0[qz] = v;
+    }
+    eo_line<T, D1, Q, 1, BT>(g0, t0);
+  }
+
   // ---- mass (B only, one D per point)
   __device__ static void m1(int t, T* s) {
     T xr[D1], bx[Q];
@@ -528,6 +558,34 @@ __device__ __forceinline__ void diffusion_block(int tid, int e0, int nel, const 
   if (tid < nel * N2) Ln::d4(tid % N2, sm + (tid / N2) * SE);
   __syncthreads();
   if (tid < nel * N1) Ln::template d5<TX>(tid % N1, sm + (tid / N1) * SE, ye + (size_t)(e0 + tid / N1) * ND);
+}
+
+// Convection (beta . grad u, v): forward stages of diffusion, backward
+// stages of mass; D block Dq + e*3*Q^3.
+template <typename T, int D1, int Q, typename TX = T>
+__device__ __forceinline__ void convection_block(int tid, int e0, int nel, const int32_t* __restrict__ e2l,
+                                                 const T* __restrict__ Dq, T* sm, const TX* __restrict__ x,
+                                                 TX* __restrict__ ye) {
+  using Ln = Lines<T, D1, Q>;
+  constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
+  constexpr int N1 = D1 * D1, N2 = D1 * Q;
+  const int el = tid / QQ, t = tid % QQ;
+  const bool valid = el < nel;
+  const size_t ev = valid ? (size_t)(e0 + el) : 0;
+  gather_x<T, D1, Q, TX>(t, valid, e2l + ev * ND, x, Ln::X(sm + el * SE), Ln::XP);
+  __syncthreads();
+  if (tid < nel * N1) Ln::d1(tid % N1, sm + (tid / N1) * SE);
+  __syncthreads();
+  if (tid < nel * N2) Ln::d2(tid % N2, sm + (tid / N2) * SE);
+  __syncthreads();
+  T t0[D1];
+  Ln::template c3<false>(t, valid, Dq + ev * 3 * NQ, sm + el * SE, t0);
+  __syncthreads();
+  Ln::m3_store(t, sm + el * SE, t0);
+  __syncthreads();
+  if (tid < nel * N2) Ln::m4(tid % N2, sm + (tid / N2) * SE);
+  __syncthreads();
+  if (tid < nel * N1) Ln::template m5<TX>(tid % N1, sm + (tid / N1) * SE, ye + (size_t)(e0 + tid / N1) * ND);
 }
 
 template <typename T, int D1, int Q, typename TX = T, bool DS = false>

@@ -59,6 +59,45 @@ __global__ void k_setup(int64_t ne, int Q, int kind, Geo geo, const double* __re
   }
 }
 
+// Convection: D = coef * w * adj(J) beta (= coef w det J J^-1 beta),
+// point-major [e][q][3]; beta [e][q][3] physical.
+template <typename Geo>
+__global__ void k_setup_conv(int64_t ne, int Q, Geo geo, const double* __restrict__ qwts,
+                             const double* __restrict__ coef, const double* __restrict__ beta,
+                             double* __restrict__ Dout, int* __restrict__ flag) {
+  const int nq = Q * Q * Q;
+  const int64_t total = ne * nq;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / nq;
+    const int q = (int)(t % nq);
+    const int q1 = q % Q, q2 = (q / Q) % Q, q3 = q / (Q * Q);
+    Geo h = geo;
+    h.load(e);
+    double J[3][3];
+    h.jacobian(q1, q2, q3, J);
+    double C[3][3];  // cofactors; adj(J)[a][b] = C[b][a]
+    C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    C[0][1] = -(J[1][0] * J[2][2] - J[1][2] * J[2][0]);
+    C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    C[1][0] = -(J[0][1] * J[2][2] - J[0][2] * J[2][1]);
+    C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    C[1][2] = -(J[0][0] * J[2][1] - J[0][1] * J[2][0]);
+    C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    C[2][1] = -(J[0][0] * J[1][2] - J[0][2] * J[1][0]);
+    C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+    if (!(det > 0.0)) {
+      if (atomicExch(&flag[0], 1) == 0) flag[1] = (int)e;
+    }
+    const double w = qwts[q1] * qwts[q2] * qwts[q3] * coef[e];
+    const double* b = beta + t * 3;
+    double* De = Dout + t * 3;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) De[a] = w * (C[0][a] * b[0] + C[1][a] * b[1] + C[2][a] * b[2]);
+  }
+}
+
 // x at the tensor points (q1, q2, q3) of a P^3 set: the Gauss points
 // (quadrature-point coordinates, out [ne][P^3][3]).
 template <typename Geo>
@@ -121,13 +160,22 @@ fem_status fem_launch_setup(const fem_form* f, cudaStream_t s) {
   const int64_t total = sp->ne * f->nq;
   const int grid = grid_for(total, 256);
   const fem_mesh* m = sp->mesh;
+  const bool conv = f->kind == FEM_CONVECTION;
   if (m->geo_k > 0) {
     FEM_TRY(fem_form_geo_tables(f));
     const NodalGeo g{m->d_gnodes, f->d_gB, f->d_gG, m->geo_k + 1, nullptr};
-    k_setup<NodalGeo><<<grid, 256, 0, s>>>(sp->ne, f->q1d, f->kind, g, f->d_qwts, f->d_coef, f->d_D, f->d_flag);
+    if (conv)
+      k_setup_conv<NodalGeo><<<grid, 256, 0, s>>>(sp->ne, f->q1d, g, f->d_qwts, f->d_coef, f->d_beta, f->d_D,
+                                                  f->d_flag);
+    else
+      k_setup<NodalGeo><<<grid, 256, 0, s>>>(sp->ne, f->q1d, f->kind, g, f->d_qwts, f->d_coef, f->d_D, f->d_flag);
   } else {
     const Hex8Geo g{m->d_coords, m->d_hex, f->d_qpts, {}};
-    k_setup<Hex8Geo><<<grid, 256, 0, s>>>(sp->ne, f->q1d, f->kind, g, f->d_qwts, f->d_coef, f->d_D, f->d_flag);
+    if (conv)
+      k_setup_conv<Hex8Geo><<<grid, 256, 0, s>>>(sp->ne, f->q1d, g, f->d_qwts, f->d_coef, f->d_beta, f->d_D,
+                                                 f->d_flag);
+    else
+      k_setup<Hex8Geo><<<grid, 256, 0, s>>>(sp->ne, f->q1d, f->kind, g, f->d_qwts, f->d_coef, f->d_D, f->d_flag);
   }
   FEM_LAUNCHED();
   return FEM_OK;

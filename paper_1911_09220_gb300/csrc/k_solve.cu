@@ -451,6 +451,7 @@ extern "C" fem_status fem_solve(const fem_form* fc, const double* b, double* xio
                                 fem_solve_info* info, void* stream) {
   if (!fc || !b || !xio) return fem_fail(FEM_EINVAL, "fem_solve: NULL argument");
   if (!fc->d_ess_mask) return fem_fail(FEM_EINVAL, "fem_solve: call fem_form_set_essential first (n may be 0)");
+  if (fc->kind == FEM_CONVECTION) return fem_fail(FEM_EINVAL, "fem_solve: CG needs a symmetric (mass or diffusion) form");
   fem_solve_opts o;
   fem_solve_opts_default(&o);
   if (opts) o = *opts;
