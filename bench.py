@@ -306,6 +306,27 @@ def run_sweep(args):
                     sol["speedup_mixed_ru"] = sol["f64"]["seconds"] / sol["mixed_ru"]["seconds"]
                     out["solve"] = sol
             del form, x32, y32, d
+        # convection (beta . grad u, v) with beta = (1 + y, sin 2z, x y - 1/2)
+        probe = F.Form(space, "mass", q)
+        xq = probe.qpoint_coords()
+        beta = torch.stack([1.0 + xq[..., 1], torch.sin(2.0 * xq[..., 2]), xq[..., 0] * xq[..., 1] - 0.5],
+                           -1).contiguous()
+        del xq, probe
+        cform = F.Form.convection(space, beta, q1d=q, coef=kap)
+        del beta
+        D1 = p + 1
+        cflops = 2.0 * (3 * q * D1 ** 3 + 4 * q ** 2 * D1 ** 2 + 4 * q ** 3 * D1 + 3 * q ** 3) * E
+        ye = torch.empty((E, D1 ** 3), dtype=torch.float64, device="cuda")
+        ye32 = torch.empty((E, D1 ** 3), dtype=torch.float32, device="cuda")
+        x32 = x.float()
+        tc = time_events(lambda: cform.apply(x, y), args.steps, 3)
+        tc64 = time_events(lambda: cform.apply_element(x, ye), args.steps, 3)
+        tc32 = time_events(lambda: cform.apply_element(x32, ye32), args.steps, 3)
+        tcdf = time_events(lambda: cform.apply_element(x, ye, arith="df64"), args.steps, 3)
+        out["convection"] = {"f64_ms": tc, "f64_gdofs": n / tc * 1e-6,
+                             "f64_element_frac_fp64_peak": cflops / tc64 * 1e-9 / FP64_PEAK_TFLOPS,
+                             "element_ms": {"f64": tc64, "f32": tc32, "df64": tcdf}}
+        del cform, ye, ye32, x32
         print(json.dumps(out), flush=True)
         del space, x, y
         torch.cuda.empty_cache()

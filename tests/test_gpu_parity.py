@@ -82,6 +82,12 @@ def test_apply_parity_df64(kind, p):
     y64 = torch.empty_like(y)
     cs.form.apply(cuda(x), y64)
     assert relerr(y.cpu().numpy(), y64.cpu().numpy()) <= TOL
+    # the two public halves: a float64 E-vector, then the FP64 scatter
+    ye = torch.empty(cs.space.ne * (p + 1) ** 3, dtype=torch.float64, device="cuda")
+    cs.form.apply_element(cuda(x), ye, arith="df64")
+    y2 = torch.empty_like(y)
+    cs.form.scatter(ye, y2)
+    assert relerr(y2.cpu().numpy(), ref) <= TOL
 
 
 def test_df64_constrained_and_small_magnitudes():
