@@ -35,8 +35,9 @@ def supported(p, q1d):
 
 
 def _stream(stream=None):
+    """cudaStream_t of a torch.cuda.Stream, a raw handle, or the current stream."""
     if stream is not None:
-        return C.c_void_p(int(stream))
+        return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     import torch
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
