@@ -1,0 +1,93 @@
+"""Parity at the benchmark's full size, in the launch configuration bench.py
+times: p = 4, q = 6, 68^3 hexes perturbed 0.15h (20,346,417 DOFs), the
+same seeded generators (mesh seed 14, lognormal seed 24, x seed 34). The
+oracle cannot assemble this matrix, so it computes sampled outputs one DOF
+at a time from the rows of the element matrices that hold the DOF
+(oracle.assemble.sampled_apply, with its own numbering); properties that
+hold at any size are checked on the whole output vector."""
+
+import numpy as np
+import pytest
+
+from fem_inputs import hex_lattice, lognormal, x_uniform
+from oracle import assemble, numbering
+
+from gpu_util import cuda
+
+pytestmark = pytest.mark.gpu
+
+P, Q, N = 4, 6, 68
+
+
+@pytest.fixture(scope="module")
+def full():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1911_09220_gb300 import build
+    build.build()
+    import paper_1911_09220_gb300 as F
+    c, h = hex_lattice(N, 0.15, seed=10 + P)
+    kap = lognormal(20 + P, h.shape[0])
+    num = numbering.build(h, P, nv=c.shape[0])
+    n = num["ndof"]
+    x = x_uniform(30 + P, n)
+    space = F.Space(F.Mesh(c, h), P)
+    assert space.ndof == n == 20346417
+    # samples: every kind of DOF (vertices, edges, faces, interiors), on and
+    # off the boundary, plus uniformly drawn ones
+    rng = np.random.default_rng(5)
+    nv = c.shape[0]
+    n_edge_dofs = num["n_edges"] * (P - 1)
+    n_face_dofs = num["n_faces"] * (P - 1) ** 2
+    starts = [0, nv, nv + n_edge_dofs, nv + n_edge_dofs + n_face_dofs, n]
+    rows = [rng.integers(starts[k], starts[k + 1], 12) for k in range(4)]
+    rows.append(rng.choice(num["boundary_dofs"], 12, replace=False))
+    rows.append(rng.integers(0, n, 20))
+    rows = np.unique(np.concatenate(rows))
+    return {"c": c, "h": h, "kap": kap, "num": num, "x": x, "space": space, "rows": rows, "F": F}
+
+
+def _sampled(full, kind):
+    return assemble.sampled_apply(full["c"], full["h"], full["num"]["e2l"], P, Q, kind, full["kap"], full["x"],
+                                  full["rows"])
+
+
+@pytest.mark.parametrize("kind", ["diffusion", "mass"])
+def test_sampled_rows(full, kind):
+    import torch
+    F = full["F"]
+    form = F.Form(full["space"], kind, Q, coef=cuda(full["kap"]))
+    xd = cuda(full["x"])
+    y = torch.empty_like(xd)
+    ref = _sampled(full, kind)
+    scale = np.abs(ref).max()
+    rows = torch.as_tensor(full["rows"], device="cuda")
+    form.apply(xd, y)
+    assert np.abs(y[rows].cpu().numpy() - ref).max() <= 1e-12 * scale
+    form.apply(xd, y, arith="df64")
+    assert np.abs(y[rows].cpu().numpy() - ref).max() <= 1e-12 * scale
+    y32 = torch.empty(xd.numel(), dtype=torch.float32, device="cuda")
+    form.apply(xd.float(), y32)
+    assert np.abs(y32[rows].double().cpu().numpy() - ref).max() <= 2e-5 * scale
+
+
+def test_properties_on_the_whole_vector(full):
+    """Constants in the diffusion kernel, symmetry u.(A v) = v.(A u), and
+    positivity of u.(A u), evaluated on all 20.3M entries."""
+    import torch
+    F = full["F"]
+    form = F.Form(full["space"], "diffusion", Q, coef=cuda(full["kap"]))
+    n = full["space"].ndof
+    one = torch.ones(n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(one)
+    form.apply(one, y)
+    u = cuda(full["x"])
+    v = cuda(x_uniform(99, n))
+    Au, Av = torch.empty_like(u), torch.empty_like(u)
+    form.apply(u, Au)
+    form.apply(v, Av)
+    assert y.abs().max().item() <= 1e-12 * Au.abs().max().item()
+    a, b = torch.dot(u, Av).item(), torch.dot(v, Au).item()
+    assert abs(a - b) <= 1e-12 * (u.abs() * Av.abs()).sum().item()
+    assert torch.dot(u, Au).item() > 0
