@@ -227,8 +227,10 @@ def run_reference(args):
     return 0
 
 
-SWEEP_N = {"4e6": {1: 158, 2: 79, 3: 53, 4: 39, 5: 32, 6: 26, 7: 23, 8: 20},
-           "2e7": {1: 270, 2: 135, 3: 90, 4: 68, 5: 54, 6: 45, 7: 39, 8: 34}}
+SWEEP_N = {"1e6": {1: 99, 2: 49, 3: 33, 4: 25, 5: 20, 6: 16, 7: 14, 8: 12},
+           "4e6": {1: 158, 2: 79, 3: 53, 4: 39, 5: 32, 6: 26, 7: 23, 8: 20},
+           "2e7": {1: 270, 2: 135, 3: 90, 4: 68, 5: 54, 6: 45, 7: 39, 8: 34},
+           "3e7": {1: 310, 2: 155, 3: 103, 4: 77, 5: 62, 6: 52, 7: 44, 8: 39}}
 
 
 def _sin_rhs(form, b):
@@ -640,7 +642,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--solve-maxit", type=int, default=20000)
     ap.add_argument("--workload", default="apply", choices=["apply", "sweep", "batch", "grad", "paper2d", "mg", "curved"])
-    ap.add_argument("--sweep-size", default="4e6", choices=["4e6", "2e7"])
+    ap.add_argument("--sweep-size", default="4e6", choices=["1e6", "4e6", "2e7", "3e7"])
     ap.add_argument("--orders", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--nprob", type=int, default=256)
     ap.add_argument("--nrhs", type=int, default=8)
