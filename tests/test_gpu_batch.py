@@ -132,3 +132,25 @@ def test_batch_rejects_high_order():
     with pytest.raises(F.FemError) as ei:
         F.Batch([form], 2)
     assert "FEM_EUNSUPPORTED" in str(ei.value)
+
+
+@pytest.mark.parametrize("kind", ["diffusion", "mass"])
+def test_vector_form_is_a_one_problem_batch(kind):
+    """A vector mass / diffusion form (the scalar operator on each of vdim
+    components with the same D, components node-major) is a batch of one
+    problem with nrhs = vdim: against the oracle's block-diagonal I (x) A."""
+    import scipy.sparse as sp
+    import torch
+    import paper_1911_09220_gb300 as F
+    c, h = make_mesh(3, seed=77, shuffle=True, drop=2)
+    kappa = lognormal(78, h.shape[0])
+    space = F.Space(F.Mesh(c, h), 3)
+    form = F.Form(space, kind, 5, coef=cuda(kappa))
+    prob = assemble.Problem(c, h, 3, 5, kappa=kappa, rho=kappa)
+    vdim = 3
+    bt = F.Batch([form], vdim)
+    X = cuda(x_uniform(79, bt.total_len))
+    Y = torch.empty_like(X)
+    bt.apply(X, Y)
+    A = sp.kron(sp.identity(vdim), prob.matrix(kind)).tocsr()
+    assert relerr(Y.cpu().numpy(), A @ X.cpu().numpy()) <= TOL
