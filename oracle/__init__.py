@@ -30,6 +30,8 @@ matrix with the same quadrature):
 * curved elements: the order-k nodal geometry of Sec. 3.1 in place of the
   trilinear map (`curved`);
 * the convection operator (beta . grad u, v) (`convection`);
+* linear elasticity on vector H1, lambda div div + 2 mu eps:eps
+  (`elasticity`);
 * p-multigrid: level hierarchy, nodal-interpolation transfers, coarse
   essential DOFs, Chebyshev-Jacobi smoothing, the V-cycle and flexible CG
   (`multigrid`; the paper names matrix-free p-multigrid, Sec. 5.2, without
@@ -42,4 +44,4 @@ residual; the error against this FP64 oracle is reported per result).
 """
 
 from . import (rules, lagrange, numbering, element, assemble, solve, gradient, twod, multigrid, curved,  # noqa: F401
-               convection)
+               convection, elasticity)

@@ -1,0 +1,72 @@
+"""Pins for the elasticity oracle: the six rigid-body modes (translations and
+infinitesimal rotations, exactly representable on trilinear meshes) are in
+the kernel on every row; a linear displacement (constant strain) passes the
+patch test on interior rows; the component-diagonal blocks sum to
+(lambda + 4 mu) times the scalar stiffness matrix; symmetry and positive
+semi-definiteness; renumbering invariance."""
+
+import numpy as np
+import pytest
+
+from fem_inputs import hex_lattice, lognormal
+from oracle import assemble, elasticity
+
+
+def _vec(X, f):
+    """Stack f(X) [ndof,3] component-major."""
+    return np.concatenate([f(X)[:, c] for c in range(3)])
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_rigid_modes_patch_and_trace(p):
+    c, h = hex_lattice(3, 0.2, seed=4, shuffle=True)
+    E = h.shape[0]
+    lam, mu = lognormal(1, E), lognormal(2, E)
+    ep = elasticity.ElasticityProblem(c, h, p, p + 2, lam, mu)
+    tri = assemble.Problem(c, h, p, p + 2)
+    X = tri.dof_coords()
+    K = ep.K
+    kmax = abs(K).max()
+    modes = [lambda X, d=d: np.eye(3)[d][None, :] + 0 * X for d in range(3)]
+    for axis in range(3):
+        w = np.eye(3)[axis]
+        modes.append(lambda X, w=w: np.cross(w[None, :], X))
+    for f in modes:
+        assert np.abs(K @ _vec(X, f)).max() <= 1e-12 * kmax
+    # constant strain with constant coefficients: interior rows vanish
+    ep1 = elasticity.ElasticityProblem(c, h, p, p + 2, np.full(E, 1.7), np.full(E, 0.6))
+    A = np.array([[0.3, -0.2, 0.5], [0.1, 0.8, -0.4], [0.7, 0.2, -0.6]])
+    u = _vec(X, lambda X: X @ A.T)
+    inter = np.tile(~tri.num["boundary_mask"], 3)
+    r = ep1.K @ u
+    assert np.abs(r[inter]).max() <= 1e-12 * abs(ep1.K).max()
+    assert np.abs(r).max() > 1e-6        # boundary rows carry the traction
+    # component trace identity
+    n = ep.ndof
+    tr = sum(K[cc * n:(cc + 1) * n, cc * n:(cc + 1) * n] for cc in range(3))
+    Lk = assemble.Problem(c, h, p, p + 2, kappa=lam + 4 * mu).K
+    assert abs(tr - Lk).max() <= 1e-12 * kmax
+    # symmetry, positive semi-definiteness
+    assert abs(K - K.T).max() <= 1e-13 * kmax
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        v = rng.uniform(-1, 1, 3 * n)
+        assert v @ (K @ v) > 0
+
+
+def test_invariance_under_renumbering():
+    p = 2
+    c0, h0 = hex_lattice(2, 0.1, seed=7)
+    c1, h1 = hex_lattice(2, 0.1, seed=7, shuffle=True, shuffle_seed=11)
+    E = h0.shape[0]
+    P0 = elasticity.ElasticityProblem(c0, h0, p, p + 2, np.full(E, 2.0), np.full(E, 0.5))
+    P1 = elasticity.ElasticityProblem(c1, h1, p, p + 2, np.full(E, 2.0), np.full(E, 0.5))
+    X0 = assemble.Problem(c0, h0, p, p + 2).dof_coords()
+    X1 = assemble.Problem(c1, h1, p, p + 2).dof_coords()
+    key = lambda X: np.lexsort(np.round(X, 11).T[::-1])
+    o0, o1 = key(X0), key(X1)
+    perm = np.empty(X0.shape[0], dtype=np.int64)
+    perm[o0] = o1
+    n = X0.shape[0]
+    vperm = np.concatenate([perm + cc * n for cc in range(3)])
+    np.testing.assert_allclose(P1.K.toarray()[np.ix_(vperm, vperm)], P0.K.toarray(), atol=1e-11)
