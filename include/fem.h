@@ -67,7 +67,7 @@ enum {
   FEM_EUNSUPPORTED = 7   /* (p, q1d) or size outside the compiled set */
 };
 
-enum { FEM_MASS = 0, FEM_DIFFUSION = 1, FEM_CONVECTION = 2 };  /* bilinear form kind */
+enum { FEM_MASS = 0, FEM_DIFFUSION = 1, FEM_CONVECTION = 2, FEM_ELASTICITY = 3 };  /* bilinear form kind */
 /* Vector / compute type. FEM_DF64: float64 vectors, element arithmetic in
  * double-float (pairs of floats, 48-bit significand, on the FP32 pipe) with a
  * double-float copy of D made on first use; the operator agrees with the FP64
@@ -180,7 +180,30 @@ fem_status fem_form_create_convection(const fem_space* space, int q1d, const dou
                                       const double* coef, void* stream, fem_form** out);
 /* Replace the velocity of a convection form (recomputes D). */
 fem_status fem_form_set_velocity(fem_form* form, const double* beta_q, void* stream);
-/* Replace the per-element coefficient (recomputes D). */
+/* Linear elasticity a(u, v) = int lambda (div u)(div v) + 2 mu eps(u):eps(v)
+ * on the vector H1 space of three components (Sec. 5.3 lists elasticity
+ * among MFEM's integrators; the paper gives no elasticity kernel, so the
+ * operator is written out from this definition). Vectors of an elasticity
+ * form hold 3 * ndof entries, component-major ("by nodes"): component c of
+ * global DOF i at c * ndof + i; essential DOF ids, the diagonal, the
+ * solution and the load vector use the same numbering. PA stores, per
+ * element and quadrature point, 12 float64 values [ne][q1d^3][12]:
+ * J^-1 (row-major, entry 3 s + r = d xhat_s / d x_r), w det J lambda_e,
+ * w det J mu_e and a zero pad. The apply computes, at every point, the
+ * physical gradient H = Ghat J^-1 of the three components, the scaled
+ * stress S = w det J (lambda tr(H) I + mu (H + H^T)) and F = S J^-T, then
+ * runs the backward gradient stages of the diffusion operator on each
+ * component of F. Its E-vector is [3][ne][(p+1)^3].
+ * lambda, mu: device float64 [ne], per-element Lame coefficients, required.
+ * Hexahedral meshes only; fem_compliance_grad, fem_mg_create and
+ * fem_batch_create reject the form (FEM_EINVAL). fem_rhs takes fq
+ * [3][ne][q1d^3] (the three body-force components). */
+fem_status fem_form_create_elasticity(const fem_space* space, int q1d, const double* lambda,
+                                      const double* mu, void* stream, fem_form** out);
+/* Replace the Lame coefficients of an elasticity form (recomputes D). */
+fem_status fem_form_set_lame(fem_form* form, const double* lambda, const double* mu, void* stream);
+/* Replace the per-element coefficient (recomputes D). Elasticity forms take
+ * fem_form_set_lame instead (FEM_EINVAL). */
 fem_status fem_form_set_coef(fem_form* form, const double* coef, void* stream);
 /* Essential DOF list (device int32 [n], any order, no duplicates needed):
  * defines the constrained operator A_c = (I-E) A (I-E) + E (reading of the
@@ -199,8 +222,8 @@ fem_status fem_form_set_essential(fem_form* form, const int32_t* ess, int64_t n,
 fem_status fem_apply(const fem_form* form, int dtype, const void* x, void* y,
                      int constrained, void* stream);
 /* The two halves of fem_apply with a caller-provided E-vector
- * ye [ne][(p+1)^3] of the vector dtype (float64 for FEM_DF64): element
- * kernel, then scatter. */
+ * ye [ne][(p+1)^3] ([3][ne][(p+1)^3] for elasticity) of the vector dtype
+ * (float64 for FEM_DF64): element kernel, then scatter. */
 fem_status fem_apply_element(const fem_form* form, int dtype, const void* x,
                              void* ye, void* stream);
 fem_status fem_scatter(const fem_form* form, int dtype, const void* ye, void* y,
@@ -214,8 +237,8 @@ fem_status fem_scatter(const fem_form* form, int dtype, const void* ye, void* y,
  * synchronise the device and can fail) is not acceptable.
  * The E-vector scratch is a fixed library-owned device array of 4,194,304
  * doubles (32 MiB), held on every GPU that loads the library until the
- * process exits. Limit: ne * (p+1)^3 <= 4,194,304, else FEM_EINVAL (use
- * fem_apply). x, y: device float64 [ndof], caller-owned, not aliased.
+ * process exits. Limit: ne * (p+1)^3 <= 4,194,304 (three times that for
+ * elasticity), else FEM_EINVAL (use fem_apply). x, y: device float64 [ndof], caller-owned, not aliased.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress with that device current); make that first call
  * before any stream capture. Every call shares the one array: calls that
@@ -228,6 +251,10 @@ fem_status fem_apply_noalloc(const fem_form* form, const double* x, double* y,
  * Sec. 4.4 and Sec. 5.2) ----------------------------------------------------
  * diag_i = sum_e sum_q sum_ab D_ab(q) dphi_i/dxhat_a dphi_i/dxhat_b
  * (diffusion) or sum_e sum_q D(q) phi_i(q)^2 (mass); float64 device [ndof].
+ * Elasticity: [3 * ndof]; component c uses the symmetric 3x3 matrix
+ * w det J ((lambda + mu) a_c a_c^T + mu J^-1 J^-T), a_c = column c of J^-1,
+ * in place of D (the (c, c) block's diagonal); needs ne * q1d^3 * 6
+ * float64 of temporary device memory.
  * constrained != 0 sets diag = 1 on essential DOFs. */
 fem_status fem_assemble_diagonal(const fem_form* form, double* diag,
                                  int constrained, void* stream);

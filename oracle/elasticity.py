@@ -8,17 +8,25 @@ g = J^-T ghat,
   K_e[(c,i),(d,j)] = sum_q w_q detJ_q [ lambda g_c(phi_i) g_d(phi_j)
                      + mu ( delta_cd g(phi_i).g(phi_j) + g_d(phi_i) g_c(phi_j) ) ].
 Global vectors are component-major ("by nodes"): entry c * ndof + i.
+Geometry: the trilinear map of `element.geometry`, or an order-k nodal
+geometry of `curved`.
 """
 
 import numpy as np
 import scipy.sparse as sp
 
-from . import element, numbering
+from . import curved, element, numbering
 
 
 def stiffness(ref, X, lam, mu):
-    """Element matrices [E, 3*D3, 3*D3] (rows/cols component-major)."""
+    """Element matrices [E, 3*D3, 3*D3] (rows/cols component-major) on the
+    trilinear geometry of the corner coordinates X [E, 8, 3]."""
     _, _, det, Jinv = element.geometry(ref, X)
+    return stiffness_from_geometry(ref, det, Jinv, lam, mu)
+
+
+def stiffness_from_geometry(ref, det, Jinv, lam, mu):
+    """Element matrices from det J [E, Q] and J^-1 [E, Q, 3, 3] at the points."""
     g = np.einsum("eqcr,qcd->eqrd", Jinv, ref.dphi)                # [E,Q,3,D] physical gradients
     w = ref.w[None, :] * det                                       # [E,Q]
     lam = np.asarray(lam, dtype=np.float64)
@@ -38,7 +46,10 @@ def stiffness(ref, X, lam, mu):
 
 
 class ElasticityProblem:
-    def __init__(self, coords, hexes, p, q, lam, mu):
+    """Assembled elasticity matrix [3 ndof, 3 ndof]. Xn, k: optional order-k
+    nodal geometry (else the trilinear vertex map)."""
+
+    def __init__(self, coords, hexes, p, q, lam, mu, Xn=None, k=0):
         self.coords = np.asarray(coords, dtype=np.float64)
         self.hexes = np.asarray(hexes, dtype=np.int64)
         self.p, self.q = p, q
@@ -46,7 +57,11 @@ class ElasticityProblem:
         self.ref = element.Reference(p, q)
         self.num = numbering.build(self.hexes, p, nv=self.coords.shape[0])
         self.e2l, self.ndof = self.num["e2l"], self.num["ndof"]
-        Ke = stiffness(self.ref, self.coords[self.hexes], lam, mu)
+        if k:
+            _, _, det, Jinv = curved.geometry(curved.NodalReference(self.ref, k), Xn)
+            Ke = stiffness_from_geometry(self.ref, det, Jinv, lam, mu)
+        else:
+            Ke = stiffness(self.ref, self.coords[self.hexes], lam, mu)
         # vector element DOF list: component c of local DOF i -> c * ndof + e2l[e, i]
         v2l = np.concatenate([self.e2l + c * self.ndof for c in range(3)], axis=1)
         rows = np.repeat(v2l, v2l.shape[1], axis=1).ravel()

@@ -164,6 +164,8 @@ class Form:
     """Partially assembled mass or diffusion form (Sec. 4.3-4.4): setup stores
     D at the quadrature points; apply runs G, B, D, B^T, G^T on the fly."""
 
+    vdim = 1
+
     def __init__(self, space, kind="diffusion", q1d=None, coef=None, stream=None):
         import torch
         L = B.lib()
@@ -177,6 +179,40 @@ class Form:
                                   _stream(stream), C.byref(h)))
         self._h = h
         self.ess = None
+        self.vdim = 1
+
+    @property
+    def n(self):
+        """Length of the form's vectors: vdim * ndof (component-major)."""
+        return self.vdim * self.space.ndof
+
+    @classmethod
+    def elasticity(cls, space, lam, mu, q1d=None, stream=None):
+        """Linear elasticity lambda (div u)(div v) + 2 mu eps(u):eps(v) on the
+        three-component vector space: lam, mu device float64 [ne]. Vectors
+        hold 3 * ndof entries, component c of DOF i at c * ndof + i."""
+        import torch
+        L = B.lib()
+        self = cls.__new__(cls)
+        self.space = space
+        self.kind = B.FEM_ELASTICITY
+        self.q1d = int(q1d) if q1d is not None else space.p + 2
+        self.nq = self.q1d ** space.dim
+        self._coef = None
+        self._lam, self._mu = lam.contiguous(), mu.contiguous()
+        h = C.c_void_p()
+        B.check(L.fem_form_create_elasticity(space._h, self.q1d, _ptr(self._lam, torch.float64, "lam"),
+                                             _ptr(self._mu, torch.float64, "mu"), _stream(stream), C.byref(h)))
+        self._h = h
+        self.ess = None
+        self.vdim = 3
+        return self
+
+    def set_lame(self, lam, mu, stream=None):
+        import torch
+        self._lam, self._mu = lam.contiguous(), mu.contiguous()
+        B.check(B.lib().fem_form_set_lame(self._h, _ptr(self._lam, torch.float64, "lam"),
+                                          _ptr(self._mu, torch.float64, "mu"), _stream(stream)))
 
     @classmethod
     def convection(cls, space, beta, q1d=None, coef=None, stream=None):
@@ -198,6 +234,7 @@ class Form:
                                              _ptr(self._coef, torch.float64, "coef"), _stream(stream), C.byref(h)))
         self._h = h
         self.ess = None
+        self.vdim = 1
         return self
 
     def set_velocity(self, beta, stream=None):

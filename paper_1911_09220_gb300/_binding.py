@@ -12,7 +12,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfem.so")
 
 FEM_OK, FEM_EINVAL, FEM_ENOMEM, FEM_EINVERTED, FEM_ENOCONV, FEM_EBREAKDOWN, FEM_ECUDA, FEM_EUNSUPPORTED = range(8)
-FEM_MASS, FEM_DIFFUSION, FEM_CONVECTION = 0, 1, 2
+FEM_MASS, FEM_DIFFUSION, FEM_CONVECTION, FEM_ELASTICITY = 0, 1, 2, 3
 FEM_F64, FEM_F32, FEM_DF64 = 0, 1, 2
 FEM_SOLVE_F64, FEM_SOLVE_MIXED, FEM_SOLVE_DF64, FEM_SOLVE_MIXED_RU = 0, 1, 2, 3
 
@@ -66,6 +66,8 @@ SIGNATURES = {
     "fem_form_create": (I, [P, I, I, P, P, C.POINTER(P)]),
     "fem_form_create_convection": (I, [P, I, P, P, P, C.POINTER(P)]),
     "fem_form_set_velocity": (I, [P, P, P]),
+    "fem_form_create_elasticity": (I, [P, I, P, P, P, C.POINTER(P)]),
+    "fem_form_set_lame": (I, [P, P, P, P]),
     "fem_form_destroy": (None, [P]),
     "fem_form_set_coef": (I, [P, P, P]),
     "fem_form_set_essential": (I, [P, P, I64, P]),

@@ -489,7 +489,7 @@ extern "C" fem_status fem_space_dof_coords(const fem_space* sp, double* out, voi
 
 // ----------------------------------------------------------------- form ----
 static fem_status form_create(const fem_space* sp, int kind, int q1d, const double* coef, const double* beta,
-                              void* stream, fem_form** out);
+                              const double* mu, void* stream, fem_form** out);
 
 extern "C" fem_status fem_form_create(const fem_space* sp, int kind, int q1d, const double* coef,
                                       void* stream, fem_form** out) {
@@ -497,9 +497,11 @@ extern "C" fem_status fem_form_create(const fem_space* sp, int kind, int q1d, co
   *out = nullptr;
   if (kind == FEM_CONVECTION)
     return fem_fail(FEM_EINVAL, "fem_form_create: convection forms need a velocity (fem_form_create_convection)");
+  if (kind == FEM_ELASTICITY)
+    return fem_fail(FEM_EINVAL, "fem_form_create: elasticity forms need Lame coefficients (fem_form_create_elasticity)");
   if (kind != FEM_MASS && kind != FEM_DIFFUSION)
     return fem_fail(FEM_EINVAL, "fem_form_create: unknown kind %d", kind);
-  return form_create(sp, kind, q1d, coef, nullptr, stream, out);
+  return form_create(sp, kind, q1d, coef, nullptr, nullptr, stream, out);
 }
 
 extern "C" fem_status fem_form_create_convection(const fem_space* sp, int q1d, const double* beta_q,
@@ -507,15 +509,39 @@ extern "C" fem_status fem_form_create_convection(const fem_space* sp, int q1d, c
   if (!sp || !out || !beta_q) return fem_fail(FEM_EINVAL, "fem_form_create_convection: NULL argument");
   *out = nullptr;
   if (sp->mesh->dim != 3) return fem_fail(FEM_EUNSUPPORTED, "fem_form_create_convection: hexahedral meshes only");
-  return form_create(sp, FEM_CONVECTION, q1d, coef, beta_q, stream, out);
+  return form_create(sp, FEM_CONVECTION, q1d, coef, beta_q, nullptr, stream, out);
+}
+
+extern "C" fem_status fem_form_create_elasticity(const fem_space* sp, int q1d, const double* lambda,
+                                                 const double* mu, void* stream, fem_form** out) {
+  if (!sp || !out || !lambda || !mu) return fem_fail(FEM_EINVAL, "fem_form_create_elasticity: NULL argument");
+  *out = nullptr;
+  if (sp->mesh->dim != 3) return fem_fail(FEM_EUNSUPPORTED, "fem_form_create_elasticity: hexahedral meshes only");
+  return form_create(sp, FEM_ELASTICITY, q1d, lambda, nullptr, mu, stream, out);
+}
+
+static fem_status form_setup(fem_form* f, cudaStream_t s);
+
+// Copy the per-element coefficient (NULL: ones) into the form.
+static fem_status copy_coef(fem_form* f, const double* coef, cudaStream_t s) {
+  const int64_t ne = f->space->ne;
+  if (coef) {
+    FEM_CUDA(cudaMemcpyAsync(f->d_coef, coef, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+  } else {
+    std::vector<double> ones(ne, 1.0);
+    FEM_CUDA(cudaMemcpyAsync(f->d_coef, ones.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+  }
+  return FEM_OK;
 }
 
 static fem_status form_create(const fem_space* sp, int kind, int q1d, const double* coef, const double* beta,
-                              void* stream, fem_form** out) {
+                              const double* mu, void* stream, fem_form** out) {
   if (!fem_kernels_supported(sp->p, q1d))
     return fem_fail(FEM_EUNSUPPORTED, "fem_form_create: (p=%d, q1d=%d) not compiled", sp->p, q1d);
   FEM_TRY(fem_apply_tables_init());
   if (sp->mesh->dim == 2) FEM_TRY(fem_2d_tables_init());
+  if (kind == FEM_ELASTICITY) FEM_TRY(fem_elast_tables_init());
   cudaStream_t s = (cudaStream_t)stream;
   fem_form* f = new fem_form();
   f->space = sp;
@@ -523,7 +549,8 @@ static fem_status form_create(const fem_space* sp, int kind, int q1d, const doub
   f->q1d = q1d;
   const int dim = sp->mesh->dim;
   f->nq = dim == 3 ? q1d * q1d * q1d : q1d * q1d;
-  f->ncomp = (kind == FEM_DIFFUSION) ? (dim == 3 ? 6 : 3) : kind == FEM_CONVECTION ? 3 : 1;
+  f->ncomp = (kind == FEM_DIFFUSION) ? (dim == 3 ? 6 : 3) : kind == FEM_CONVECTION ? 3 : kind == FEM_ELASTICITY ? 12 : 1;
+  f->vdim = kind == FEM_ELASTICITY ? 3 : 1;
   std::vector<double> pts, wts, B, G;
   fem_gauss_rule(q1d, pts, wts);
   fem_lagrange_tables(sp->nodes, pts, B, G);
@@ -554,7 +581,13 @@ static fem_status form_create(const fem_space* sp, int kind, int q1d, const doub
   up(&f->d_qwts, wts);
   if (st == FEM_OK) st = dev_alloc(&f->d_coef, (size_t)sp->ne);
   if (st == FEM_OK) st = dev_alloc(&f->d_D, (size_t)sp->ne * f->ncomp * f->nq + 2);  // +16 bytes slack
-  if (st == FEM_OK) st = dev_alloc((double**)&f->d_ye, (size_t)sp->ne * sp->nd);
+  if (st == FEM_OK) st = dev_alloc((double**)&f->d_ye, (size_t)f->vdim * sp->ne * sp->nd);
+  if (st == FEM_OK && mu) {
+    st = dev_alloc(&f->d_mu, (size_t)sp->ne);
+    if (st == FEM_OK &&
+        cudaMemcpyAsync(f->d_mu, mu, sizeof(double) * sp->ne, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      st = fem_fail(FEM_ECUDA, "fem_form_create: mu copy failed");
+  }
   if (st == FEM_OK) st = dev_alloc(&f->d_flag, 4);
   if (st == FEM_OK && cudaMallocHost((void**)&f->h_pinned, 64) != cudaSuccess)
     st = fem_fail(FEM_ENOMEM, "fem_form_create: pinned host allocation failed");
@@ -568,12 +601,12 @@ static fem_status form_create(const fem_space* sp, int kind, int q1d, const doub
     fem_form_destroy(f);
     return st;
   }
-  st = fem_form_set_coef(f, coef, stream);
+  st = copy_coef(f, coef, s);
+  if (st == FEM_OK) st = form_setup(f, s);
   if (st != FEM_OK) {
     fem_form_destroy(f);
     return st;
   }
-  (void)s;
   *out = f;
   return FEM_OK;
 }
@@ -596,19 +629,20 @@ fem_status fem_form_geo_tables(const fem_form* fc) {
   return FEM_OK;
 }
 
-static fem_status form_setup(fem_form* f, cudaStream_t s);
-
 extern "C" fem_status fem_form_set_coef(fem_form* f, const double* coef, void* stream) {
   if (!f) return fem_fail(FEM_EINVAL, "fem_form_set_coef: NULL form");
+  if (f->kind == FEM_ELASTICITY) return fem_fail(FEM_EINVAL, "fem_form_set_coef: elasticity forms take fem_form_set_lame");
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t ne = f->space->ne;
-  if (coef) {
-    FEM_CUDA(cudaMemcpyAsync(f->d_coef, coef, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
-  } else {
-    std::vector<double> ones(ne, 1.0);
-    FEM_CUDA(cudaMemcpyAsync(f->d_coef, ones.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, s));
-    FEM_CUDA(cudaStreamSynchronize(s));
-  }
+  FEM_TRY(copy_coef(f, coef, s));
+  return form_setup(f, s);
+}
+
+extern "C" fem_status fem_form_set_lame(fem_form* f, const double* lambda, const double* mu, void* stream) {
+  if (!f || !lambda || !mu) return fem_fail(FEM_EINVAL, "fem_form_set_lame: NULL argument");
+  if (f->kind != FEM_ELASTICITY) return fem_fail(FEM_EINVAL, "fem_form_set_lame: not an elasticity form");
+  cudaStream_t s = (cudaStream_t)stream;
+  FEM_TRY(copy_coef(f, lambda, s));
+  FEM_CUDA(cudaMemcpyAsync(f->d_mu, mu, sizeof(double) * f->space->ne, cudaMemcpyDeviceToDevice, s));
   return form_setup(f, s);
 }
 
@@ -637,6 +671,7 @@ extern "C" fem_status fem_form_set_velocity(fem_form* f, const double* beta, voi
 extern "C" void fem_form_destroy(fem_form* f) {
   if (!f) return;
   dev_free(f->d_coef);
+  dev_free(f->d_mu);
   dev_free(f->d_D);
   dev_free(f->d_D32);
   dev_free(f->d_B);
@@ -666,7 +701,7 @@ extern "C" fem_status fem_form_set_essential(fem_form* f, const int32_t* ess, in
   if (!f) return fem_fail(FEM_EINVAL, "fem_form_set_essential: NULL form");
   if (n < 0 || (n > 0 && !ess)) return fem_fail(FEM_EINVAL, "fem_form_set_essential: bad list");
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t ndof = f->space->ndof;
+  const int64_t ndof = fem_form_len(f);
   if (!f->d_ess_mask) FEM_TRY(dev_alloc(&f->d_ess_mask, (size_t)ndof));
   dev_free(f->d_ess);
   f->n_ess = n;

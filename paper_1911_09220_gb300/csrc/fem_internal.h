@@ -77,8 +77,10 @@ struct fem_space {
 struct fem_form {
   const fem_space* space = nullptr;
   int kind = FEM_DIFFUSION;
-  int q1d = 0, nq = 0, ncomp = 0;  // nq = q1d^3, ncomp 6 or 1
-  double* d_coef = nullptr;        // [ne]
+  int q1d = 0, nq = 0, ncomp = 0;  // nq = q1d^3; ncomp 6, 3, 1 or 12 (elasticity)
+  int vdim = 1;                    // vector components per DOF (3 for elasticity)
+  double* d_coef = nullptr;        // [ne] (elasticity: lambda)
+  double* d_mu = nullptr;          // elasticity: mu [ne]
   double* d_D = nullptr;           // [ne][ncomp][nq]
   float* d_D32 = nullptr;          // lazily made float copy
   double* d_B = nullptr;           // [q1d][D1] basis values at Gauss points
@@ -110,6 +112,9 @@ struct fem_form {
   int geo_k = 0;
 };
 
+// Length of the form's vectors: vdim * ndof (component-major).
+inline int64_t fem_form_len(const fem_form* f) { return (int64_t)f->vdim * f->space->ndof; }
+
 // ---------------------------------------------------------------- basis -----
 // 1D tables on [0,1]: GLL nodes (D1 = p+1), Gauss-Legendre points/weights (q),
 // B[k][j] = l_j(x_k), G[k][j] = l_j'(x_k) for GLL Lagrange polynomials l_j.
@@ -133,6 +138,11 @@ fem_status fem_launch_scatter(const fem_form* f, int dtype, const void* ye, void
 fem_status fem_launch_zero_ess(const fem_form* f, int dtype, const void* x, void* xz,
                                cudaStream_t s);
 fem_status fem_launch_diag_element(const fem_form* f, double* ye, cudaStream_t s);
+// Elasticity element kernel (k_elasticity.cu) and its diagonal helper: the
+// 6-component matrix of component c at every point, [ne][q1d^3][6].
+fem_status fem_launch_apply_elasticity(const fem_form* f, int dtype, const void* x, void* ye, cudaStream_t s,
+                                       const int* skip);
+fem_status fem_launch_elasticity_diag_D(const fem_form* f, int c, double* Dc, cudaStream_t s);
 fem_status fem_launch_rhs_element(const fem_form* f, const double* fq, double* ye,
                                   cudaStream_t s);
 fem_status fem_launch_grad(const fem_form* f, const double* u, double* g, cudaStream_t s);
@@ -145,6 +155,7 @@ int fem_scatter_blocks(int64_t ndof);
 fem_status fem_apply_tables_init();
 fem_status fem_batch_tables_init();
 fem_status fem_2d_tables_init();
+fem_status fem_elast_tables_init();
 // Quadrilateral (2D) counterparts, dispatched on mesh->dim == 2 (k_2d.cu).
 fem_status fem_launch_setup_2d(const fem_form* f, cudaStream_t s);
 fem_status fem_launch_qpoint_coords_2d(const fem_form* f, double* xq, cudaStream_t s);

@@ -63,25 +63,36 @@ fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G
 // (y_i = xin_i where mask_i) and per-block partial sums of xin . y. Each
 // thread keeps kU DOFs in flight (their off -> idx -> ye load chains are
 // independent), the DOFs of one round being kU grid strides apart so that
-// every load stays coalesced across the warp.
-template <typename T>
+// every load stays coalesced across the warp. VD = 3: vector entries
+// i in [0, 3 ndof), component c = i / ndof of DOF i - c ndof, whose slots
+// are read from the E-vector component ye + c * nend.
+template <typename T, int VD = 1>
 __global__ void k_scatter(const int* __restrict__ skip, int64_t ndof, const int32_t* __restrict__ off,
                           const int32_t* __restrict__ idx, const T* __restrict__ ye, T* __restrict__ y,
                           const uint8_t* __restrict__ mask, const T* __restrict__ xin,
-                          double* __restrict__ pdot) {
+                          double* __restrict__ pdot, int64_t nend = 0) {
   constexpr int kU = 4;
   __shared__ double red[32];
   if (skip && *skip) return;
   double acc = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < ndof; base += stride * kU) {
+  const int64_t n = VD * ndof;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < n; base += stride * kU) {
     int32_t a[kU], b[kU];
+    const T* yc[kU];
     int len = 0;
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int64_t i = base + u * stride;
-      a[u] = i < ndof ? __ldg(off + i) : 0;
-      b[u] = i < ndof ? __ldg(off + i + 1) : 0;
+      int64_t li = i;
+      yc[u] = ye;
+      if (VD > 1) {
+        const int c = (i >= ndof) + (i >= 2 * ndof);
+        li = i - c * ndof;
+        yc[u] = ye + c * nend;
+      }
+      a[u] = i < n ? __ldg(off + li) : 0;
+      b[u] = i < n ? __ldg(off + li + 1) : 0;
       len = max(len, b[u] - a[u]);
     }
     T sum[kU];
@@ -93,12 +104,12 @@ __global__ void k_scatter(const int* __restrict__ skip, int64_t ndof, const int3
       for (int u = 0; u < kU; ++u) sl[u] = a[u] + j < b[u] ? __ldg(idx + a[u] + j) : -1;
 #pragma unroll
       for (int u = 0; u < kU; ++u)
-        if (sl[u] >= 0) sum[u] += __ldg(ye + sl[u]);
+        if (sl[u] >= 0) sum[u] += __ldg(yc[u] + sl[u]);
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int64_t i = base + u * stride;
-      if (i < ndof) {
+      if (i < n) {
         T v = sum[u];
         if (mask && mask[i]) v = xin[i];
         y[i] = v;
@@ -179,6 +190,7 @@ fem_status fem_form_ensure_df64(const fem_form* fc, cudaStream_t s) {
 fem_status fem_launch_apply_element(const fem_form* f, int dtype, const void* x, void* ye, cudaStream_t s,
                                     const int* skip) {
   if (f->space->mesh->dim == 2) return fem_launch_apply_element_2d(f, dtype, x, ye, s, skip);
+  if (f->kind == FEM_ELASTICITY) return fem_launch_apply_elasticity(f, dtype, x, ye, s, skip);
   const int p = f->space->p, q = f->q1d;
   if (dtype == FEM_F64) {
 #define X(P, Q)                                                                                            \
@@ -212,19 +224,28 @@ fem_status fem_launch_apply_element(const fem_form* f, int dtype, const void* x,
 fem_status fem_launch_scatter(const fem_form* f, int dtype, const void* ye, void* y, const uint8_t* mask,
                               const void* xin, double* pdot, int nblocks, cudaStream_t s, const int* skip) {
   const fem_space* sp = f->space;
-  const int grid = nblocks > 0 ? nblocks : fem_scatter_blocks(sp->ndof);
-  if (dtype == FEM_F64)
+  const int grid = nblocks > 0 ? nblocks : fem_scatter_blocks(fem_form_len(f));
+  const int64_t nend = sp->ne * (int64_t)sp->nd;
+  if (f->vdim == 3) {
+    if (dtype == FEM_F64)
+      k_scatter<double, 3><<<grid, 256, 0, s>>>(skip, sp->ndof, sp->d_l2e_off, sp->d_l2e_idx, (const double*)ye,
+                                                (double*)y, mask, (const double*)xin, pdot, nend);
+    else
+      k_scatter<float, 3><<<grid, 256, 0, s>>>(skip, sp->ndof, sp->d_l2e_off, sp->d_l2e_idx, (const float*)ye,
+                                               (float*)y, mask, (const float*)xin, pdot, nend);
+  } else if (dtype == FEM_F64) {
     k_scatter<double><<<grid, 256, 0, s>>>(skip, sp->ndof, sp->d_l2e_off, sp->d_l2e_idx, (const double*)ye,
                                            (double*)y, mask, (const double*)xin, pdot);
-  else
+  } else {
     k_scatter<float><<<grid, 256, 0, s>>>(skip, sp->ndof, sp->d_l2e_off, sp->d_l2e_idx, (const float*)ye,
                                           (float*)y, mask, (const float*)xin, pdot);
+  }
   FEM_LAUNCHED();
   return FEM_OK;
 }
 
 fem_status fem_launch_zero_ess(const fem_form* f, int dtype, const void* x, void* xz, cudaStream_t s) {
-  const int64_t n = f->space->ndof;
+  const int64_t n = fem_form_len(f);
   if (dtype == FEM_F64)
     k_zero_ess<double><<<grid_for(n, 256), 256, 0, s>>>(n, (const double*)x, f->d_ess_mask, (double*)xz);
   else
@@ -277,7 +298,7 @@ extern "C" fem_status fem_apply(const fem_form* fc, int dtype, const void* x, vo
     return fem_fail(FEM_EINVAL, "fem_apply: constrained apply needs fem_form_set_essential");
   void* ye = f->d_ye;  // sized for doubles; float E-vectors use the front half
   if (constrained) {
-    FEM_TRY(ensure_work(f, vt, (size_t)f->space->ndof));
+    FEM_TRY(ensure_work(f, vt, (size_t)fem_form_len(f)));
     void* xz = vt == FEM_F64 ? (void*)f->d_work64 : (void*)f->d_work32;
     FEM_TRY(fem_launch_zero_ess(f, vt, x, xz, s));
     FEM_TRY(fem_launch_apply_element(f, dtype, xz, ye, s));

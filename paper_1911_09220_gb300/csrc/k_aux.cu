@@ -274,14 +274,15 @@ fem_status set_smem(K kernel, size_t bytes) {
   return FEM_OK;
 }
 
+// kind FEM_DIFFUSION reads D as [ne][nq][6], FEM_MASS as [ne][nq].
 template <int P, int Q>
-fem_status launch_diag(const fem_form* f, double* ye, cudaStream_t s) {
+fem_status launch_diag(const fem_form* f, const double* D, int kind, double* ye, cudaStream_t s) {
   constexpr int D1 = P + 1, NE = ne_per_block_aux(P);
   const int ne = (int)f->space->ne;
   const size_t bytes = sizeof(double) * NE * (D1 * Q * Q + 3 * D1 * D1 * Q);
   auto k = k_diag<D1, Q, NE>;
   FEM_TRY(set_smem(k, bytes));
-  k<<<(ne + NE - 1) / NE, dim3(Q, Q, NE), bytes, s>>>(ne, f->kind, f->d_D, f->d_B, f->d_G, ye);
+  k<<<(ne + NE - 1) / NE, dim3(Q, Q, NE), bytes, s>>>(ne, kind, D, f->d_B, f->d_G, ye);
   FEM_LAUNCHED();
   return FEM_OK;
 }
@@ -319,24 +320,53 @@ fem_status launch_grad(const fem_form* f, const double* u, double* g, cudaStream
 
 }  // namespace
 
-fem_status fem_launch_diag_element(const fem_form* f, double* ye, cudaStream_t s) {
-  if (f->space->mesh->dim == 2) return fem_launch_diag_element_2d(f, ye, s);
+static fem_status diag_pq(const fem_form* f, const double* D, int kind, double* ye, cudaStream_t s) {
   const int p = f->space->p, q = f->q1d;
 #define X(P, Q) \
-  if (p == P && q == Q) return launch_diag<P, Q>(f, ye, s);
+  if (p == P && q == Q) return launch_diag<P, Q>(f, D, kind, ye, s);
   FEM_FOR_EACH_PQ(X)
 #undef X
   return fem_fail(FEM_EUNSUPPORTED, "diag: (p=%d, q1d=%d) not compiled", p, q);
 }
 
+fem_status fem_launch_diag_element(const fem_form* f, double* ye, cudaStream_t s) {
+  if (f->space->mesh->dim == 2) return fem_launch_diag_element_2d(f, ye, s);
+  if (f->kind != FEM_ELASTICITY) return diag_pq(f, f->d_D, f->kind, ye, s);
+  // elasticity: the (c, c) block's diagonal is the diffusion diagonal with
+  // the per-point matrix D^c; one temporary [ne][nq][6] reused for c = 0..2
+  double* Dc = nullptr;
+  FEM_TRY(dev_alloc(&Dc, (size_t)f->space->ne * f->nq * 6));
+  fem_status st = FEM_OK;
+  const size_t nend = (size_t)f->space->ne * f->space->nd;
+  for (int c = 0; c < 3 && st == FEM_OK; ++c) {
+    st = fem_launch_elasticity_diag_D(f, c, Dc, s);
+    if (st == FEM_OK) st = diag_pq(f, Dc, FEM_DIFFUSION, ye + c * nend, s);
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess && st == FEM_OK)
+    st = fem_fail(FEM_ECUDA, "diag: %s", cudaGetErrorString(cudaGetLastError()));
+  dev_free(Dc);
+  return st;
+}
+
 fem_status fem_launch_rhs_element(const fem_form* f, const double* fq, double* ye, cudaStream_t s) {
   if (f->space->mesh->dim == 2) return fem_launch_rhs_element_2d(f, fq, ye, s);
   const int p = f->space->p, q = f->q1d;
-#define X(P, Q) \
-  if (p == P && q == Q) return launch_rhs<P, Q>(f, fq, ye, s);
-  FEM_FOR_EACH_PQ(X)
+  // vector forms: component c of fq [vdim][ne][nq] into ye [vdim][ne][nd]
+  const size_t nq = (size_t)f->space->ne * f->nq, nend = (size_t)f->space->ne * f->space->nd;
+  for (int c = 0; c < f->vdim; ++c) {
+    bool done = false;
+    fem_status st = FEM_OK;
+#define X(P, Q)                                                \
+  if (!done && p == P && q == Q) {                             \
+    st = launch_rhs<P, Q>(f, fq + c * nq, ye + c * nend, s);   \
+    done = true;                                               \
+  }
+    FEM_FOR_EACH_PQ(X)
 #undef X
-  return fem_fail(FEM_EUNSUPPORTED, "rhs: (p=%d, q1d=%d) not compiled", p, q);
+    if (!done) return fem_fail(FEM_EUNSUPPORTED, "rhs: (p=%d, q1d=%d) not compiled", p, q);
+    if (st != FEM_OK) return st;
+  }
+  return FEM_OK;
 }
 
 fem_status fem_launch_grad(const fem_form* f, const double* u, double* g, cudaStream_t s) {
@@ -358,7 +388,7 @@ extern "C" fem_status fem_assemble_diagonal(const fem_form* f, double* diag, int
   FEM_TRY(fem_launch_diag_element(f, (double*)f->d_ye, s));
   FEM_TRY(fem_launch_scatter(f, FEM_F64, f->d_ye, diag, nullptr, nullptr, nullptr, 0, s));
   if (constrained) {
-    const int64_t n = f->space->ndof;
+    const int64_t n = fem_form_len(f);
     k_set_ess<<<grid_for(n, 256), 256, 0, s>>>(n, f->d_ess_mask, diag, 1.0);
     FEM_LAUNCHED();
   }
@@ -384,7 +414,7 @@ extern "C" fem_status fem_lift_rhs(const fem_form* fc, const double* b, const do
   if (bc == b || bc == g) return fem_fail(FEM_EINVAL, "fem_lift_rhs: bc must not alias b or g");
   fem_form* f = const_cast<fem_form*>(fc);
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t n = f->space->ndof;
+  const int64_t n = fem_form_len(f);
   // scratch: [0,n) essential part of g, [n,2n) A applied to it
   if (f->work64_len < (size_t)2 * n) {
     dev_free(f->d_work64);

@@ -646,6 +646,10 @@ extern "C" fem_status fem_batch_create(const fem_form* const* forms, int nprob, 
       delete b;
       return fem_fail(FEM_EUNSUPPORTED, "fem_batch_create: form %d is a convection form", i);
     }
+    if (f->kind == FEM_ELASTICITY) {
+      delete b;
+      return fem_fail(FEM_EINVAL, "fem_batch_create: form %d is an elasticity form", i);
+    }
     if (sp->mesh->dim != 3) {
       delete b;
       return fem_fail(FEM_EUNSUPPORTED, "fem_batch_create: form %d is on a 2D mesh; batches hold hexahedra", i);

@@ -152,6 +152,39 @@ __device__ __forceinline__ void d_load6(const df64* p, df64* d) {
   }
 }
 
+// The twelve values of one elasticity point record (J^-1 row-major, w det J
+// lambda, w det J mu, pad): 96-byte records for double and double-float,
+// 48-byte for float, loaded as 16-byte vectors.
+__device__ __forceinline__ void d_load12(const double* p, double* d) {
+  const double2* v = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double2 w = __ldg(v + k);
+    d[2 * k] = w.x;
+    d[2 * k + 1] = w.y;
+  }
+}
+__device__ __forceinline__ void d_load12(const float* p, float* d) {
+  const float4* v = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4 w = __ldg(v + k);
+    d[4 * k] = w.x;
+    d[4 * k + 1] = w.y;
+    d[4 * k + 2] = w.z;
+    d[4 * k + 3] = w.w;
+  }
+}
+__device__ __forceinline__ void d_load12(const df64* p, df64* d) {
+  const float4* v = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float4 w = __ldg(v + k);
+    d[2 * k] = df64(w.x, w.y);
+    d[2 * k + 1] = df64(w.z, w.w);
+  }
+}
+
 // ------------------------------------------------ staged D (bulk copy) ----
 // One thread of the block copies the block's contiguous D tile from global
 // to shared memory with a single cp.async.bulk whose completion is counted on
@@ -457,6 +490,69 @@ struct Lines {
     eo_line<T, D1, Q, 1, BT>(g0, t0);
   }
 
+  // ---- elasticity: three components, each with its own slab (component c
+  // of the element at s + c * SE). The forward stages d1, d2 and the
+  // backward stages d3_store, d4, d5 are the diffusion ones run on each
+  // component; S3 couples the components through the stress at each point:
+  //   H[c][r] = sum_s gh[c][s] M[s][r]          (physical gradient, M = J^-1)
+  //   S = lw tr(H) I + mw (H + H^T)             (lw, mw = w det J lambda, mu)
+  //   F[c][s] = sum_r S[c][r] M[s][r]           (= S J^-T)
+  // out[c][0..2] are the back-z lines of F[c][0..2] (the t0, t1, t2 of d3).
+  __device__ static void e3(int t, bool valid, const T* __restrict__ De, T* s, T (&out)[3][3][D1]) {
+    const int qy = t / Q, qx = t % Q;
+    T g[3][3][Q];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T* sc = s + c * L::SE;
+      T rbb[D1], rgb[D1], rbg[D1];
+      const T *sbb = BB(sc) + qy * RC + qx, *sgb = GB(sc) + qy * RC + qx, *sbg = BG(sc) + qy * RC + qx;
+#pragma unroll
+      for (int z = 0; z < D1; ++z) {
+        rbb[z] = sbb[z * Q];
+        rgb[z] = sgb[z * Q];
+        rbg[z] = sbg[z * Q];
+      }
+      eo_line<T, Q, D1, 1, BF>(rgb, g[c][0]);
+      eo_line<T, Q, D1, 1, BF>(rbg, g[c][1]);
+      eo_line<T, Q, D1, -1, GF>(rbb, g[c][2]);
+    }
+    const T* Dp = De + (size_t)t * 12;  // point-major: [q][12]
+#pragma unroll
+    for (int qz = 0; qz < Q; ++qz) {
+      T m[12];
+      if (valid) {
+        d_load12(Dp + (size_t)qz * QQ * 12, m);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) m[k] = 0;
+      }
+      T H[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          H[c][r] = fe_norm(g[c][0][qz] * m[r] + g[c][1][qz] * m[3 + r] + g[c][2][qz] * m[6 + r]);
+      const T lt = fe_norm(m[9] * fe_norm(fe_norm(H[0][0] + H[1][1]) + H[2][2])), mw = m[10];
+      T S[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) S[c][c] = fe_norm(lt + mw * fe_norm(H[c][c] + H[c][c]));
+      S[0][1] = S[1][0] = fe_norm(mw * fe_norm(H[0][1] + H[1][0]));
+      S[0][2] = S[2][0] = fe_norm(mw * fe_norm(H[0][2] + H[2][0]));
+      S[1][2] = S[2][1] = fe_norm(mw * fe_norm(H[1][2] + H[2][1]));
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          g[c][a][qz] = fe_norm(S[c][0] * m[3 * a] + S[c][1] * m[3 * a + 1] + S[c][2] * m[3 * a + 2]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      eo_line<T, D1, Q, 1, BT>(g[c][0], out[c][0]);
+      eo_line<T, D1, Q, 1, BT>(g[c][1], out[c][1]);
+      eo_line<T, D1, Q, -1, GT>(g[c][2], out[c][2]);
+    }
+  }
+
   // ---- mass (B only, one D per point)
   __device__ static void m1(int t, T* s) {
     T xr[D1], bx[Q];
@@ -613,6 +709,51 @@ __device__ __forceinline__ void mass_block(int tid, int e0, int nel, const int32
   if (tid < nel * N2) Ln::m4(tid % N2, sm + (tid / N2) * SE);
   __syncthreads();
   if (tid < nel * N1) Ln::template m5<TX>(tid % N1, sm + (tid / N1) * SE, ye + (size_t)(e0 + tid / N1) * ND);
+}
+
+// Linear elasticity on the three components of a vector H1 field
+// (component-major vectors: component c of DOF i at c * ndof + i; E-vector
+// [3][ne][D1^3]). The block's NT threads own NE planes of Q*Q threads for
+// S3 (one point line of one element each); every other stage loops its
+// lines of all (element, component) slabs over the block's threads, slab
+// (el, c) at sm + (3 el + c) SE. D block: Dq + e * 12 Q^3.
+template <typename T, int D1, int Q, int NT, typename TX = T>
+__device__ __forceinline__ void elasticity_block(int tid, int e0, int nel, int ne, int64_t ndof,
+                                                 const int32_t* __restrict__ e2l, const T* __restrict__ Dq, T* sm,
+                                                 const TX* __restrict__ x, TX* __restrict__ ye) {
+  using Ln = Lines<T, D1, Q>;
+  constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
+  constexpr int N1 = D1 * D1, N2 = D1 * Q, XP = Ln::XP;
+  // gather: one map entry, three component values
+  for (int i = tid; i < nel * ND; i += NT) {
+    const int el = i / ND, k = i % ND;
+    const int32_t g = __ldg(e2l + (size_t)(e0 + el) * ND + k);
+    const TX v0 = __ldg(x + g), v1 = __ldg(x + ndof + g), v2 = __ldg(x + 2 * ndof + g);
+    T* sx = sm + 3 * el * SE + (k / D1) * XP + k % D1;
+    sx[0] = fe_from<T>(v0);
+    sx[SE] = fe_from<T>(v1);
+    sx[2 * SE] = fe_from<T>(v2);
+  }
+  __syncthreads();
+  for (int i = tid; i < 3 * nel * N1; i += NT) Ln::d1(i % N1, sm + (i / N1) * SE);
+  __syncthreads();
+  for (int i = tid; i < 3 * nel * N2; i += NT) Ln::d2(i % N2, sm + (i / N2) * SE);
+  __syncthreads();
+  const int el = tid / QQ, t = tid % QQ;
+  const bool valid = el < nel;
+  const size_t ev = valid ? (size_t)(e0 + el) : 0;
+  T out[3][3][D1];
+  Ln::e3(t, valid, Dq + ev * 12 * NQ, sm + 3 * el * SE, out);
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 3; ++c) Ln::d3_store(t, sm + (3 * el + c) * SE, out[c][0], out[c][1], out[c][2]);
+  __syncthreads();
+  for (int i = tid; i < 3 * nel * N2; i += NT) Ln::d4(i % N2, sm + (i / N2) * SE);
+  __syncthreads();
+  for (int i = tid; i < 3 * nel * N1; i += NT) {
+    const int sl = i / N1, l = sl / 3, c = sl % 3;
+    Ln::template d5<TX>(i % N1, sm + sl * SE, ye + ((size_t)c * ne + e0 + l) * ND);
+  }
 }
 
 // Hint the L2 to fetch a contiguous byte range with one bulk prefetch

@@ -818,7 +818,8 @@ extern "C" fem_status fem_mg_create(const fem_form* fine, const fem_mg_opts* opt
   *out = nullptr;
   if (!fine->d_ess_mask) return fem_fail(FEM_EINVAL, "fem_mg_create: call fem_form_set_essential first (n may be 0)");
   if (fine->space->mesh->dim != 3) return fem_fail(FEM_EUNSUPPORTED, "fem_mg_create: hexahedral meshes only");
-  if (fine->kind == FEM_CONVECTION) return fem_fail(FEM_EINVAL, "fem_mg_create: needs a symmetric (mass or diffusion) form");
+  if (fine->kind != FEM_MASS && fine->kind != FEM_DIFFUSION)
+    return fem_fail(FEM_EINVAL, "fem_mg_create: needs a scalar symmetric (mass or diffusion) form");
   fem_mg_opts o;
   fem_mg_opts_default(&o);
   if (opts) o = *opts;

@@ -51,10 +51,10 @@ fem_status noalloc_scratch(double** out) {
 extern "C" fem_status fem_apply_noalloc(const fem_form* f, const double* x, double* y, void* stream) {
   if (!f || !x || !y) return fem_fail(FEM_EINVAL, "fem_apply_noalloc: NULL argument");
   if (x == y) return fem_fail(FEM_EINVAL, "fem_apply_noalloc: y must not alias x");
-  const int64_t need = f->space->ne * (int64_t)f->space->nd;
+  const int64_t need = f->vdim * f->space->ne * (int64_t)f->space->nd;
   if (need > FEM_NOALLOC_MAX_EVEC)
     return fem_fail(FEM_EINVAL,
-                    "fem_apply_noalloc: E-vector of %lld entries (ne * (p+1)^3) exceeds the fixed scratch of "
+                    "fem_apply_noalloc: E-vector of %lld entries (vdim * ne * (p+1)^3) exceeds the fixed scratch of "
                     "%d entries; use fem_apply",
                     (long long)need, FEM_NOALLOC_MAX_EVEC);
   double* ye = nullptr;

@@ -98,6 +98,71 @@ __global__ void k_setup_conv(int64_t ne, int Q, Geo geo, const double* __restric
   }
 }
 
+// Elasticity: per point J^-1 (row-major, [3 s + r] = d xhat_s / d x_r =
+// adj(J)[s][r] / det J), w det J lambda_e, w det J mu_e and a zero pad
+// (12 values, point-major [e][q][12]: 16-byte aligned records for the
+// apply's vector loads).
+template <typename Geo>
+__global__ void k_setup_elast(int64_t ne, int Q, Geo geo, const double* __restrict__ qwts,
+                              const double* __restrict__ lam, const double* __restrict__ mu,
+                              double* __restrict__ Dout, int* __restrict__ flag) {
+  const int nq = Q * Q * Q;
+  const int64_t total = ne * nq;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / nq;
+    const int q = (int)(t % nq);
+    const int q1 = q % Q, q2 = (q / Q) % Q, q3 = q / (Q * Q);
+    Geo h = geo;
+    h.load(e);
+    double J[3][3];
+    h.jacobian(q1, q2, q3, J);
+    double C[3][3];  // cofactors; adj(J)[a][b] = C[b][a]
+    C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    C[0][1] = -(J[1][0] * J[2][2] - J[1][2] * J[2][0]);
+    C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    C[1][0] = -(J[0][1] * J[2][2] - J[0][2] * J[2][1]);
+    C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    C[1][2] = -(J[0][0] * J[2][1] - J[0][1] * J[2][0]);
+    C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    C[2][1] = -(J[0][0] * J[1][2] - J[0][2] * J[1][0]);
+    C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+    if (!(det > 0.0)) {
+      if (atomicExch(&flag[0], 1) == 0) flag[1] = (int)e;
+    }
+    const double wd = qwts[q1] * qwts[q2] * qwts[q3] * det;
+    double* De = Dout + t * 12;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) De[3 * a + r] = C[r][a] / det;
+    De[9] = wd * lam[e];
+    De[10] = wd * mu[e];
+    De[11] = 0.0;
+  }
+}
+
+// Elasticity diagonal: the symmetric matrix of component c at every point,
+//   D^c = w det J ((lambda + mu) a_c a_c^T + mu J^-1 J^-T),  a_c[s] = J^-1[s][c],
+// in the diffusion layout [e][q][6] (00, 01, 02, 11, 12, 22): the (c, c)
+// block's diagonal is then the diffusion diagonal with D^c.
+__global__ void k_elast_diag_D(int64_t total, int c, const double* __restrict__ De, double* __restrict__ Dc) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double* m = De + t * 12;
+    const double lm = m[9] + m[10], mu = m[10];
+    double* o = Dc + t * 6;
+    const int S[6] = {0, 0, 0, 1, 1, 2}, U[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const double* ms = m + 3 * S[k];
+      const double* mt = m + 3 * U[k];
+      o[k] = lm * ms[c] * mt[c] + mu * (ms[0] * mt[0] + ms[1] * mt[1] + ms[2] * mt[2]);
+    }
+  }
+}
+
 // x at the tensor points (q1, q2, q3) of a P^3 set: the Gauss points
 // (quadrature-point coordinates, out [ne][P^3][3]).
 template <typename Geo>
@@ -160,18 +225,24 @@ fem_status fem_launch_setup(const fem_form* f, cudaStream_t s) {
   const int64_t total = sp->ne * f->nq;
   const int grid = grid_for(total, 256);
   const fem_mesh* m = sp->mesh;
-  const bool conv = f->kind == FEM_CONVECTION;
+  const bool conv = f->kind == FEM_CONVECTION, elast = f->kind == FEM_ELASTICITY;
   if (m->geo_k > 0) {
     FEM_TRY(fem_form_geo_tables(f));
     const NodalGeo g{m->d_gnodes, f->d_gB, f->d_gG, m->geo_k + 1, nullptr};
-    if (conv)
+    if (elast)
+      k_setup_elast<NodalGeo><<<grid, 256, 0, s>>>(sp->ne, f->q1d, g, f->d_qwts, f->d_coef, f->d_mu, f->d_D,
+                                                   f->d_flag);
+    else if (conv)
       k_setup_conv<NodalGeo><<<grid, 256, 0, s>>>(sp->ne, f->q1d, g, f->d_qwts, f->d_coef, f->d_beta, f->d_D,
                                                   f->d_flag);
     else
       k_setup<NodalGeo><<<grid, 256, 0, s>>>(sp->ne, f->q1d, f->kind, g, f->d_qwts, f->d_coef, f->d_D, f->d_flag);
   } else {
     const Hex8Geo g{m->d_coords, m->d_hex, f->d_qpts, {}};
-    if (conv)
+    if (elast)
+      k_setup_elast<Hex8Geo><<<grid, 256, 0, s>>>(sp->ne, f->q1d, g, f->d_qwts, f->d_coef, f->d_mu, f->d_D,
+                                                  f->d_flag);
+    else if (conv)
       k_setup_conv<Hex8Geo><<<grid, 256, 0, s>>>(sp->ne, f->q1d, g, f->d_qwts, f->d_coef, f->d_beta, f->d_D,
                                                  f->d_flag);
     else
@@ -226,8 +297,15 @@ fem_status fem_launch_dof_coords(const fem_space* sp, double* out, cudaStream_t 
 }
 
 fem_status fem_launch_mark_ess(const fem_form* f, cudaStream_t s) {
-  k_mark_ess<<<grid_for(f->n_ess, 256), 256, 0, s>>>(f->n_ess, f->space->ndof, f->d_ess, f->d_ess_mask,
+  k_mark_ess<<<grid_for(f->n_ess, 256), 256, 0, s>>>(f->n_ess, fem_form_len(f), f->d_ess, f->d_ess_mask,
                                                      f->d_flag);
+  FEM_LAUNCHED();
+  return FEM_OK;
+}
+
+fem_status fem_launch_elasticity_diag_D(const fem_form* f, int c, double* Dc, cudaStream_t s) {
+  const int64_t total = f->space->ne * f->nq;
+  k_elast_diag_D<<<grid_for(total, 256), 256, 0, s>>>(total, c, f->d_D, Dc);
   FEM_LAUNCHED();
   return FEM_OK;
 }

@@ -286,7 +286,7 @@ struct Work {
 };
 
 fem_status get_work(fem_form* f, bool mixed, Work& w) {
-  const int64_t n = f->space->ndof;
+  const int64_t n = fem_form_len(f);
   w.n = n;
   w.nb = fem_scatter_blocks(n);
   const size_t need64 = (size_t)7 * n;

@@ -70,3 +70,17 @@ def test_invariance_under_renumbering():
     n = X0.shape[0]
     vperm = np.concatenate([perm + cc * n for cc in range(3)])
     np.testing.assert_allclose(P1.K.toarray()[np.ix_(vperm, vperm)], P0.K.toarray(), atol=1e-11)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_nodal_geometry_of_a_trilinear_mesh(k):
+    """The order-k nodal geometry that writes the trilinear map as a grid
+    function gives the trilinear operator (same J at every point)."""
+    from oracle import curved
+    c, h = hex_lattice(2, 0.2, seed=9, shuffle=True)
+    E = h.shape[0]
+    lam, mu = lognormal(5, E), lognormal(6, E)
+    P0 = elasticity.ElasticityProblem(c, h, 2, 4, lam, mu)
+    Xn = curved.nodes_from_corners(c[h.astype(np.int64)], k)
+    P1 = elasticity.ElasticityProblem(c, h, 2, 4, lam, mu, Xn=Xn, k=k)
+    assert abs(P0.K - P1.K).max() <= 1e-12 * abs(P0.K).max()
