@@ -335,6 +335,94 @@ def run_sweep(args):
     return 0
 
 
+# Lattice sizes of the elasticity workload: 3 * ndof ~ 4.1e6-4.3e6 vector entries.
+ELAST_N = {1: 110, 2: 55, 3: 37, 4: 28, 5: 22, 6: 18, 7: 16, 8: 14}
+
+
+def elasticity_flops(p, q, E):
+    """Algorithmic flops of one elasticity apply: the diffusion sum
+    factorization on three components (unfolded 1D operators, 2 flops per
+    multiply-add) plus the stress map at every point (H = Ghat J^-1: 45,
+    trace and lambda term: 3, stress: 15, F = S J^-T: 45; 108 flops)."""
+    D1, Q = p + 1, q
+    return (6 * (4 * Q * D1 ** 3 + 6 * Q ** 2 * D1 ** 2 + 6 * Q ** 3 * D1) + 108 * Q ** 3) * E
+
+
+def run_elasticity(args):
+    """Linear elasticity workload, one JSON line per order p: a 0.15h-perturbed
+    lattice with 3 ndof ~ 4.2e6 vector entries, lognormal lambda and mu per
+    element; setup, FP64 / double-float / FP32 apply, the diagonal, and
+    Jacobi-PCG (FP64 and FP32-inner refinement) to 1e-8 for a clamped body
+    under gravity."""
+    import torch
+    from paper_1911_09220_gb300 import build as fbuild
+    fbuild.build()
+    import paper_1911_09220_gb300 as F
+    from fem_inputs import hex_lattice, lognormal, x_uniform
+    for p in [int(v) for v in args.orders.split(",")]:
+        N, q = ELAST_N[p], p + 2
+        c, h = hex_lattice(N, 0.15, seed=60 + p)
+        E = h.shape[0]
+        lam = torch.as_tensor(lognormal(70 + p, E), device="cuda")
+        mu = torch.as_tensor(lognormal(80 + p, E), device="cuda")
+        space = F.Space(F.Mesh(c, h), p)
+        form = F.Form.elasticity(space, lam, mu, q1d=q)
+        n = form.n
+        x = torch.as_tensor(x_uniform(90 + p, n), device="cuda")
+        y = torch.empty_like(x)
+        x32, y32 = x.float(), torch.empty(n, dtype=torch.float32, device="cuda")
+        ye = torch.empty(3 * E * (p + 1) ** 3, dtype=torch.float64, device="cuda")
+        ye32 = torch.empty(3 * E * (p + 1) ** 3, dtype=torch.float32, device="cuda")
+        flops = elasticity_flops(p, q, E)
+        bytes32 = 4 * (12 * q ** 3 * E + 2 * n) + 4 * (p + 1) ** 3 * E
+        t64 = time_events(lambda: form.apply(x, y), args.steps, 3)
+        tdf = time_events(lambda: form.apply(x, y, arith="df64"), args.steps, 3)
+        t32 = time_events(lambda: form.apply(x32, y32), args.steps, 3)
+        te64 = time_events(lambda: form.apply_element(x, ye), args.steps, 3)
+        tedf = time_events(lambda: form.apply_element(x, ye, arith="df64"), args.steps, 3)
+        te32 = time_events(lambda: form.apply_element(x32, ye32), args.steps, 3)
+        del ye, ye32
+        d = torch.empty_like(x)
+        tdiag = time_events(lambda: form.diagonal(d), 3, 1)
+        tset = time_events(lambda: form.set_lame(lam, mu), 3, 1)
+        out = {"workload": f"elasticity p={p}, q={q}, {N}^3 hexes", "p": p, "q1d": q, "N": N, "elements": E,
+               "ndof": space.ndof, "vector_len": n,
+               "f64": {"ms": t64, "gdofs": n / t64 * 1e-6, "element_ms": te64,
+                       "element_frac_fp64_peak": flops / te64 * 1e-9 / FP64_PEAK_TFLOPS},
+               "df64": {"ms": tdf, "gdofs": n / tdf * 1e-6, "element_ms": tedf},
+               "f32": {"ms": t32, "gdofs": n / t32 * 1e-6, "element_ms": te32,
+                       "element_alg_gbs": bytes32 / te32 * 1e-6,
+                       "element_frac_hbm": bytes32 / te32 * 1e-6 / peaks().get("hbm_gbs", 6800.0),
+                       "element_tflops": flops / te32 * 1e-9},
+               "alg_flops": flops, "diag_ms": tdiag, "setup_ms": tset}
+        if not args.no_solve:
+            ndof = space.ndof
+            bd = torch.as_tensor(space.boundary_dofs(), device="cuda", dtype=torch.int64)
+            form.set_essential(torch.cat([bd + k * ndof for k in range(3)]).to(torch.int32))
+            fq = torch.zeros((3, E, q ** 3), dtype=torch.float64, device="cuda")
+            fq[2] = -1.0
+            b = torch.empty_like(x)
+            form.rhs(fq, b)
+            del fq
+            bc = torch.empty_like(b)
+            form.lift_rhs(b, torch.zeros_like(b), bc)
+            sol = {}
+            for prec in ("f64", "mixed"):
+                u = torch.zeros_like(b)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info = form.solve(bc, u, rtol=1e-8, maxit=args.solve_maxit, precision=prec, raise_on_error=False)
+                torch.cuda.synchronize()
+                sol[prec] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
+                             "outer": info["outer"], "relres": info["relres"], "converged": info["converged"]}
+            sol["speedup_mixed"] = sol["f64"]["seconds"] / sol["mixed"]["seconds"]
+            out["solve_1e-8"] = sol
+        print(json.dumps(out), flush=True)
+        del form, space, x, y, x32, y32, d
+        torch.cuda.empty_cache()
+    return 0
+
+
 def batch_config(seed=40, nprob=256):
     """Seeded sizes of the batching workload: N_i ~ U{2..24}, p_i ~ U{1..6}."""
     from fem_inputs import splitmix64
@@ -641,7 +729,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--solve-maxit", type=int, default=20000)
-    ap.add_argument("--workload", default="apply", choices=["apply", "sweep", "batch", "grad", "paper2d", "mg", "curved"])
+    ap.add_argument("--workload", default="apply", choices=["apply", "sweep", "batch", "grad", "paper2d", "mg", "curved",
+                                                         "elasticity"])
     ap.add_argument("--sweep-size", default="4e6", choices=["1e6", "4e6", "2e7", "3e7"])
     ap.add_argument("--orders", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--nprob", type=int, default=256)
@@ -663,6 +752,8 @@ def main():
         return run_curved(args)
     if args.workload == "grad":
         return run_grad(args)
+    if args.workload == "elasticity":
+        return run_elasticity(args)
 
     import torch
     import torch.distributed as dist
