@@ -29,12 +29,16 @@ step by step in the order it is applied, is:
 * outer iteration: flexible CG (Notay 2000; beta = z_new . (r_new - r) /
   z . r), which stays correct when the preconditioner is not a fixed linear
   map (the coarsest-level CG is not).
+* elasticity (three-component vectors, component-major): every level is the
+  elasticity operator with the same Lame coefficients; the coarse essential
+  rule is applied to each component's mask, and P is block-diagonal with the
+  scalar P in each component's block.
 """
 
 import numpy as np
 import scipy.sparse as sp
 
-from . import assemble, lagrange, numbering, rules
+from . import assemble, elasticity, lagrange, numbering, rules
 from . import solve as osolve
 
 HASH_MUL = 2654435761
@@ -98,7 +102,7 @@ def prolongation(e2l_f, p_f, n_f, e2l_c, p_c, n_c):
 class Level:
     def __init__(self, prob, ess_mask):
         self.prob = prob
-        self.n = prob.ndof
+        self.n = prob.K.shape[0]
         self.ess = ess_mask
         K = prob.K
         self.A = osolve.constrain(K, np.nonzero(ess_mask)[0])
@@ -122,26 +126,38 @@ def power_lambda(A, D, free, m):
 
 class PMG:
     """Hierarchy and V-cycle. coords/hexes/p/q/kappa define the fine form;
-    ess: fine essential DOF ids."""
+    ess: fine essential DOF ids. lame = (lambda, mu): the elasticity form
+    instead (kappa unused; ess ids index the 3 ndof vector)."""
 
     def __init__(self, coords, hexes, p, q, kappa, ess, cheb_order=2, alpha=0.25, beta=1.1, power_its=20,
-                 coarse_its=30, fine_prob=None):
+                 coarse_its=30, fine_prob=None, lame=None):
         self.K, self.alpha, self.beta = cheb_order, alpha, beta
         self.coarse_its = coarse_its
         orders = level_orders(p)
         self.orders = orders
         dq = q - p
-        probs = [fine_prob if fine_prob is not None else assemble.Problem(coords, hexes, p, q, kappa=kappa)]
+        if lame is None:
+            vd = 1
+            make = lambda pl: assemble.Problem(coords, hexes, pl, pl + dq, kappa=kappa)
+        else:
+            vd = 3
+            make = lambda pl: elasticity.ElasticityProblem(coords, hexes, pl, pl + dq, lame[0], lame[1])
+        self.vdim = vd
+        probs = [fine_prob if fine_prob is not None else make(p)]
         for pl in orders[1:]:
-            probs.append(assemble.Problem(coords, hexes, pl, pl + dq, kappa=kappa))
-        mask = np.zeros(probs[0].ndof, dtype=bool)
+            probs.append(make(pl))
+        mask = np.zeros(vd * probs[0].ndof, dtype=bool)
         mask[np.asarray(ess, dtype=np.int64)] = True
         self.levels = [Level(probs[0], mask)]
         for l in range(1, len(orders)):
             f, c = probs[l - 1], probs[l]
-            m = coarse_essential(f.e2l, f.p, self.levels[-1].ess, c.e2l, c.p, c.ndof)
+            fm = self.levels[-1].ess
+            m = np.concatenate([coarse_essential(f.e2l, f.p, fm[k * f.ndof:(k + 1) * f.ndof], c.e2l, c.p, c.ndof)
+                                for k in range(vd)])
             self.levels.append(Level(c, m))
             Pm = prolongation(f.e2l, f.p, f.ndof, c.e2l, c.p, c.ndof)
+            if vd > 1:
+                Pm = sp.block_diag([Pm] * vd, format="csr")
             Ef = sp.diags((~self.levels[l - 1].ess).astype(np.float64))
             Ec = sp.diags((~m).astype(np.float64))
             self.levels[l - 1].P = (Ef @ Pm @ Ec).tocsr()
