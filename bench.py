@@ -352,8 +352,9 @@ def run_elasticity(args):
     """Linear elasticity workload, one JSON line per order p: a 0.15h-perturbed
     lattice with 3 ndof ~ 4.2e6 vector entries, lognormal lambda and mu per
     element; setup, FP64 / double-float / FP32 apply, the diagonal, and
-    Jacobi-PCG (FP64 and FP32-inner refinement) to 1e-8 for a clamped body
-    under gravity."""
+    Jacobi-PCG (FP64 and FP32-inner refinement) and p-multigrid flexible CG
+    (FP32 V-cycle, double-float outer) to 1e-8 for a clamped body under
+    gravity."""
     import torch
     from paper_1911_09220_gb300 import build as fbuild
     fbuild.build()
@@ -416,6 +417,22 @@ def run_elasticity(args):
                 sol[prec] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
                              "outer": info["outer"], "relres": info["relres"], "converged": info["converged"]}
             sol["speedup_mixed"] = sol["f64"]["seconds"] / sol["mixed"]["seconds"]
+            # p-multigrid flexible CG: FP32 V-cycle, double-float outer operator
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mg = F.Multigrid(form, precision="f32")
+            torch.cuda.synchronize()
+            t_mg = time.perf_counter() - t0
+            u = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = mg.solve(bc, u, rtol=1e-8, check_every=4, raise_on_error=False, arith="df64")
+            torch.cuda.synchronize()
+            sol["pmg_f32_df64"] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
+                                   "relres": info["relres"], "converged": info["converged"],
+                                   "hierarchy_setup_s": t_mg}
+            sol["speedup_pmg"] = sol["f64"]["seconds"] / sol["pmg_f32_df64"]["seconds"]
+            del mg
             out["solve_1e-8"] = sol
         print(json.dumps(out), flush=True)
         del form, space, x, y, x32, y32, d

@@ -195,8 +195,8 @@ fem_status fem_form_set_velocity(fem_form* form, const double* beta_q, void* str
  * runs the backward gradient stages of the diffusion operator on each
  * component of F. Its E-vector is [3][ne][(p+1)^3].
  * lambda, mu: device float64 [ne], per-element Lame coefficients, required.
- * Hexahedral meshes only; fem_compliance_grad, fem_mg_create and
- * fem_batch_create reject the form (FEM_EINVAL). fem_rhs takes fq
+ * Hexahedral meshes only; fem_compliance_grad and fem_batch_create reject
+ * the form (FEM_EINVAL); fem_mg_create builds a vector hierarchy. fem_rhs takes fq
  * [3][ne][q1d^3] (the three body-force components). */
 fem_status fem_form_create_elasticity(const fem_space* space, int q1d, const double* lambda,
                                       const double* mu, void* stream, fem_form** out);
@@ -374,7 +374,12 @@ fem_status fem_batch_tiles(const fem_batch* batch, int* tiles_host);
  * D^-1 A_c from v_i = frac(i * 2654435761 / 2^32) - 1/2. Coarsest level:
  * coarse_its Jacobi-PCG iterations from zero. V-cycle: pre-smoothing from
  * zero, restricted residual, recursion, prolongated correction,
- * post-smoothing. 3D (hexahedral) forms only. */
+ * post-smoothing. 3D (hexahedral) forms only. Elasticity forms: every
+ * level is an elasticity form with the same Lame coefficients, the
+ * essential rule and the transfers act on each component (P is
+ * block-diagonal over the components of component-major vectors), and
+ * all vectors below are [3 ndof] of their level. Convection forms are
+ * rejected (FEM_EINVAL). */
 typedef struct fem_mg fem_mg;
 typedef struct {
   int cheb_order;       /* Chebyshev steps per pre- and post-smoothing (2) */
@@ -396,7 +401,8 @@ fem_status fem_mg_create(const fem_form* fine, const fem_mg_opts* opts, void* st
                          fem_mg** out);
 void fem_mg_destroy(fem_mg* mg);
 /* Level count and, per level l (fine first), order, lambda estimate (0 on
- * the coarsest level) and DOF count; each host array may be NULL or holds
+ * the coarsest level) and vector length (DOF count times the form's
+ * components); each host array may be NULL or holds
  * at least nlevels entries. */
 fem_status fem_mg_info(const fem_mg* mg, int* nlevels, int* orders_host,
                        double* lambdas_host, int64_t* ndofs_host);

@@ -426,7 +426,8 @@ class Multigrid:
     """p-multigrid preconditioner of a form (levels p, p/2, ..., 1; Chebyshev-
     Jacobi smoothing; coarsest level by Jacobi-PCG) and flexible CG with it.
     precision: "f64" or "f32" (arithmetic of the V-cycle; the outer iteration
-    is FP64). set_essential must have been called on the form."""
+    is FP64). set_essential must have been called on the form. Elasticity
+    forms get a vector hierarchy (vectors of length 3 ndof on every level)."""
 
     def __init__(self, form, cheb_order=2, cheb_lo=0.25, cheb_hi=1.1, power_its=20, coarse_its=30,
                  precision="f64", stream=None):
@@ -457,6 +458,7 @@ class Multigrid:
             raise IndexError(level)
         v = Form.__new__(_FormView)
         v._h, v._owner, v.space, v.ess = C.c_void_p(h), self, None, None
+        v.vdim = self.form.vdim
         return v
 
     def prolong(self, level, zc, zf, stream=None):

@@ -24,6 +24,11 @@
 //   coarsest    a fixed number of Jacobi-PCG iterations from zero;
 //   outer       flexible CG (Notay 2000; beta = z.(r - r_old) / z_old.r_old)
 //               in FP64, the V-cycle in FP64 or FP32.
+//   vector      elasticity forms: every level is an elasticity form with the
+//               same Lame coefficients; the essential rule and the transfers
+//               act on each component separately (P = blockdiag(P, P, P) on
+//               component-major vectors); smoother, coarsest CG and outer
+//               iteration run on the whole vector.
 //
 // Every kernel takes the outer iteration's `done` word and returns at once
 // when it is set, so whole outer iterations (V-cycle included) are captured
@@ -505,7 +510,8 @@ struct MgLevel {
   fem_space* sp_own = nullptr;  // owned space and form of the coarse levels
   fem_form* f_own = nullptr;
   int p = 0, D1 = 0, nd = 0;
-  int64_t n = 0;
+  int vdim = 1;                 // vector components (3 for elasticity)
+  int64_t n = 0;                // vector length vdim * ndof
   double lam = 0.0, inv_theta = 0.0;
   std::vector<double> c1, c2;   // Chebyshev step coefficients
   double* diag64 = nullptr;
@@ -624,20 +630,30 @@ fem_status vcycle(fem_mg* m, size_t l, const int* skip, cudaStream_t s) {
   const fem_space* sc = C.f->space;
   T* yef = reinterpret_cast<T*>(L.f->d_ye);
   T* yec = reinterpret_cast<T*>(C.f->d_ye);
-  const int64_t nslots = sf->ne * (int64_t)sf->nd;
-  k_mg_spread<T><<<grid_for(nslots, 256), 256, 0, s>>>(nslots, sf->d_e2l, sf->d_l2e_off, sf->d_l2e_idx,
-                                                       L.f->d_ess_mask, res, yef, skip);
-  FEM_LAUNCHED();
-  FEM_TRY(launch_interp<T>(L.D1, C.D1, false, (int)sf->ne, nullptr, nullptr, yef, L.It, yec, skip, s));
+  // (vector forms: each component through the scalar transfer, on its
+  // slices of the L-vectors, masks and E-vectors)
+  const int64_t nslots = sf->ne * (int64_t)sf->nd, cslots = sc->ne * (int64_t)sc->nd;
+  const int64_t nf = sf->ndof, nc = sc->ndof;
+  for (int c = 0; c < L.vdim; ++c) {
+    k_mg_spread<T><<<grid_for(nslots, 256), 256, 0, s>>>(nslots, sf->d_e2l, sf->d_l2e_off, sf->d_l2e_idx,
+                                                         L.f->d_ess_mask + c * nf, res + c * nf, yef + c * nslots,
+                                                         skip);
+    FEM_LAUNCHED();
+    FEM_TRY(launch_interp<T>(L.D1, C.D1, false, (int)sf->ne, nullptr, nullptr, yef + c * nslots, L.It,
+                             yec + c * cslots, skip, s));
+  }
   const int dt = std::is_same<T, float>::value ? FEM_F32 : FEM_F64;
   FEM_TRY(fem_launch_scatter(C.f, dt, yec, lvec<T>(C, 0), C.f->d_ess_mask, m->zero, nullptr, 0, s, skip));
   // coarse correction
   FEM_TRY(vcycle<T>(m, l + 1, skip, s));
   // prolongation: z += P~ z_c
-  FEM_TRY(launch_interp<T>(L.D1, C.D1, true, (int)sf->ne, sc->d_e2l, C.f->d_ess_mask, lvec<T>(C, 1), L.I, yef, skip,
-                           s));
-  k_mg_pick<T><<<nb, 256, 0, s>>>(n, sf->d_l2e_off, sf->d_l2e_idx, L.f->d_ess_mask, yef, z, skip);
-  FEM_LAUNCHED();
+  for (int c = 0; c < L.vdim; ++c) {
+    FEM_TRY(launch_interp<T>(L.D1, C.D1, true, (int)sf->ne, sc->d_e2l, C.f->d_ess_mask + c * nc,
+                             lvec<T>(C, 1) + c * nc, L.I, yef + c * nslots, skip, s));
+    k_mg_pick<T><<<vblocks(nf), 256, 0, s>>>(nf, sf->d_l2e_off, sf->d_l2e_idx, L.f->d_ess_mask + c * nf,
+                                             yef + c * nslots, z + c * nf, skip);
+    FEM_LAUNCHED();
+  }
   // post-smoothing from z
   FEM_TRY(level_apply<T>(L, z, q, skip, s));
   k_cheb_post<T><<<nb, 256, 0, s>>>(n, r, q, D, it, res, d, z, skip);
@@ -736,7 +752,8 @@ int signature(int k, int D1) {
   return s;
 }
 
-std::vector<int32_t> coarse_ess(const fem_space* sf, const std::vector<uint8_t>& essf, const fem_space* sc) {
+// essf: the fine mask of one component ([sf->ndof]).
+std::vector<int32_t> coarse_ess(const fem_space* sf, const uint8_t* essf, const fem_space* sc) {
   const int Df = sf->D1, Dc = sc->D1, ndf = sf->nd, ndc = sc->nd;
   std::vector<int> sigf(ndf), sigc(ndc);
   for (int k = 0; k < ndf; ++k) sigf[k] = signature(k, Df);
@@ -818,8 +835,8 @@ extern "C" fem_status fem_mg_create(const fem_form* fine, const fem_mg_opts* opt
   *out = nullptr;
   if (!fine->d_ess_mask) return fem_fail(FEM_EINVAL, "fem_mg_create: call fem_form_set_essential first (n may be 0)");
   if (fine->space->mesh->dim != 3) return fem_fail(FEM_EUNSUPPORTED, "fem_mg_create: hexahedral meshes only");
-  if (fine->kind != FEM_MASS && fine->kind != FEM_DIFFUSION)
-    return fem_fail(FEM_EINVAL, "fem_mg_create: needs a scalar symmetric (mass or diffusion) form");
+  if (fine->kind != FEM_MASS && fine->kind != FEM_DIFFUSION && fine->kind != FEM_ELASTICITY)
+    return fem_fail(FEM_EINVAL, "fem_mg_create: needs a symmetric (mass, diffusion or elasticity) form");
   fem_mg_opts o;
   fem_mg_opts_default(&o);
   if (opts) o = *opts;
@@ -843,25 +860,37 @@ extern "C" fem_status fem_mg_create(const fem_form* fine, const fem_mg_opts* opt
   L0.p = sp0->p;
   L0.D1 = sp0->D1;
   L0.nd = sp0->nd;
-  L0.n = sp0->ndof;
+  L0.vdim = fine->vdim;
+  L0.n = fem_form_len(fine);
   m->lv.push_back(L0);
-  std::vector<uint8_t> essf(sp0->ndof);
-  if (cudaMemcpy(essf.data(), fine->d_ess_mask, sp0->ndof, cudaMemcpyDeviceToHost) != cudaSuccess)
+  const int vd = fine->vdim;
+  std::vector<uint8_t> essf(L0.n);
+  if (cudaMemcpy(essf.data(), fine->d_ess_mask, L0.n, cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(fem_fail(FEM_ECUDA, "fem_mg_create: reading the essential mask failed"));
   while (m->lv.back().p > 1) {
     const MgLevel& F = m->lv.back();
     MgLevel C;
     C.p = F.p / 2;
     if ((st = fem_space_create(sp0->mesh, C.p, &C.sp_own)) != FEM_OK) return fail(st);
-    if ((st = fem_form_create(C.sp_own, fine->kind, C.p + dq, fine->d_coef, stream, &C.f_own)) != FEM_OK) {
+    if (fine->kind == FEM_ELASTICITY)
+      st = fem_form_create_elasticity(C.sp_own, C.p + dq, fine->d_coef, fine->d_mu, stream, &C.f_own);
+    else
+      st = fem_form_create(C.sp_own, fine->kind, C.p + dq, fine->d_coef, stream, &C.f_own);
+    if (st != FEM_OK) {
       fem_space_destroy(C.sp_own);
       return fail(st);
     }
     C.f = C.f_own;
     C.D1 = C.sp_own->D1;
     C.nd = C.sp_own->nd;
-    C.n = C.sp_own->ndof;
-    const std::vector<int32_t> ess = coarse_ess(F.f->space, essf, C.sp_own);
+    C.vdim = vd;
+    C.n = vd * C.sp_own->ndof;
+    // coarse essential DOFs of each component from that component's fine mask
+    std::vector<int32_t> ess;
+    for (int c = 0; c < vd; ++c) {
+      const std::vector<int32_t> ec = coarse_ess(F.f->space, essf.data() + c * F.f->space->ndof, C.sp_own);
+      for (int32_t i : ec) ess.push_back(i + (int32_t)(c * C.sp_own->ndof));
+    }
     int32_t* d_ess = nullptr;
     st = dev_alloc(&d_ess, ess.size());
     if (st == FEM_OK && !ess.empty() &&
@@ -950,11 +979,14 @@ extern "C" fem_status fem_mg_prolong(fem_mg* m, int level, const double* zc, dou
   const fem_space* sf = L.f->space;
   double* yef = reinterpret_cast<double*>(L.f->d_ye);
   FEM_CUDA(cudaMemsetAsync(zf, 0, sizeof(double) * L.n, s));
-  FEM_TRY(launch_interp<double>(L.D1, C.D1, true, (int)sf->ne, C.f->space->d_e2l, C.f->d_ess_mask, zc, L.I, yef,
-                                m->d_never, s));
-  k_mg_pick<double><<<vblocks(L.n), 256, 0, s>>>(L.n, sf->d_l2e_off, sf->d_l2e_idx, L.f->d_ess_mask, yef, zf,
-                                                 m->d_never);
-  FEM_LAUNCHED();
+  const int64_t nf = sf->ndof, nc = C.f->space->ndof, nslots = sf->ne * (int64_t)sf->nd;
+  for (int c = 0; c < L.vdim; ++c) {
+    FEM_TRY(launch_interp<double>(L.D1, C.D1, true, (int)sf->ne, C.f->space->d_e2l, C.f->d_ess_mask + c * nc,
+                                  zc + c * nc, L.I, yef + c * nslots, m->d_never, s));
+    k_mg_pick<double><<<vblocks(nf), 256, 0, s>>>(nf, sf->d_l2e_off, sf->d_l2e_idx, L.f->d_ess_mask + c * nf,
+                                                  yef + c * nslots, zf + c * nf, m->d_never);
+    FEM_LAUNCHED();
+  }
   return FEM_OK;
 }
 
@@ -966,11 +998,16 @@ extern "C" fem_status fem_mg_restrict(fem_mg* m, int level, const double* rf, do
   const fem_space* sf = L.f->space;
   double* yef = reinterpret_cast<double*>(L.f->d_ye);
   double* yec = reinterpret_cast<double*>(C.f->d_ye);
-  const int64_t nslots = sf->ne * (int64_t)sf->nd;
-  k_mg_spread<double><<<grid_for(nslots, 256), 256, 0, s>>>(nslots, sf->d_e2l, sf->d_l2e_off, sf->d_l2e_idx,
-                                                            L.f->d_ess_mask, rf, yef, m->d_never);
-  FEM_LAUNCHED();
-  FEM_TRY(launch_interp<double>(L.D1, C.D1, false, (int)sf->ne, nullptr, nullptr, yef, L.It, yec, m->d_never, s));
+  const int64_t nslots = sf->ne * (int64_t)sf->nd, cslots = C.f->space->ne * (int64_t)C.f->space->nd;
+  const int64_t nf = sf->ndof;
+  for (int c = 0; c < L.vdim; ++c) {
+    k_mg_spread<double><<<grid_for(nslots, 256), 256, 0, s>>>(nslots, sf->d_e2l, sf->d_l2e_off, sf->d_l2e_idx,
+                                                              L.f->d_ess_mask + c * nf, rf + c * nf,
+                                                              yef + c * nslots, m->d_never);
+    FEM_LAUNCHED();
+    FEM_TRY(launch_interp<double>(L.D1, C.D1, false, (int)sf->ne, nullptr, nullptr, yef + c * nslots, L.It,
+                                  yec + c * cslots, m->d_never, s));
+  }
   // essential rows of the coarse level: 0 (the scatter's constraint rows
   // take xin = rc itself after it was zeroed there)
   FEM_CUDA(cudaMemsetAsync(rc, 0, sizeof(double) * C.n, s));

@@ -5,7 +5,8 @@ orders, ragged last blocks, trilinear and curved geometry, both compiled
 quadrature orders), its two halves, the no-allocation entry point, the
 constrained apply, the assembled diagonal, the vector load vector,
 Jacobi-PCG solves against the oracle's dense solution, set_lame, and the
-entry points that reject a vector form. Tolerances as for diffusion
+entry points that reject a vector form (the vector p-multigrid hierarchy is
+tested in test_gpu_multigrid.py). Tolerances as for diffusion
 (1e-12 relative to the largest entry; FP32 2e-5)."""
 
 import numpy as np
@@ -188,8 +189,6 @@ def test_set_lame_and_rejections():
     with pytest.raises(F.FemError):
         form.set_coef(cuda(lam2))
     form.set_essential(form.space.boundary_dofs())
-    with pytest.raises(F.FemError):
-        F.Multigrid(form)
     with pytest.raises(F.FemError):
         F.Batch([form], 1)
     with pytest.raises(F.FemError):

@@ -199,3 +199,91 @@ def test_errors():
     with pytest.raises(F.FemError) as ei:
         F.Multigrid(f2)
     assert ei.value.status == 7
+
+
+# ---- vector hierarchy of an elasticity form
+def _esetup(p, N=3, drop=0, ess_kind="clamped", seed=15, **kw):
+    import paper_1911_09220_gb300 as F
+    from oracle import elasticity as oel
+    c, h = make_mesh(N, perturb=0.15, seed=seed, shuffle=True, drop=drop)
+    E = h.shape[0]
+    lam, mu = lognormal(seed + 1, E), lognormal(seed + 2, E)
+    fine = oel.ElasticityProblem(c, h, p, p + 2, lam, mu)
+    n = fine.ndof
+    bd = assemble.Problem(c, h, p, p + 2).num["boundary_dofs"]
+    if ess_kind == "clamped":
+        ess = np.concatenate([bd + k * n for k in range(3)])
+    else:  # one face clamped in all components, the normal component elsewhere on the boundary
+        X = assemble.Problem(c, h, p, p + 2).dof_coords()
+        face = np.nonzero(np.abs(X[:, 0]) < 1e-12)[0]
+        ess = np.unique(np.concatenate([face, face + n, face + 2 * n, bd]))
+    space = F.Space(F.Mesh(c, h), p)
+    form = F.Form.elasticity(space, cuda(lam), cuda(mu), q1d=p + 2)
+    form.set_essential(ess)
+    okw = {k: v for k, v in kw.items() if k != "precision"}
+    M = omg.PMG(c, h, p, p + 2, None, ess, fine_prob=fine, lame=(lam, mu), **okw)
+    G = F.Multigrid(form, **kw)
+    return M, G, form, fine, ess
+
+
+@pytest.mark.parametrize("ess_kind", ["clamped", "mixed"])
+@pytest.mark.parametrize("p,N,drop", [(2, 3, 2), (4, 2, 1), (5, 2, 0)])
+def test_elasticity_levels_transfers_vcycle(p, N, drop, ess_kind):
+    import torch
+    M, G, form, fine, ess = _esetup(p, N, drop, ess_kind=ess_kind)
+    info = G.info()
+    assert info["orders"] == omg.level_orders(p)
+    assert info["ndofs"] == [lv.n for lv in M.levels]
+    for l, lv in enumerate(M.levels[:-1]):
+        assert abs(info["lambdas"][l] - lv.lam) <= 1e-10 * lv.lam
+    for l, lv in enumerate(M.levels):
+        f = G.level_form(l)
+        x = x_uniform(60 + l, lv.n)
+        y = torch.empty(lv.n, dtype=torch.float64, device="cuda")
+        f.apply(cuda(x), y, constrained=True)
+        assert relerr(y.cpu().numpy(), lv.A @ x) <= 1e-12
+        d = torch.empty_like(y)
+        f.diagonal(d, constrained=True)
+        assert relerr(d.cpu().numpy(), lv.D) <= 1e-12
+        if l + 1 < len(M.levels):
+            nc = M.levels[l + 1].n
+            zc = x_uniform(70 + l, nc)
+            zf = torch.empty(lv.n, dtype=torch.float64, device="cuda")
+            G.prolong(l, cuda(zc), zf)
+            assert relerr(zf.cpu().numpy(), lv.P @ zc) <= 1e-13
+            rc = torch.empty(nc, dtype=torch.float64, device="cuda")
+            G.restrict(l, cuda(x), rc)
+            assert relerr(rc.cpu().numpy(), lv.P.T @ x) <= 1e-13
+    r = x_uniform(80 + p, fine.K.shape[0])
+    r[ess] = 0.0
+    z = torch.empty(r.size, dtype=torch.float64, device="cuda")
+    G.vcycle(cuda(r), z)
+    assert relerr(z.cpu().numpy(), M.vcycle(r)) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("p,N", [(2, 3), (4, 2)])
+def test_elasticity_solve(p, N, precision):
+    import torch
+    M, G, form, fine, ess = _esetup(p, N, precision=precision)
+    n = fine.K.shape[0]
+    if precision == "f32":
+        r = x_uniform(90 + p, n)
+        r[ess] = 0.0
+        z = torch.empty(n, dtype=torch.float64, device="cuda")
+        G.vcycle(cuda(r), z)
+        assert relerr(z.cpu().numpy(), M.vcycle(r)) <= 1e-4
+    bvec = x_uniform(95 + p, n)
+    bc = torch.empty(n, dtype=torch.float64, device="cuda")
+    form.lift_rhs(cuda(bvec), torch.zeros_like(bc), bc)
+    x = torch.zeros_like(bc)
+    info = G.solve(bc, x, rtol=1e-10)
+    assert info["converged"]
+    Ac = M.levels[0].A
+    bco = osolve.constrain_rhs(fine.K, bvec, ess)
+    u = x.cpu().numpy()
+    assert np.linalg.norm(bco - Ac @ u) / np.linalg.norm(bco) <= 1.01e-10
+    xo, ito, relo = M.fcg(bco, rtol=1e-10)
+    assert abs(info["iterations"] - ito) <= 1
+    _, pinfo = osolve.pcg(Ac, bco, rtol=1e-10)
+    assert 3 * info["iterations"] < pinfo["iterations"]
