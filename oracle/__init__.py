@@ -35,7 +35,10 @@ matrix with the same quadrature):
 * p-multigrid: level hierarchy, nodal-interpolation transfers, coarse
   essential DOFs, Chebyshev-Jacobi smoothing, the V-cycle and flexible CG
   (`multigrid`; the paper names matrix-free p-multigrid, Sec. 5.2, without
-  an algorithm: the module header states the reading).
+  an algorithm: the module header states the reading);
+* the assembled CSR product as a plain C loop, OpenMP over rows, for timing
+  the CPU baseline on all host cores (`cspmv`, `spmv.c`; imported on
+  demand, compiled by gcc).
 
 Parity status: every function is pinned by `tests/test_oracle_*.py` against
 closed forms, invariants or brute force, except the mixed-precision error,
