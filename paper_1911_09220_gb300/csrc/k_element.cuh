@@ -295,6 +295,56 @@ __host__ __device__ constexpr int best_stride(int lo, int n, int A, bool stride_
   return best;
 }
 
+// The same cost with the readers of NE consecutive elements side by side
+// (reader i belongs to element i / n, whose slab starts SE words after the
+// previous one): the packed stages and the S3 planes put the lines of two
+// elements into one warp whenever n is not a multiple of the bank group.
+__host__ __device__ constexpr int bank_cost_packed(int n, int A, int m_lo, int m_hi, int wbytes, int ne, int se) {
+  const int G = wbytes == 8 ? 16 : 32;
+  const int total = ne * n;
+  int cost = 0;
+  for (int g0 = 0; g0 < total; g0 += G) {
+    int cnt[32] = {};
+    int worst = 0;
+    for (int i = g0; i < total && i < g0 + G; ++i) {
+      const int el = i / n, r = i % n;
+      const int w = el * se + (r % A) * m_lo + (r / A) * m_hi;
+      const int b = w % G;
+      cnt[b] += 1;
+      if (cnt[b] > worst) worst = cnt[b];
+    }
+    cost += worst;
+  }
+  return cost;
+}
+
+// Slab stride >= lo (candidates lo .. lo + 31) of least total cost over the
+// shared-memory accesses of all stages, each weighted by the values a line
+// reads or writes (S1: X rows in, BX/GX out; S2: BX/GX in, BB/GB/BG out;
+// S3: BB/GB/BG in, T0-T2 out; S4: T0-T2 in, UA/UB out; S5: UA/UB in),
+// modelled on 8 elements.
+__host__ __device__ constexpr int best_slab(int lo, int D1, int Q, int XP, int RB, int RC, int RT, int RU,
+                                            int wbytes) {
+  const int N1 = D1 * D1, N2 = D1 * Q, QQ = Q * Q, NEm = 8;
+  int best = lo, best_cost = 1 << 30;
+  for (int se = lo; se < lo + 32; ++se) {
+    const int c = D1 * bank_cost_packed(N1, N1, XP, 0, wbytes, NEm, se) +
+                  2 * Q * bank_cost_packed(N1, N1, 1, 0, wbytes, NEm, se) +
+                  2 * D1 * bank_cost_packed(N2, Q, RB, D1, wbytes, NEm, se) +
+                  3 * Q * bank_cost_packed(N2, N2, 1, 0, wbytes, NEm, se) +
+                  3 * D1 * bank_cost_packed(QQ, Q, 1, RC, wbytes, NEm, se) +
+                  3 * D1 * bank_cost_packed(QQ, QQ, 1, 0, wbytes, NEm, se) +
+                  3 * Q * bank_cost_packed(N2, Q, 1, RT, wbytes, NEm, se) +
+                  2 * D1 * bank_cost_packed(N2, N2, 1, 0, wbytes, NEm, se) +
+                  2 * Q * bank_cost_packed(N1, D1, RU, Q, wbytes, NEm, se);
+    if (c < best_cost) {
+      best_cost = c;
+      best = se;
+    }
+  }
+  return best;
+}
+
 // Per-element shared-memory plan (in units of T):
 //   phase A  region 0: X [z][y][XP], dead after S1, then BB, GB, BG [qy][RC]
 //            over (z, qx); region 1 (offset R0): BX, GX [qx][RB] over (z, y)
@@ -310,7 +360,9 @@ struct ElemSmem {
   static constexpr int R0 = D1 * D1 * XP > 3 * Q * RC ? D1 * D1 * XP : 3 * Q * RC;
   static constexpr int SA = R0 + 2 * Q * RB;
   static constexpr int SB = 3 * D1 * RT + 2 * D1 * RU;
-  static constexpr int SE = SA > SB ? SA : SB;  // per element, in T
+  // per element, in T: the larger phase, padded to the slab stride of least
+  // bank conflicts between neighbouring elements' slabs
+  static constexpr int SE = best_slab(SA > SB ? SA : SB, D1, Q, XP, RB, RC, RT, RU, W);
 };
 
 // ------------------------------------------------------ stage bodies ----
