@@ -371,7 +371,8 @@ fem_status fem_batch_tiles(const fem_batch* batch, int* tiles_host);
  * free DOFs on both sides; restriction = P^T. Smoother: cheb_order steps of
  * Jacobi-preconditioned Chebyshev iteration on [cheb_lo, 1] * cheb_hi *
  * lambda, lambda = D-Rayleigh quotient after power_its power iterations on
- * D^-1 A_c from v_i = frac(i * 2654435761 / 2^32) - 1/2. Coarsest level:
+ * D^-1 A_c from v_i = frac(i * 2654435761 / 2^32) - 1/2 (A_c applied in
+ * double-float, FP64 vectors and dot products). Coarsest level:
  * coarse_its Jacobi-PCG iterations from zero. V-cycle: pre-smoothing from
  * zero, restricted residual, recursion, prolongated correction,
  * post-smoothing. 3D (hexahedral) forms only. Elasticity forms: every

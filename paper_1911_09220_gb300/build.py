@@ -59,7 +59,7 @@ def _compile(src, obj, nvcc, cuda_home, verbose_ptxas):
         if verbose_ptxas:
             cmd += ["-Xptxas", "-v"]
     else:
-        cmd = ["g++", "-c", src, "-o", obj, "-std=c++17", "-O2", "-fPIC", *inc,
+        cmd = ["g++", "-c", src, "-o", obj, "-std=c++17", "-O2", "-fPIC", "-pthread", *inc,
                "-I", os.path.join(cuda_home, "include")]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -97,7 +97,7 @@ def build(force=False, jobs=None, verbose_ptxas=False, quiet=True):
     if todo or not os.path.exists(LIB):
         tmp = LIB + ".tmp"
         rpath = os.path.join(cuda_home, "lib64")
-        cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart", "-Xlinker", "-rpath", "-Xlinker", rpath]
+        cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart", "-lpthread", "-Xlinker", "-rpath", "-Xlinker", rpath]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

@@ -1,6 +1,7 @@
 // Host side of the C ABI: errors, mesh ingest, the H1 space (global numbering,
 // element restriction table and its inverse, boundary DOFs) and form setup.
 #include <algorithm>
+#include <thread>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -169,6 +170,55 @@ int64_t first_appearance_ids(std::vector<K>& keys, std::vector<int32_t>& id_of_s
 static fem_status space_finish(fem_space* sp, fem_space** out);
 static fem_status space_create_2d(const fem_mesh* mesh, int p, fem_space** out);
 
+// Edge and face ids of a hexahedral mesh (first appearance order), built
+// once per mesh and shared by all its spaces: they do not depend on p.
+static void mesh_topology(const fem_mesh* mesh) {
+  std::lock_guard<std::mutex> lock(mesh->topo_mu);
+  if (mesh->topo_done) return;
+  const int64_t ne = mesh->ne, nv = mesh->nv;
+  const int32_t* hex = mesh->hex.data();
+  // edges: key lo*nv+hi, slot e*12+le
+  std::vector<Key2> ek((size_t)ne * 12);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int le = 0; le < 12; ++le) {
+      uint64_t a = (uint64_t)hex[8 * e + kEdge[le][0]], b = (uint64_t)hex[8 * e + kEdge[le][1]];
+      if (a > b) std::swap(a, b);
+      ek[e * 12 + le] = Key2{a * (uint64_t)nv + b, (uint32_t)(e * 12 + le)};
+    }
+  mesh->n_edges = first_appearance_ids(
+      ek, mesh->edge_id, [](const Key2& x, const Key2& y) { return x.a == y.a; },
+      [](const Key2& x, const Key2& y) { return x.a < y.a; });
+  std::vector<Key2>().swap(ek);
+  // faces: key of the sorted 4 corners
+  std::vector<Key4> fk((size_t)ne * 6);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int lf = 0; lf < 6; ++lf) {
+      uint64_t v[4];
+      for (int c = 0; c < 4; ++c) v[c] = (uint64_t)hex[8 * e + kFace[lf][c]];
+      std::sort(v, v + 4);
+      fk[e * 6 + lf] = Key4{v[0] * (uint64_t)nv + v[1], v[2] * (uint64_t)nv + v[3], (uint32_t)(e * 6 + lf)};
+    }
+  mesh->n_faces = first_appearance_ids(
+      fk, mesh->face_id, [](const Key4& x, const Key4& y) { return x.a == y.a && x.b == y.b; },
+      [](const Key4& x, const Key4& y) { return x.a < y.a || (x.a == y.a && x.b < y.b); });
+  mesh->topo_done = true;
+}
+
+// Run fn(e0, e1) over [0, ne) in contiguous element ranges on up to 16 host
+// threads (each element's work is independent).
+template <typename F>
+static void for_elements(int64_t ne, F fn) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), 16, ne / 4096 + 1}));
+  if (nt == 1) {
+    fn((int64_t)0, ne);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int64_t t = 0; t < nt; ++t) th.emplace_back(fn, ne * t / nt, ne * (t + 1) / nt);
+  for (auto& x : th) x.join();
+}
+
 extern "C" fem_status fem_space_create(const fem_mesh* mesh, int p, fem_space** out) {
   if (!out || !mesh) return fem_fail(FEM_EINVAL, "fem_space_create: NULL argument");
   *out = nullptr;
@@ -181,34 +231,10 @@ extern "C" fem_status fem_space_create(const fem_mesh* mesh, int p, fem_space** 
     return fem_fail(FEM_EUNSUPPORTED, "fem_space_create: ne*(p+1)^3 exceeds int32");
   const int32_t* hex = mesh->hex.data();
 
-  // edges: key lo*nv+hi, slot e*12+le
-  std::vector<Key2> ek((size_t)ne * 12);
-  for (int64_t e = 0; e < ne; ++e)
-    for (int le = 0; le < 12; ++le) {
-      uint64_t a = (uint64_t)hex[8 * e + kEdge[le][0]], b = (uint64_t)hex[8 * e + kEdge[le][1]];
-      if (a > b) std::swap(a, b);
-      ek[e * 12 + le] = Key2{a * (uint64_t)nv + b, (uint32_t)(e * 12 + le)};
-    }
-  std::vector<int32_t> edge_id;
-  const int64_t n_edges = first_appearance_ids(
-      ek, edge_id, [](const Key2& x, const Key2& y) { return x.a == y.a; },
-      [](const Key2& x, const Key2& y) { return x.a < y.a; });
-  std::vector<Key2>().swap(ek);
-
-  // faces: key of the sorted 4 corners
-  std::vector<Key4> fk((size_t)ne * 6);
-  for (int64_t e = 0; e < ne; ++e)
-    for (int lf = 0; lf < 6; ++lf) {
-      uint64_t v[4];
-      for (int c = 0; c < 4; ++c) v[c] = (uint64_t)hex[8 * e + kFace[lf][c]];
-      std::sort(v, v + 4);
-      fk[e * 6 + lf] = Key4{v[0] * (uint64_t)nv + v[1], v[2] * (uint64_t)nv + v[3], (uint32_t)(e * 6 + lf)};
-    }
-  std::vector<int32_t> face_id;
-  const int64_t n_faces = first_appearance_ids(
-      fk, face_id, [](const Key4& x, const Key4& y) { return x.a == y.a && x.b == y.b; },
-      [](const Key4& x, const Key4& y) { return x.a < y.a || (x.a == y.a && x.b < y.b); });
-  std::vector<Key4>().swap(fk);
+  mesh_topology(mesh);
+  const int64_t n_edges = mesh->n_edges, n_faces = mesh->n_faces;
+  const std::vector<int32_t>& edge_id = mesh->edge_id;
+  const std::vector<int32_t>& face_id = mesh->face_id;
 
   const int64_t pm1 = p - 1;
   const int64_t off_e = nv, off_f = off_e + n_edges * pm1, off_i = off_f + n_faces * pm1 * pm1;
@@ -264,7 +290,8 @@ extern "C" fem_status fem_space_create(const fem_mesh* mesh, int p, fem_space** 
   sp->n_edges = n_edges;
   sp->n_faces = n_faces;
   sp->e2l.assign((size_t)ne * nd, -1);
-  for (int64_t e = 0; e < ne; ++e) {
+  for_elements(ne, [&](int64_t e0, int64_t e1) {
+  for (int64_t e = e0; e < e1; ++e) {
     const int32_t* h = hex + 8 * e;
     int32_t* row = sp->e2l.data() + (size_t)e * nd;
     for (int k = 0; k < nd; ++k) {
@@ -300,6 +327,7 @@ extern "C" fem_status fem_space_create(const fem_mesh* mesh, int p, fem_space** 
       }
     }
   }
+  });
 
   // boundary DOFs: every lattice point of a face with one adjacent element
   {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -56,6 +57,13 @@ struct fem_mesh {
   // optional order-k nodal geometry (Sec. 3.1 "nodes"): [ne][(k+1)^3][3]
   int geo_k = 0;
   double* d_gnodes = nullptr;
+  // hexahedral topology shared by every space on the mesh (built by the
+  // first fem_space_create): edge and face ids in order of first appearance
+  // per (element, local edge / face) slot
+  mutable std::mutex topo_mu;
+  mutable bool topo_done = false;
+  mutable int64_t n_edges = 0, n_faces = 0;
+  mutable std::vector<int32_t> edge_id, face_id;  // [ne][12], [ne][6]
 };
 
 struct fem_space {

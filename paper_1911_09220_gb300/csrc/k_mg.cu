@@ -20,7 +20,8 @@
 //   smoother    K Chebyshev steps with Jacobi preconditioning (Saad, Iterative
 //               Methods for Sparse Linear Systems, Alg. 12.1) on
 //               [cheb_lo, 1] * cheb_hi * lambda, lambda = the D-Rayleigh
-//               quotient after power iterations on D^-1 A_c;
+//               quotient after power iterations on D^-1 A_c (the operator
+//               applied in double-float);
 //   coarsest    a fixed number of Jacobi-PCG iterations from zero;
 //   outer       flexible CG (Notay 2000; beta = z.(r - r_old) / z_old.r_old)
 //               in FP64, the V-cycle in FP64 or FP32.
@@ -555,6 +556,14 @@ fem_status level_apply(const MgLevel& L, const T* x, T* y, const int* skip, cuda
 
 int vblocks(int64_t n) { return grid_for(n, 256); }
 
+// y = A_c x in double-float element arithmetic on FP64 vectors (x zero on
+// essential DOFs): the lambda estimate needs no more than its ~1e-13
+// accuracy, and it runs on the FP32 pipe at about 4x the FP64 apply's rate.
+fem_status level_apply_df(const MgLevel& L, const double* x, double* y, const int* skip, cudaStream_t s) {
+  FEM_TRY(fem_launch_apply_element(L.f, FEM_DF64, x, L.f->d_ye, s, skip));
+  return fem_launch_scatter(L.f, FEM_F64, L.f->d_ye, y, L.f->d_ess_mask, x, nullptr, 0, s, skip);
+}
+
 // Dispatch of the interpolation kernel over the compiled (D1f, D1c) pairs.
 template <typename T>
 fem_status launch_interp(int D1f, int D1c, bool prolong, int ne, const int32_t* map, const uint8_t* ess, const T* in,
@@ -685,6 +694,8 @@ fem_status precond(fem_mg* m, const double* r, double* z, const int* skip, cudaS
   return FEM_OK;
 }
 
+fem_status power_lambda_iterate(fem_mg* m, MgLevel& L, double* v, double* w, double* u, cudaStream_t s);
+
 fem_status read_words(fem_mg* m, const void* d, size_t bytes, void* out, cudaStream_t s) {
   FEM_CUDA(cudaMemcpyAsync(m->h, d, bytes, cudaMemcpyDeviceToHost, s));
   FEM_CUDA(cudaStreamSynchronize(s));
@@ -692,9 +703,23 @@ fem_status read_words(fem_mg* m, const void* d, size_t bytes, void* out, cudaStr
   return FEM_OK;
 }
 
-// lambda of D^-1 A_c on level L (FP64 operator), power iterations as in the
-// module header; uses the level's FP64 scratch w64 (4 n doubles).
+// lambda of D^-1 A_c on level L (double-float operator, FP64 vectors and
+// dot products), power iterations as in the module header; uses the level's
+// FP64 scratch w64 (4 n doubles). A double-float copy of D made only for
+// this is freed again.
 fem_status power_lambda(fem_mg* m, MgLevel& L, double* v, double* w, double* u, cudaStream_t s) {
+  const bool had_df = L.f->d_Ddf != nullptr;
+  fem_status st = power_lambda_iterate(m, L, v, w, u, s);
+  if (!had_df) {
+    fem_form* f = const_cast<fem_form*>(L.f);
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == FEM_OK)
+      st = fem_fail(FEM_ECUDA, "multigrid: lambda estimate failed");
+    dev_free(f->d_Ddf);
+  }
+  return st;
+}
+
+fem_status power_lambda_iterate(fem_mg* m, MgLevel& L, double* v, double* w, double* u, cudaStream_t s) {
   const int64_t n = L.n;
   const int nb = vblocks(n);
   const int* never = m->d_never;
@@ -713,7 +738,7 @@ fem_status power_lambda(fem_mg* m, MgLevel& L, double* v, double* w, double* u, 
   FEM_LAUNCHED();
   double lam = 0.0;
   for (int it = 0; it < m->o.power_its; ++it) {
-    FEM_TRY(level_apply<double>(L, v, w, never, s));
+    FEM_TRY(level_apply_df(L, v, w, never, s));
     k_pow_dots<<<nb, 256, 0, s>>>(n, v, w, L.diag64, u, m->part);
     k_sum3<<<1, kRed, 0, s>>>(m->part, nb, sums);
     FEM_LAUNCHED();
