@@ -244,3 +244,27 @@ def test_multigrid_solve_trilinear_and_curved(p, curvedk):
         assert info["converged"], (precision, info)
         u = x.cpu().numpy()
         assert np.linalg.norm(bco - Ac @ u) / np.linalg.norm(bco) <= 1.01e-10, precision
+
+
+def test_deterministic():
+    """Fixed-order scatter and reductions: repeated applies and multigrid
+    solves give bit-identical results."""
+    import torch
+    import paper_1911_09220_gb300 as F
+    form, prob, (c, h, lam, mu) = _setup(3)
+    x = cuda(x_uniform(21, form.n))
+    y1, y2 = torch.empty_like(x), torch.empty_like(x)
+    for arith in (None, "df64"):
+        form.apply(x, y1, arith=arith)
+        form.apply(x, y2, arith=arith)
+        assert torch.equal(y1, y2)
+    ndof = form.space.ndof
+    bd = form.space.boundary_dofs()
+    form.set_essential(np.concatenate([bd + k * ndof for k in range(3)]))
+    bc = torch.empty_like(x)
+    form.lift_rhs(x, torch.zeros_like(x), bc)
+    mg = F.Multigrid(form, precision="f32")
+    u1, u2 = torch.zeros_like(x), torch.zeros_like(x)
+    i1 = mg.solve(bc, u1, rtol=1e-10)
+    i2 = mg.solve(bc, u2, rtol=1e-10)
+    assert i1["iterations"] == i2["iterations"] and torch.equal(u1, u2)
