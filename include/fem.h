@@ -429,8 +429,10 @@ fem_status fem_mg_restrict(fem_mg* mg, int level, const double* rf, double* rc, 
  * residual disagrees with the recursive one), check_every, use_graph, and
  * precision FEM_SOLVE_F64 or FEM_SOLVE_DF64 (arithmetic of the outer
  * operator apply; the final true residual is always FP64); the other fields
- * are ignored. Synchronises `stream`. Errors: FEM_EINVAL (other precision),
- * FEM_ENOCONV, FEM_EBREAKDOWN. */
+ * are ignored. The essential entries of the initial guess are replaced by
+ * those of b (A_c x = b fixes them; the V-cycle never corrects them).
+ * Synchronises `stream`. Errors: FEM_EINVAL (other precision), FEM_ENOCONV,
+ * FEM_EBREAKDOWN. */
 fem_status fem_mg_solve(fem_mg* mg, const double* b, double* x, const fem_solve_opts* opts,
                         fem_solve_info* info, void* stream);
 

@@ -138,6 +138,14 @@ __global__ void k_mg_spread(int64_t nslots, const int32_t* __restrict__ e2l, con
   }
 }
 
+// dst_i = src_i on essential DOFs.
+__global__ void k_copy_ess(int64_t n, const uint8_t* __restrict__ ess, const double* __restrict__ src,
+                           double* __restrict__ dst) {
+  GRID_LOOP(i, n) {
+    if (ess[i]) dst[i] = src[i];
+  }
+}
+
 // Prolongation, second half: z_i += (free i) ? ye[first slot of i] : 0
 template <typename T>
 __global__ void k_mg_pick(int64_t n, const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
@@ -1102,6 +1110,10 @@ extern "C" fem_status fem_mg_solve(fem_mg* m, const double* b, double* xio, cons
   fem_solve_info inf;
   std::memset(&inf, 0, sizeof inf);
   FEM_CUDA(cudaMemcpyAsync(x, xio, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  // A_c x = b fixes the essential entries: x_ess = b_ess (the V-cycle never
+  // corrects them, so an initial guess that disagrees there is replaced)
+  k_copy_ess<<<vblocks(n), 256, 0, s>>>(n, L.f->d_ess_mask, b, x);
+  FEM_LAUNCHED();
   // ||b||^2
   k_dot2<<<nb, 256, 0, s>>>(n, b, b, m->part);
   k_sum1<<<1, kRed, 0, s>>>(m->part, nb, m->part + 3 * nb);

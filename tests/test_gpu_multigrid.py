@@ -287,3 +287,24 @@ def test_elasticity_solve(p, N, precision):
     assert abs(info["iterations"] - ito) <= 1
     _, pinfo = osolve.pcg(Ac, bco, rtol=1e-10)
     assert 3 * info["iterations"] < pinfo["iterations"]
+
+
+def test_solve_with_dirichlet_values_from_zero_guess():
+    """Non-zero essential values g: b_c = lift(b, g) has b_ess = g; starting
+    from x = 0 the solve takes x_ess = g and converges on the free DOFs."""
+    import torch
+    M, G, form, fine, ess, keep = _setup(3, 3)
+    n = fine.ndof
+    g = np.zeros(n)
+    g[ess] = x_uniform(41, len(ess))
+    bvec = x_uniform(42, n)
+    bc = torch.empty(n, dtype=torch.float64, device="cuda")
+    form.lift_rhs(cuda(bvec), cuda(g), bc)
+    x = torch.zeros_like(bc)
+    info = G.solve(bc, x, rtol=1e-10)
+    assert info["converged"]
+    u = x.cpu().numpy()
+    assert np.array_equal(u[ess], g[ess])
+    Ac = M.levels[0].A
+    bco = osolve.constrain_rhs(fine.K, bvec, ess, g[ess])
+    assert np.linalg.norm(bco - Ac @ u) / np.linalg.norm(bco) <= 1.01e-10
