@@ -616,6 +616,70 @@ def run_paper2d(args):
     return 0
 
 
+MG_SWEEP = [(2, 0.25, 1.1, 20), (2, 0.25, 1.1, 30), (2, 0.25, 1.1, 40), (2, 0.25, 1.1, 60), (3, 0.2, 1.1, 30),
+            (3, 0.2, 1.1, 40), (4, 0.2, 1.1, 30), (2, 0.3, 1.2, 30)]
+
+
+def run_mgsweep(args):
+    """Smoother and coarse-solve parameters of the p-multigrid solve: for each
+    (Chebyshev order K, interval low end, cheb_hi, coarsest-level PCG
+    iterations) of MG_SWEEP, flexible CG with an FP32 V-cycle and the
+    double-float outer operator, best of two solves. --kind diffusion: the
+    mg workload's problem (p, N, rtol 1e-10); --kind elasticity: the
+    elasticity workload's problem for each p of --orders (rtol 1e-8). One
+    JSON line per configuration."""
+    import torch
+    from paper_1911_09220_gb300 import build as fbuild
+    fbuild.build()
+    import paper_1911_09220_gb300 as F
+    from fem_inputs import hex_lattice, lognormal
+    problems = []
+    if args.kind == "diffusion":
+        p, N = args.p, args.N
+        c, h, kappa, _ = make_problem(p, N)
+        space = F.Space(F.Mesh(c, h), p)
+        form = F.Form(space, "diffusion", p + 2, coef=torch.as_tensor(kappa, device="cuda"))
+        form.set_essential(torch.as_tensor(space.boundary_dofs(), device="cuda"))
+        b = torch.empty(space.ndof, dtype=torch.float64, device="cuda")
+        _sin_rhs(form, b)
+        problems.append((p, N, form, b, 1e-10))
+    else:
+        for p in [int(v) for v in args.orders.split(",")]:
+            N = ELAST_N[p]
+            c, h = hex_lattice(N, 0.15, seed=60 + p)
+            E = h.shape[0]
+            space = F.Space(F.Mesh(c, h), p)
+            form = F.Form.elasticity(space, torch.as_tensor(lognormal(70 + p, E), device="cuda"),
+                                     torch.as_tensor(lognormal(80 + p, E), device="cuda"), q1d=p + 2)
+            bd = torch.as_tensor(space.boundary_dofs(), device="cuda", dtype=torch.int64)
+            form.set_essential(torch.cat([bd + k * space.ndof for k in range(3)]).to(torch.int32))
+            fq = torch.zeros((3, E, (p + 2) ** 3), dtype=torch.float64, device="cuda")
+            fq[2] = -1.0
+            b = torch.empty(form.n, dtype=torch.float64, device="cuda")
+            form.rhs(fq, b)
+            problems.append((p, N, form, b, 1e-8))
+    for p, N, form, b, rtol in problems:
+        bc = torch.empty_like(b)
+        form.lift_rhs(b, torch.zeros_like(b), bc)
+        for K, lo, hi, cits in MG_SWEEP:
+            mg = F.Multigrid(form, cheb_order=K, cheb_lo=lo, cheb_hi=hi, coarse_its=cits, precision="f32")
+            best, it, conv = None, None, None
+            for _ in range(2):
+                u = torch.zeros_like(b)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info = mg.solve(bc, u, rtol=rtol, check_every=4, raise_on_error=False, arith="df64")
+                torch.cuda.synchronize()
+                t = time.perf_counter() - t0
+                if best is None or t < best:
+                    best, it, conv = t, info["iterations"], info["converged"]
+            print(json.dumps({"kind": args.kind, "p": p, "N": N, "rtol": rtol, "cheb_order": K, "cheb_lo": lo,
+                              "cheb_hi": hi, "coarse_its": cits, "iterations": it, "seconds": best,
+                              "converged": conv}), flush=True)
+            del mg
+    return 0
+
+
 def run_mg(args):
     """p-multigrid workload: the apply workload's problem (p, N; lognormal
     kappa, sin sin sin right-hand side, homogeneous Dirichlet conditions),
@@ -772,7 +836,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--solve-maxit", type=int, default=20000)
     ap.add_argument("--workload", default="apply", choices=["apply", "sweep", "batch", "grad", "paper2d", "mg", "curved",
-                                                         "elasticity"])
+                                                         "elasticity", "mgsweep"])
+    ap.add_argument("--kind", default="diffusion", choices=["diffusion", "elasticity"])
     ap.add_argument("--sweep-size", default="4e6", choices=["1e6", "4e6", "2e7", "3e7"])
     ap.add_argument("--orders", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--nprob", type=int, default=256)
@@ -796,6 +861,8 @@ def main():
         return run_grad(args)
     if args.workload == "elasticity":
         return run_elasticity(args)
+    if args.workload == "mgsweep":
+        return run_mgsweep(args)
 
     import torch
     import torch.distributed as dist
