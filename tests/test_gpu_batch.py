@@ -154,3 +154,59 @@ def test_vector_form_is_a_one_problem_batch(kind):
     bt.apply(X, Y)
     A = sp.kron(sp.identity(vdim), prob.matrix(kind)).tocsr()
     assert relerr(Y.cpu().numpy(), A @ X.cpu().numpy()) <= TOL
+
+
+def test_config_size_batch():
+    """The batching configuration at full size, in the bench's launch
+    configuration: 256 diffusion problems, N_i ~ U{2..24} and p_i ~ U{1..6}
+    from SplitMix64 seed 40 (N = 2 + d mod 23, p = 1 + d mod 6 on
+    alternating draws), meshes seeded 4000 + i, kappa 5000 + i, 8
+    right-hand sides from x seed 41 (71.5M DOFs, 572M unknowns). Every
+    problem and right-hand side against the single-problem apply (FP64
+    1e-12, FP32 2e-5 relative), and sampled rows of three problems against
+    the oracle's row-by-row apply."""
+    import torch
+    import paper_1911_09220_gb300 as F
+    from fem_inputs import hex_lattice
+    from oracle import numbering
+    d = splitmix64(40, 512)
+    Ns = [2 + int(v % np.uint64(23)) for v in d[0::2]]
+    ps = [1 + int(v % np.uint64(6)) for v in d[1::2]]
+    forms, meshes = [], []
+    for i, (N, p) in enumerate(zip(Ns, ps)):
+        c, h = hex_lattice(N, 0.15, seed=4000 + i)
+        kap = lognormal(5000 + i, h.shape[0])
+        sp = F.Space(F.Mesh(c, h), p)
+        forms.append(F.Form(sp, "diffusion", p + 2, coef=cuda(kap)))
+        meshes.append((c, h, kap))
+    bt = F.Batch(forms, 8)
+    assert bt.total_len == 8 * int(bt.off[-1])
+    X = cuda(x_uniform(41, bt.total_len))
+    Y = torch.empty_like(X)
+    bt.apply(X, Y)
+    for i, f in enumerate(forms):
+        for r in (0, 7):
+            x = bt.block(X, i, r).contiguous()
+            y = torch.empty_like(x)
+            f.apply(x, y)
+            assert relerr(bt.block(Y, i, r).cpu().numpy(), y.cpu().numpy()) <= TOL, (i, r)
+    # FP32 batch on the same systems
+    X32 = X.float()
+    Y32 = torch.empty_like(X32)
+    bt.apply(X32, Y32)
+    for i in range(0, 256, 17):
+        x = bt.block(X32, i, 3).contiguous()
+        y = torch.empty_like(x)
+        forms[i].apply(x, y)
+        assert relerr(bt.block(Y32, i, 3).double().cpu().numpy(), y.double().cpu().numpy()) <= 2e-5, i
+    # oracle rows for the three largest problems
+    big = sorted(range(256), key=lambda i: -forms[i].space.ndof)[:3]
+    for i in big:
+        c, h, kap = meshes[i]
+        p = ps[i]
+        num = numbering.build(h, p, nv=c.shape[0])
+        x = bt.block(X, i, 5).cpu().numpy()
+        rows = np.unique(np.random.default_rng(i).integers(0, num["ndof"], 40))
+        ref = assemble.sampled_apply(c, h, num["e2l"], p, p + 2, "diffusion", kap, x, rows)
+        got = bt.block(Y, i, 5).cpu().numpy()[rows]
+        assert np.abs(got - ref).max() <= TOL * np.abs(ref).max(), i

@@ -1,8 +1,10 @@
-"""Parity at the benchmark's full size, in the launch configuration bench.py
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
 times: p = 4, q = 6, 68^3 hexes perturbed 0.15h (20,346,417 DOFs), the
-same seeded generators (mesh seed 14, lognormal seed 24, x seed 34). The
-oracle cannot assemble this matrix, so it computes sampled outputs one DOF
-at a time from the rows of the element matrices that hold the DOF
+same seeded generators (mesh seed 14, lognormal seed 24, x seed 34); the
+precision configuration's p = 6, 45^3 (19,902,511 DOFs); and the sweep
+configuration at its 1e6-DOF size for every p = 1..8. The oracle cannot
+assemble these matrices, so it computes sampled outputs one DOF at a time
+from the rows of the element matrices that hold the DOF
 (oracle.assemble.sampled_apply, with its own numbering); properties that
 hold at any size are checked on the whole output vector."""
 
@@ -91,3 +93,44 @@ def test_properties_on_the_whole_vector(full):
     a, b = torch.dot(u, Av).item(), torch.dot(v, Au).item()
     assert abs(a - b) <= 1e-12 * (u.abs() * Av.abs()).sum().item()
     assert torch.dot(u, Au).item() > 0
+
+
+# (p, N): the sweep's 1e6-DOF lattices (p = 1..8) and the precision
+# configuration's p = 6 at ~2e7 DOFs; q = p + 2, the sweep's seeds
+CONFIG_SIZES = [(1, 99), (2, 49), (3, 33), (4, 25), (5, 20), (6, 16), (7, 14), (8, 12), (6, 45)]
+
+
+@pytest.mark.parametrize("p,N", CONFIG_SIZES)
+def test_sampled_rows_config_sizes(p, N):
+    import torch
+    import paper_1911_09220_gb300 as F
+    q = p + 2
+    c, h = hex_lattice(N, 0.15, seed=10 + p)
+    kap = lognormal(20 + p, h.shape[0])
+    num = numbering.build(h, p, nv=c.shape[0])
+    n = num["ndof"]
+    space = F.Space(F.Mesh(c, h), p)
+    assert space.ndof == n
+    x = x_uniform(30 + p, n)
+    rng = np.random.default_rng(100 + p)
+    nv = c.shape[0]
+    starts = [0, nv, nv + num["n_edges"] * (p - 1), nv + num["n_edges"] * (p - 1) + num["n_faces"] * (p - 1) ** 2, n]
+    rows = [rng.integers(starts[k], starts[k + 1], 6) for k in range(4) if starts[k + 1] > starts[k]]
+    rows.append(rng.choice(num["boundary_dofs"], 6, replace=False))
+    rows.append(rng.integers(0, n, 10))
+    rows = np.unique(np.concatenate(rows))
+    xd = cuda(x)
+    rt = torch.as_tensor(rows, device="cuda")
+    for kind in ("diffusion", "mass"):
+        ref = assemble.sampled_apply(c, h, num["e2l"], p, q, kind, kap, x, rows)
+        scale = np.abs(ref).max()
+        form = F.Form(space, kind, q, coef=cuda(kap))
+        y = torch.empty_like(xd)
+        form.apply(xd, y)
+        assert np.abs(y[rt].cpu().numpy() - ref).max() <= 1e-12 * scale, (kind, "f64")
+        form.apply(xd, y, arith="df64")
+        assert np.abs(y[rt].cpu().numpy() - ref).max() <= 1e-12 * scale, (kind, "df64")
+        y32 = torch.empty(n, dtype=torch.float32, device="cuda")
+        form.apply(xd.float(), y32)
+        assert np.abs(y32[rt].double().cpu().numpy() - ref).max() <= 2e-5 * scale, (kind, "f32")
+        del form, y, y32
