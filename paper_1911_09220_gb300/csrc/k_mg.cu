@@ -484,7 +484,8 @@ __global__ void k_hash_vec(int64_t n, const uint8_t* __restrict__ ess, double* _
   }
 }
 
-__global__ void k_scale(int64_t n, const double* __restrict__ a, double s, double* __restrict__ b) {
+// b = s a; may run in place (b == a), so the pointers are not restrict.
+__global__ void k_scale(int64_t n, const double* a, double s, double* b) {
   GRID_LOOP(i, n) b[i] = a[i] * s;
 }
 
