@@ -457,6 +457,14 @@ def run_elasticity(args):
                                    "relres": info["relres"], "converged": info["converged"],
                                    "hierarchy_setup_s": t_mg}
             sol["speedup_pmg"] = sol["f64"]["seconds"] / sol["pmg_f32_df64"]["seconds"]
+            u = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = mg.solve(bc, u, rtol=1e-8, check_every=4, raise_on_error=False, arith="f32")
+            torch.cuda.synchronize()
+            sol["pmg_f32_f32"] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
+                                  "outer": info["outer"], "relres": info["relres"], "converged": info["converged"]}
+            sol["speedup_pmg_f32_outer"] = sol["f64"]["seconds"] / sol["pmg_f32_f32"]["seconds"]
             del mg
             out["solve_1e-8"] = sol
         print(json.dumps(out), flush=True)
@@ -714,7 +722,7 @@ def run_mg(args):
         res = {"setup_s": ts, "levels": mg.info()}
         z = torch.empty_like(b)
         res["vcycle_ms"] = time_events(lambda: mg.vcycle(bc, z), 5, 2)
-        for arith in ("f64", "df64"):
+        for arith in ("f64", "df64", "f32"):
             best = None
             for _ in range(2):
                 u = torch.zeros_like(b)
@@ -1066,6 +1074,17 @@ def main():
                                  "levels": mg.info()["orders"]}
         solve["pmg_vs_f64_maxrel"] = (u - sols["f64"]).abs().max().item() / sols["f64"].abs().max().item()
         solve["speedup_pmg"] = solve["f64"]["seconds"] / dt
+        # the same with the FP32 outer operator inside FP64 refinement
+        u = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = mg.solve(bc, u, rtol=1e-10, check_every=4, raise_on_error=False, arith="f32")
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        solve["pmg_f32_f32"] = {"seconds": dt, "iterations": info["iterations"], "outer": info["outer"],
+                                "converged": info["converged"], "relres": info["relres"],
+                                "vs_f64_maxrel": (u - sols["f64"]).abs().max().item() / sols["f64"].abs().max().item()}
+        solve["speedup_pmg_f32_outer"] = solve["f64"]["seconds"] / dt
         del mg
         solve["rtol"] = 1e-10
 

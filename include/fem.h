@@ -427,8 +427,11 @@ fem_status fem_mg_restrict(fem_mg* mg, int level, const double* rf, double* rc, 
  * constrained operator, preconditioned by one V-cycle per iteration. x and b
  * as for fem_solve; opts: rtol, maxit, max_outer (restarts when the true
  * residual disagrees with the recursive one), check_every, use_graph, and
- * precision FEM_SOLVE_F64 or FEM_SOLVE_DF64 (arithmetic of the outer
- * operator apply; the final true residual is always FP64); the other fields
+ * precision, the arithmetic of the outer operator apply: FEM_SOLVE_F64,
+ * FEM_SOLVE_DF64, or FEM_SOLVE_MIXED (the FP32 operator, p and q rounded to
+ * FP32 around it, inside FP64 iterative refinement: each pass runs until the
+ * recursive residual has dropped by inner_rtol, then restarts from the FP64
+ * true residual); the final true residual is always FP64; the other fields
  * are ignored. The essential entries of the initial guess are replaced by
  * those of b (A_c x = b fixes them; the V-cycle never corrects them).
  * Synchronises `stream`. Errors: FEM_EINVAL (other precision), FEM_ENOCONV,

@@ -480,16 +480,19 @@ class Multigrid:
         return z
 
     def solve(self, b, x, rtol=1e-10, maxit=500, max_outer=30, check_every=4, use_graph=True, stream=None,
-              raise_on_error=True, arith="f64"):
-        """Flexible CG with one V-cycle per iteration; arith: "f64" or "df64"
-        (double-float) for the outer operator apply."""
+              raise_on_error=True, arith="f64", inner_rtol=1e-4):
+        """Flexible CG with one V-cycle per iteration. arith, the outer
+        operator apply: "f64", "df64" (double-float), or "f32" (FP32 operator
+        inside FP64 iterative refinement: each pass reduces the residual by
+        inner_rtol, then restarts from the FP64 true residual)."""
         import torch
         o = B.SolveOpts()
         B.lib().fem_solve_opts_default(C.byref(o))
         o.rtol, o.maxit, o.max_outer = rtol, maxit, max_outer
-        if arith not in ("f64", "df64"):
-            raise ValueError(f"arith must be 'f64' or 'df64', not {arith!r}")
-        o.precision = FEM_SOLVE_F64 if arith == "f64" else FEM_SOLVE_DF64
+        if arith not in ("f64", "df64", "f32"):
+            raise ValueError(f"arith must be 'f64', 'df64' or 'f32', not {arith!r}")
+        o.precision = {"f64": FEM_SOLVE_F64, "df64": FEM_SOLVE_DF64, "f32": FEM_SOLVE_MIXED}[arith]
+        o.inner_rtol = inner_rtol
         o.check_every, o.use_graph = check_every, int(bool(use_graph))
         info = B.SolveInfo()
         st = B.lib().fem_mg_solve(self._h, _ptr(b, torch.float64, "b"), _ptr(x, torch.float64, "x"), C.byref(o),

@@ -138,6 +138,19 @@ __global__ void k_mg_spread(int64_t nslots, const int32_t* __restrict__ e2l, con
   }
 }
 
+// FP64 <-> FP32 copies of the outer iteration's p and q (skip-aware, so
+// that captured iterations after convergence do nothing).
+__global__ void k_p_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b,
+                           const int* __restrict__ skip) {
+  if (*skip) return;
+  GRID_LOOP(i, n) b[i] = (float)a[i];
+}
+__global__ void k_q_to_f64(int64_t n, const float* __restrict__ a, double* __restrict__ b,
+                           const int* __restrict__ skip) {
+  if (*skip) return;
+  GRID_LOOP(i, n) b[i] = (double)a[i];
+}
+
 // dst_i = src_i on essential DOFs.
 __global__ void k_copy_ess(int64_t n, const uint8_t* __restrict__ ess, const double* __restrict__ src,
                            double* __restrict__ dst) {
@@ -542,6 +555,7 @@ struct fem_mg {
   int* d_stop = nullptr;        // coarsest CG: stop word
   MgScalars* sc = nullptr;      // outer FCG scalars
   double* w64 = nullptr;        // FCG: x, r, rold, z, p, q, t
+  float* w32 = nullptr;         // FCG with the FP32 outer operator: p, q in FP32 (lazy)
   int* h = nullptr;             // pinned host words
   int never = 0;                // device word that stays 0 (standalone V-cycle)
   int* d_never = nullptr;
@@ -854,6 +868,7 @@ extern "C" void fem_mg_destroy(fem_mg* m) {
     if (L.sp_own) fem_space_destroy(L.sp_own);
   }
   if (m->zero) cudaFree(m->zero);
+  dev_free(m->w32);
   if (m->cc_vec) cudaFree(m->cc_vec);
   dev_free(m->part);
   dev_free(m->d_stop);
@@ -1062,8 +1077,20 @@ fem_status fcg_iteration(fem_mg* m, int dtype, double* x, double* r, double* rol
   const int64_t n = L.n;
   const int nb = m->nb;
   const int* skip = &m->sc->done;
-  FEM_TRY(fem_launch_apply_element(L.f, dtype, p, L.f->d_ye, s, skip));
-  FEM_TRY(fem_launch_scatter(L.f, FEM_F64, L.f->d_ye, q, L.f->d_ess_mask, p, m->part, nb, s, skip));
+  if (dtype == FEM_F32) {
+    // FP32 operator on the FP64 iteration: p -> FP32, FP32 apply with the
+    // constrained rows and the p.q partials (accumulated in FP64), q -> FP64
+    float *p32 = m->w32, *q32 = m->w32 + n;
+    k_p_to_f32<<<vblocks(n), 256, 0, s>>>(n, p, p32, skip);
+    FEM_LAUNCHED();
+    FEM_TRY(fem_launch_apply_element(L.f, FEM_F32, p32, L.f->d_ye, s, skip));
+    FEM_TRY(fem_launch_scatter(L.f, FEM_F32, L.f->d_ye, q32, L.f->d_ess_mask, p32, m->part, nb, s, skip));
+    k_q_to_f64<<<vblocks(n), 256, 0, s>>>(n, q32, q, skip);
+    FEM_LAUNCHED();
+  } else {
+    FEM_TRY(fem_launch_apply_element(L.f, dtype, p, L.f->d_ye, s, skip));
+    FEM_TRY(fem_launch_scatter(L.f, FEM_F64, L.f->d_ye, q, L.f->d_ess_mask, p, m->part, nb, s, skip));
+  }
   k_fg_alpha<<<1, kRed, 0, s>>>(m->sc, m->part, nb);
   k_fg_update<<<nb, 256, 0, s>>>(n, m->sc, x, r, rold, p, q, m->part);
   k_fg_check<<<1, kRed, 0, s>>>(m->sc, m->part, nb);
@@ -1098,13 +1125,20 @@ extern "C" fem_status fem_mg_solve(fem_mg* m, const double* b, double* xio, cons
   fem_solve_opts_default(&o);
   if (opts) o = *opts;
   if (!(o.rtol > 0) || o.maxit <= 0) return fem_fail(FEM_EINVAL, "fem_mg_solve: rtol > 0 and maxit > 0 required");
-  if (o.precision != FEM_SOLVE_F64 && o.precision != FEM_SOLVE_DF64)
-    return fem_fail(FEM_EINVAL, "fem_mg_solve: precision must be FEM_SOLVE_F64 or FEM_SOLVE_DF64");
-  const int dtype = o.precision == FEM_SOLVE_DF64 ? FEM_DF64 : FEM_F64;
+  if (o.precision != FEM_SOLVE_F64 && o.precision != FEM_SOLVE_DF64 && o.precision != FEM_SOLVE_MIXED)
+    return fem_fail(FEM_EINVAL, "fem_mg_solve: precision must be FEM_SOLVE_F64, FEM_SOLVE_DF64 or FEM_SOLVE_MIXED");
+  const bool mixed = o.precision == FEM_SOLVE_MIXED;
+  if (mixed && !(o.inner_rtol > 0.0 && o.inner_rtol < 1.0))
+    return fem_fail(FEM_EINVAL, "fem_mg_solve: FEM_SOLVE_MIXED needs 0 < inner_rtol < 1");
+  const int dtype = o.precision == FEM_SOLVE_DF64 ? FEM_DF64 : mixed ? FEM_F32 : FEM_F64;
   cudaStream_t s = (cudaStream_t)stream;
-  if (dtype == FEM_DF64) FEM_TRY(fem_form_ensure_df64(m->lv[0].f, s));
   const MgLevel& L = m->lv[0];
   const int64_t n = L.n;
+  if (dtype == FEM_DF64) FEM_TRY(fem_form_ensure_df64(L.f, s));
+  if (mixed) {
+    FEM_TRY(fem_form_ensure_f32(L.f, s));
+    if (!m->w32) FEM_TRY(dev_alloc(&m->w32, (size_t)2 * n));
+  }
   const int nb = m->nb;
   double* w = m->w64;
   double *x = w, *r = w + n, *rold = w + 2 * n, *z = w + 3 * n, *p = w + 4 * n, *q = w + 5 * n, *t = w + 6 * n;
@@ -1155,7 +1189,10 @@ extern "C" fem_status fem_mg_solve(fem_mg* m, const double* b, double* xio, cons
     FEM_TRY(precond(m, r, z, m->d_never, s));
     FEM_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     k_dot2<<<nb, 256, 0, s>>>(n, r, z, m->part);  // (r.z, r.r)
-    k_fg_init<<<1, kRed, 0, s>>>(m->sc, m->part, nb, tol2, o.maxit - total);
+    // FP32 outer operator: each pass reduces the true residual by inner_rtol
+    // (iterative refinement through the restarts); else straight to rtol
+    const double tol_pass = mixed ? std::max(tol2, o.inner_rtol * o.inner_rtol * rr) : tol2;
+    k_fg_init<<<1, kRed, 0, s>>>(m->sc, m->part, nb, tol_pass, o.maxit - total);
     FEM_LAUNCHED();
     // iterate: graph of k outer iterations, host polls between replays
     cudaGraphExec_t exec = nullptr;

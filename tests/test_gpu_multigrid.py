@@ -308,3 +308,44 @@ def test_solve_with_dirichlet_values_from_zero_guess():
     Ac = M.levels[0].A
     bco = osolve.constrain_rhs(fine.K, bvec, ess, g[ess])
     assert np.linalg.norm(bco - Ac @ u) / np.linalg.norm(bco) <= 1.01e-10
+
+
+@pytest.mark.parametrize("p,N,face_only", [(2, 4, False), (4, 3, True), (8, 2, False)])
+def test_solve_fp32_outer_operator(p, N, face_only):
+    """Flexible CG with the FP32 outer operator inside FP64 iterative
+    refinement (arith="f32") reaches the same 1e-10 true residual (oracle
+    CSR) and the FP64-outer solution."""
+    import torch
+    M, G, form, fine, ess, keep = _setup(p, N, face_only=face_only, precision="f32")
+    bvec = x_uniform(60 + p, fine.ndof)
+    bc = torch.empty(fine.ndof, dtype=torch.float64, device="cuda")
+    form.lift_rhs(cuda(bvec), torch.zeros_like(bc), bc)
+    x64 = torch.zeros_like(bc)
+    G.solve(bc, x64, rtol=1e-10)
+    for inner in (1e-2, 1e-4):
+        x = torch.zeros_like(bc)
+        info = G.solve(bc, x, rtol=1e-10, arith="f32", inner_rtol=inner)
+        assert info["converged"] and info["outer"] >= 2
+        u = x.cpu().numpy()
+        Ac = M.levels[0].A
+        bco = osolve.constrain_rhs(fine.K, bvec, ess)
+        assert np.linalg.norm(bco - Ac @ u) / np.linalg.norm(bco) <= 1.01e-10
+        assert relerr(u, x64.cpu().numpy()) <= 1e-7
+    import paper_1911_09220_gb300 as F
+    with pytest.raises(F.FemError):
+        G.solve(bc, x, rtol=1e-10, arith="f32", inner_rtol=1.5)
+
+
+def test_elasticity_solve_fp32_outer_operator():
+    import torch
+    M, G, form, fine, ess = _esetup(4, 2, precision="f32")
+    n = fine.K.shape[0]
+    bvec = x_uniform(99, n)
+    bc = torch.empty(n, dtype=torch.float64, device="cuda")
+    form.lift_rhs(cuda(bvec), torch.zeros_like(bc), bc)
+    x = torch.zeros_like(bc)
+    info = G.solve(bc, x, rtol=1e-10, arith="f32")
+    assert info["converged"]
+    Ac = M.levels[0].A
+    bco = osolve.constrain_rhs(fine.K, bvec, ess)
+    assert np.linalg.norm(bco - Ac @ x.cpu().numpy()) / np.linalg.norm(bco) <= 1.01e-10
