@@ -4,10 +4,12 @@
  * The library computes the matrix-free (partially assembled) action y = A x of
  * the high-order H1 mass and diffusion operators on unstructured hexahedral
  * Q_p meshes by sum factorization, the assembled diagonal, the load vector,
- * the Jacobi-preconditioned CG solve built on the action (FP64, or FP32 inner
- * iterations inside FP64 iterative refinement), batched applies/solves over
- * many independent problems, and the compliance gradient with respect to a
- * per-element coefficient.
+ * the Jacobi-preconditioned CG solve built on the action (FP64, double-float,
+ * or FP32 inner iterations inside FP64 iterative refinement), batched
+ * applies/solves over many independent problems, and the compliance gradient
+ * with respect to a per-element coefficient. Beside these: quadrilateral (2D)
+ * meshes, curved (order-k nodal) geometry, the convection and linear
+ * elasticity forms, and a p-multigrid preconditioner with flexible CG.
  *
  * The operator follows the decomposition A = P^T G^T B^T D B G P of the paper
  * (Sec. 4.3 "Operator Decomposition"; P = I on one GPU): G is the element
