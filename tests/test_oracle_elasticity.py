@@ -84,3 +84,40 @@ def test_nodal_geometry_of_a_trilinear_mesh(k):
     Xn = curved.nodes_from_corners(c[h.astype(np.int64)], k)
     P1 = elasticity.ElasticityProblem(c, h, 2, 4, lam, mu, Xn=Xn, k=k)
     assert abs(P0.K - P1.K).max() <= 1e-12 * abs(P0.K).max()
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_reproduces_a_quadratic_solution(p):
+    """Affine mesh, constant lambda and mu: a quadratic displacement u lies
+    in the space, the body force f = -div sigma(u) = -((lambda + mu)
+    grad div u + mu lap u) is constant, so the discrete solution with
+    u on the boundary is u's interpolant itself (to rounding). The force is
+    derived symbolically (sympy), independently of the oracle's matrices."""
+    sympy = pytest.importorskip("sympy")
+    from oracle import solve as osolve
+    c, h = hex_lattice(2, 0.0, seed=1, shuffle=True)
+    A = np.array([[1.2, 0.3, -0.4], [0.2, 0.9, 0.1], [-0.1, 0.25, 1.1]])    # affine map of the unit cube
+    c = c @ A.T + np.array([0.3, -0.2, 0.1])
+    E = h.shape[0]
+    lam_v, mu_v = 1.7, 0.6
+    x, y, z = sympy.symbols("x y z")
+    X = (x, y, z)
+    u = [x * y - 0.5 * z ** 2 + 0.3 * x, 0.7 * x ** 2 + y * z - 0.2 * y, -0.4 * x * z + 0.9 * y ** 2 + z]
+    div = sum(sympy.diff(u[i], X[i]) for i in range(3))
+    f = [-((lam_v + mu_v) * sympy.diff(div, X[i]) + mu_v * sum(sympy.diff(u[i], X[j], 2) for j in range(3)))
+         for i in range(3)]
+    assert all(sympy.simplify(fi).is_number for fi in f)
+    fvals = [float(fi) for fi in f]
+    ep = elasticity.ElasticityProblem(c, h, p, p + 2, np.full(E, lam_v), np.full(E, mu_v))
+    sc = assemble.Problem(c, h, p, p + 2)
+    Xd = sc.dof_coords()
+    ufun = [sympy.lambdify(X, ui, "numpy") for ui in u]
+    uvec = np.concatenate([np.broadcast_to(ufun[k](Xd[:, 0], Xd[:, 1], Xd[:, 2]), (sc.ndof,)) for k in range(3)])
+    b = np.concatenate([sc.load(lambda Y, v=fvals[k]: np.full(Y.shape[:-1], v)) for k in range(3)])
+    n = sc.ndof
+    bd = sc.num["boundary_dofs"]
+    ess = np.concatenate([bd + k * n for k in range(3)])
+    bc = osolve.constrain_rhs(ep.K, b, ess, uvec[ess])
+    Ac = osolve.constrain(ep.K, ess)
+    uh = osolve.cholesky_solve(Ac, bc)
+    assert np.abs(uh - uvec).max() <= 1e-11 * np.abs(uvec).max()
