@@ -9,6 +9,12 @@ runs in the library's kernels on the current torch stream.
     form = Form(space, "diffusion", q1d=p + 2, coef=kappa)   # PA setup (D)
     form.apply(x, y)                             # y = A x
     form.diagonal(d); form.rhs(fq, b); form.solve(b, x, rtol=1e-10)
+    Multigrid(form, precision="f32").solve(b, x, arith="f32")   # p-multigrid FCG
+
+Also: Mesh2D (quadrilaterals), Mesh.set_nodes (curved geometry),
+Form.convection, Form.elasticity (vectors of 3 * ndof), Batch (many problems
+and right-hand sides in persistent kernels), and autograd.compliance (the
+compliance gradient through torch.autograd).
 """
 
 import ctypes as C
