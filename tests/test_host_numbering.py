@@ -1,0 +1,124 @@
+"""The library's host code (mesh ingest, topology, DOF numbering, inverse
+map, boundary DOFs; csrc/fem_host.cpp and fem_basis.cpp) on CPU: the sources
+are compiled against a test-only stand-in for the CUDA runtime
+(tests/host_stub: device memory is host memory) and called through the same
+C ABI. The element->DOF table and the boundary DOF list must equal the
+oracle's, built independently from entity keys (bit for bit), for 3D and
+2D meshes, shuffled vertex orders, several orders on one mesh (the shared
+topology), and meshes large enough for the multithreaded fill."""
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from fem_inputs import hex_lattice, quad_lattice
+from oracle import numbering, twod
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1911_09220_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def hostlib(tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("hostlib") / "libfem_host_test.so")
+    cmd = ["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-pthread", "-I", os.path.join(ROOT, "tests", "host_stub"),
+           "-I", os.path.join(ROOT, "include"), "-I", CSRC, os.path.join(CSRC, "fem_host.cpp"),
+           os.path.join(CSRC, "fem_basis.cpp"), os.path.join(ROOT, "tests", "host_stub", "stub.cpp"), "-o", out]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    L = C.CDLL(out, mode=C.RTLD_LOCAL)
+    P, I64 = C.c_void_p, C.c_int64
+    for name, res, args in [("fem_mesh_create", C.c_int, [P, I64, P, I64, C.POINTER(P)]),
+                            ("fem_mesh2d_create", C.c_int, [P, I64, P, I64, C.POINTER(P)]),
+                            ("fem_space_create", C.c_int, [P, C.c_int, C.POINTER(P)]),
+                            ("fem_space_info", C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64),
+                                                         C.POINTER(C.c_int)]),
+                            ("fem_space_element_dofs", C.c_int, [P, P]),
+                            ("fem_space_boundary_dofs", C.c_int, [P, P]),
+                            ("fem_space_destroy", None, [P]), ("fem_mesh_destroy", None, [P]),
+                            ("fem_last_error", C.c_char_p, [])]:
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+    return L
+
+
+def _mesh(L, coords, cells, dim):
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    m = C.c_void_p()
+    create = L.fem_mesh_create if dim == 3 else L.fem_mesh2d_create
+    assert create(coords.ctypes.data, coords.shape[0], cells.ctypes.data, cells.shape[0], C.byref(m)) == 0, \
+        L.fem_last_error()
+    return m
+
+
+def _space(L, m, p):
+    s = C.c_void_p()
+    assert L.fem_space_create(m, p, C.byref(s)) == 0, L.fem_last_error()
+    ndof, nbdr, ne = C.c_int64(), C.c_int64(), C.c_int64()
+    pp = C.c_int()
+    assert L.fem_space_info(s, C.byref(ndof), C.byref(nbdr), C.byref(ne), C.byref(pp)) == 0
+    return s, ndof.value, nbdr.value, ne.value
+
+
+def _tables(L, s, ne, nd, nbdr):
+    e2l = np.empty((ne, nd), dtype=np.int32)
+    bdr = np.empty(nbdr, dtype=np.int32)
+    assert L.fem_space_element_dofs(s, e2l.ctypes.data) == 0
+    assert L.fem_space_boundary_dofs(s, bdr.ctypes.data) == 0
+    return e2l, bdr
+
+
+@pytest.mark.parametrize("N,shuffle", [(3, False), (3, True), (20, True)])
+def test_3d_numbering_matches_oracle(hostlib, N, shuffle):
+    L = hostlib
+    c, h = hex_lattice(N, 0.1, seed=2, shuffle=shuffle)
+    m = _mesh(L, c, h, 3)
+    orders = [4, 2, 1, 3] if N <= 3 else [2, 1]
+    for p in orders:                       # several spaces on one mesh: shared topology
+        s, ndof, nbdr, ne = _space(L, m, p)
+        e2l, bdr = _tables(L, s, ne, (p + 1) ** 3, nbdr)
+        num = numbering.build(h, p, nv=c.shape[0])
+        assert ndof == num["ndof"]
+        assert np.array_equal(e2l, num["e2l"])
+        assert np.array_equal(bdr, np.asarray(num["boundary_dofs"], dtype=np.int32))
+        L.fem_space_destroy(s)
+    L.fem_mesh_destroy(m)
+
+
+@pytest.mark.parametrize("p", [1, 2, 5])
+def test_2d_numbering_matches_oracle(hostlib, p):
+    L = hostlib
+    c, q = quad_lattice(5, 0.1, seed=3, shuffle=True)
+    m = _mesh(L, c, q, 2)
+    s = C.c_void_p()
+    assert L.fem_space_create(m, p, C.byref(s)) == 0
+    ndof, nbdr, ne = C.c_int64(), C.c_int64(), C.c_int64()
+    pp = C.c_int()
+    L.fem_space_info(s, C.byref(ndof), C.byref(nbdr), C.byref(ne), C.byref(pp))
+    e2l, bdr = _tables(L, s, ne.value, (p + 1) ** 2, nbdr.value)
+    num = twod.numbering2(q, p, nv=c.shape[0])
+    assert ndof.value == num["ndof"]
+    assert np.array_equal(e2l, num["e2l"])
+    assert np.array_equal(bdr, np.asarray(num["boundary_dofs"], dtype=np.int32))
+    L.fem_space_destroy(s)
+    L.fem_mesh_destroy(m)
+
+
+def test_mesh_errors(hostlib):
+    L = hostlib
+    c, h = hex_lattice(2, 0.0, seed=1)
+    bad = h.copy()
+    bad[0, 1] = bad[0, 0]                  # repeated vertex
+    m = C.c_void_p()
+    coords = np.ascontiguousarray(c)
+    assert L.fem_mesh_create(coords.ctypes.data, c.shape[0], bad.ctypes.data, bad.shape[0], C.byref(m)) == 1
+    assert len(L.fem_last_error()) > 0
+    m = _mesh(L, c, h, 3)
+    s = C.c_void_p()
+    assert L.fem_space_create(m, 0, C.byref(s)) == 1
+    assert L.fem_space_create(m, 9, C.byref(s)) == 7
+    L.fem_mesh_destroy(m)
