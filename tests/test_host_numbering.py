@@ -24,7 +24,10 @@ CSRC = os.path.join(ROOT, "paper_1911_09220_gb300", "csrc")
 @pytest.fixture(scope="module")
 def hostlib(tmp_path_factory):
     out = str(tmp_path_factory.mktemp("hostlib") / "libfem_host_test.so")
-    cmd = ["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-pthread", "-I", os.path.join(ROOT, "tests", "host_stub"),
+    # -Bsymbolic: the library's calls bind to its own definitions even when
+    # the real libfem.so / libcudart were loaded globally by another test
+    cmd = ["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-pthread", "-Wl,-Bsymbolic",
+           "-I", os.path.join(ROOT, "tests", "host_stub"),
            "-I", os.path.join(ROOT, "include"), "-I", CSRC, os.path.join(CSRC, "fem_host.cpp"),
            os.path.join(CSRC, "fem_basis.cpp"), os.path.join(ROOT, "tests", "host_stub", "stub.cpp"), "-o", out]
     r = subprocess.run(cmd, capture_output=True, text=True)
