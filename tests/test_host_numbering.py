@@ -125,3 +125,46 @@ def test_mesh_errors(hostlib):
     assert L.fem_space_create(m, 0, C.byref(s)) == 1
     assert L.fem_space_create(m, 9, C.byref(s)) == 7
     L.fem_mesh_destroy(m)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_numbering_over_random_orderings(hostlib, seed):
+    """Random vertex and element numberings with random proper rotations of
+    every element's vertex list (fem_inputs' shuffle): the library's table
+    equals the oracle's for p = 3."""
+    L = hostlib
+    c, h = hex_lattice(3, 0.12, seed=40 + seed, shuffle=True, shuffle_seed=500 + seed)
+    m = _mesh(L, c, h, 3)
+    s, ndof, nbdr, ne = _space(L, m, 3)
+    e2l, bdr = _tables(L, s, ne, 64, nbdr)
+    num = numbering.build(h, 3, nv=c.shape[0])
+    assert np.array_equal(e2l, num["e2l"]) and np.array_equal(bdr, np.asarray(num["boundary_dofs"], np.int32))
+    L.fem_space_destroy(s)
+    L.fem_mesh_destroy(m)
+
+
+def test_malformed_meshes_are_rejected(hostlib):
+    L = hostlib
+    c, h = hex_lattice(2, 0.0, seed=1)
+    coords = np.ascontiguousarray(c)
+    m = C.c_void_p()
+
+    def create(cc, hh, nv=None, ne=None):
+        cc = np.ascontiguousarray(cc, dtype=np.float64)
+        hh = np.ascontiguousarray(hh, dtype=np.int32)
+        return L.fem_mesh_create(cc.ctypes.data, cc.shape[0] if nv is None else nv, hh.ctypes.data,
+                                 hh.shape[0] if ne is None else ne, C.byref(m))
+
+    assert create(c, h, ne=0) == 1                       # no elements
+    assert create(c, h, nv=0) == 1                       # no vertices
+    bad = h.copy()
+    bad[3, 5] = c.shape[0]                               # index out of range
+    assert create(c, bad) == 1
+    bad = h.copy()
+    bad[2, 0] = -1                                       # negative index
+    assert create(c, bad) == 1
+    extra = np.vstack([c, [[5.0, 5.0, 5.0]]])            # a vertex no element uses
+    assert create(extra, h) == 1
+    assert L.fem_mesh_create(None, c.shape[0], h.ctypes.data, h.shape[0], C.byref(m)) == 1
+    assert create(c, h) == 0                             # the valid mesh still builds
+    L.fem_mesh_destroy(m)
