@@ -747,3 +747,40 @@ extern "C" fem_status fem_form_set_essential(fem_form* f, const int32_t* ess, in
   }
   return FEM_OK;
 }
+
+// ------------------------------------------------------ multigrid (host) ----
+// Entity signature of local node k of a (D1)^3 lattice: per axis 0 (at 0),
+// 2 (at D1-1), 1 (inside); s = s_x + 3 s_y + 9 s_z.
+static int lattice_signature(int k, int D1) {
+  const int L[3] = {k % D1, (k / D1) % D1, k / (D1 * D1)};
+  int s = 0, w = 1;
+  for (int d = 0; d < 3; ++d, w *= 3) s += w * (L[d] == 0 ? 0 : L[d] == D1 - 1 ? 2 : 1);
+  return s;
+}
+
+// Coarse essential DOFs of the p-multigrid hierarchy (k_mg.cu): a coarse
+// DOF is essential iff every fine DOF of the same mesh entity (vertex, edge,
+// face or interior of one element) is. essf: the fine mask of one component
+// ([sf->ndof]); returns the coarse DOF ids, ascending.
+std::vector<int32_t> fem_coarse_essential(const fem_space* sf, const uint8_t* essf, const fem_space* sc) {
+  const int Df = sf->D1, Dc = sc->D1, ndf = sf->nd, ndc = sc->nd;
+  std::vector<int> sigf(ndf), sigc(ndc);
+  for (int k = 0; k < ndf; ++k) sigf[k] = lattice_signature(k, Df);
+  for (int k = 0; k < ndc; ++k) sigc[k] = lattice_signature(k, Dc);
+  std::vector<uint8_t> mark(sc->ndof, 0);
+  for (int64_t e = 0; e < sf->ne; ++e) {
+    int all[27];
+    for (int s = 0; s < 27; ++s) all[s] = 1;
+    const int32_t* rf = sf->e2l.data() + (size_t)e * ndf;
+    for (int k = 0; k < ndf; ++k)
+      if (!essf[rf[k]]) all[sigf[k]] = 0;
+    const int32_t* rc = sc->e2l.data() + (size_t)e * ndc;
+    for (int k = 0; k < ndc; ++k)
+      if (all[sigc[k]]) mark[rc[k]] = 1;
+  }
+  std::vector<int32_t> out;
+  for (int64_t i = 0; i < sc->ndof; ++i)
+    if (mark[i]) out.push_back((int32_t)i);
+  return out;
+}
+

@@ -173,6 +173,10 @@ fem_status fem_launch_apply_element_2d(const fem_form* f, int dtype, const void*
 fem_status fem_launch_diag_element_2d(const fem_form* f, double* ye, cudaStream_t s);
 fem_status fem_launch_rhs_element_2d(const fem_form* f, const double* fq, double* ye, cudaStream_t s);
 fem_status fem_launch_grad_2d(const fem_form* f, const double* u, double* g, cudaStream_t s);
+// p-multigrid coarse essential DOFs (host; fem_host.cpp): a coarse DOF is
+// essential iff every fine DOF of the same mesh entity is. essf: fine mask of
+// one component [sf->ndof]; returns coarse ids, ascending.
+std::vector<int32_t> fem_coarse_essential(const fem_space* sf, const uint8_t* essf, const fem_space* sc);
 // Make the form's geometry tables match its mesh's nodal order (no-op for
 // vertex-only meshes); synchronous.
 fem_status fem_form_geo_tables(const fem_form* f);

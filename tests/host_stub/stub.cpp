@@ -39,3 +39,13 @@ fem_status fem_apply_tables_init() { return no_device(); }
 fem_status fem_2d_tables_init() { return no_device(); }
 fem_status fem_elast_tables_init() { return no_device(); }
 int fem_kernels_supported(int, int) { return 0; }
+
+// Test entry to the p-multigrid coarse essential rule (a host function of the
+// library without a public ABI): returns the count and, if out is given,
+// writes the coarse ids.
+extern "C" int64_t test_coarse_essential(const fem_space* sf, const uint8_t* essf, const fem_space* sc,
+                                         int32_t* out) {
+  const std::vector<int32_t> v = fem_coarse_essential(sf, essf, sc);
+  if (out && !v.empty()) std::memcpy(out, v.data(), sizeof(int32_t) * v.size());
+  return (int64_t)v.size();
+}

@@ -168,3 +168,33 @@ def test_malformed_meshes_are_rejected(hostlib):
     assert L.fem_mesh_create(None, c.shape[0], h.ctypes.data, h.shape[0], C.byref(m)) == 1
     assert create(c, h) == 0                             # the valid mesh still builds
     L.fem_mesh_destroy(m)
+
+
+@pytest.mark.parametrize("pf,pc", [(2, 1), (4, 2), (5, 2), (8, 4)])
+def test_multigrid_coarse_essential_rule(hostlib, pf, pc):
+    """The library's p-multigrid coarse essential rule (coarse DOF essential
+    iff every fine DOF of its mesh entity is) against the oracle's, for the
+    whole boundary, one face and random masks."""
+    from oracle import multigrid as omg
+    L = hostlib
+    f = L.test_coarse_essential
+    f.restype, f.argtypes = C.c_int64, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    c, h = hex_lattice(3, 0.1, seed=9, shuffle=True)
+    m = _mesh(L, c, h, 3)
+    sf, nf, nbf, ne = _space(L, m, pf)
+    sc, nc, nbc, _ = _space(L, m, pc)
+    e2lf, bdrf = _tables(L, sf, ne, (pf + 1) ** 3, nbf)
+    e2lc, _ = _tables(L, sc, ne, (pc + 1) ** 3, nbc)
+    from oracle import assemble
+    X = assemble.Problem(c, h, pf, pf + 2).dof_coords()
+    rng = np.random.default_rng(pf * 10 + pc)
+    masks = [np.isin(np.arange(nf), bdrf), np.abs(X[:, 0]) < 1e-12, rng.random(nf) < 0.5, rng.random(nf) < 0.95]
+    for mask in masks:
+        mk = np.ascontiguousarray(mask.astype(np.uint8))
+        out = np.empty(nc, dtype=np.int32)
+        cnt = f(sf, mk.ctypes.data, sc, out.ctypes.data)
+        ref = np.nonzero(omg.coarse_essential(e2lf, pf, mask, e2lc, pc, nc))[0]
+        assert np.array_equal(out[:cnt], ref.astype(np.int32))
+    L.fem_space_destroy(sf)
+    L.fem_space_destroy(sc)
+    L.fem_mesh_destroy(m)
