@@ -198,3 +198,36 @@ def test_multigrid_coarse_essential_rule(hostlib, pf, pc):
     L.fem_space_destroy(sf)
     L.fem_space_destroy(sc)
     L.fem_mesh_destroy(m)
+
+
+def test_set_nodes_validation(hostlib):
+    L = hostlib
+    f = L.fem_mesh_set_nodes
+    f.restype, f.argtypes = C.c_int, [C.c_void_p, C.c_int, C.c_void_p]
+    c, h = hex_lattice(2, 0.1, seed=4)
+    m = _mesh(L, c, h, 3)
+    E = h.shape[0]
+    for k in (1, 2, 8):
+        nodes = np.zeros((E, (k + 1) ** 3, 3))
+        assert f(m, k, nodes.ctypes.data) == 0
+    assert f(m, 0, None) == 0                           # back to the vertex geometry
+    assert f(m, 9, np.zeros((E, 1000, 3)).ctypes.data) == 1
+    assert f(m, -1, None) == 1
+    assert f(m, 2, None) == 1
+    bad = np.zeros((E, 27, 3))
+    bad[3, 5, 1] = np.nan
+    assert f(m, 2, bad.ctypes.data) == 1
+    bad[3, 5, 1] = np.inf
+    assert f(m, 2, bad.ctypes.data) == 1
+    # spaces on a mesh with nodes: the numbering does not change
+    good = np.zeros((E, 27, 3))
+    assert f(m, 2, good.ctypes.data) == 0
+    s, ndof, nbdr, ne = _space(L, m, 2)
+    e2l, _ = _tables(L, s, ne, 27, nbdr)
+    assert np.array_equal(e2l, numbering.build(h, 2, nv=c.shape[0])["e2l"])
+    L.fem_space_destroy(s)
+    L.fem_mesh_destroy(m)
+    cq, q = quad_lattice(2, 0.0, seed=1)
+    m2 = _mesh(L, cq, q, 2)
+    assert f(m2, 2, good.ctypes.data) == 7                # hexahedral meshes only
+    L.fem_mesh_destroy(m2)
