@@ -121,3 +121,40 @@ def test_reproduces_a_quadratic_solution(p):
     Ac = osolve.constrain(ep.K, ess)
     uh = osolve.cholesky_solve(Ac, bc)
     assert np.abs(uh - uvec).max() <= 1e-11 * np.abs(uvec).max()
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_convergence_smooth_solution(p):
+    """Smooth manufactured displacement on an affinely mapped cube, constant
+    lambda and mu, Dirichlet data from u: the nodal error of the discrete
+    solution falls at about the rate h^(p+1) under uniform refinement."""
+    sympy = pytest.importorskip("sympy")
+    from oracle import solve as osolve
+    lam_v, mu_v = 2.0, 0.7
+    x, y, z = sympy.symbols("x y z")
+    X = (x, y, z)
+    u = [sympy.sin(x + 0.5 * y) * sympy.cos(z), sympy.exp(0.3 * x) * sympy.sin(y - z), x * y * z + sympy.cos(x - y)]
+    div = sum(sympy.diff(u[i], X[i]) for i in range(3))
+    f = [-((lam_v + mu_v) * sympy.diff(div, X[i]) + mu_v * sum(sympy.diff(u[i], X[j], 2) for j in range(3)))
+         for i in range(3)]
+    uf = [sympy.lambdify(X, ui, "numpy") for ui in u]
+    ff = [sympy.lambdify(X, fi, "numpy") for fi in f]
+    A = np.array([[1.0, 0.2, 0.0], [0.0, 1.1, -0.1], [0.1, 0.0, 0.9]])
+    errs = []
+    for N in (2, 4):
+        c, h = hex_lattice(N, 0.0, seed=1)
+        c = c @ A.T
+        E = h.shape[0]
+        ep = elasticity.ElasticityProblem(c, h, p, p + 2, np.full(E, lam_v), np.full(E, mu_v))
+        sc = assemble.Problem(c, h, p, p + 2)
+        Xd = sc.dof_coords()
+        n = sc.ndof
+        uex = np.concatenate([np.broadcast_to(uf[k](Xd[:, 0], Xd[:, 1], Xd[:, 2]), (n,)) for k in range(3)])
+        b = np.concatenate([sc.load(lambda Y, k=k: np.broadcast_to(ff[k](Y[..., 0], Y[..., 1], Y[..., 2]),
+                                                                   Y.shape[:-1])) for k in range(3)])
+        bd = sc.num["boundary_dofs"]
+        ess = np.concatenate([bd + k * n for k in range(3)])
+        uh = osolve.cholesky_solve(osolve.constrain(ep.K, ess), osolve.constrain_rhs(ep.K, b, ess, uex[ess]))
+        errs.append(np.abs(uh - uex).max())
+    rate = np.log2(errs[0] / errs[1])
+    assert rate > p + 0.6, (errs, rate)
