@@ -98,3 +98,29 @@ def test_hand_numbering_p3():
     assert at(0, 1) == 10 and at(0, 2) == 11
     assert at(1, 1) == 12 and at(2, 1) == 13 and at(1, 2) == 14 and at(2, 2) == 15
     assert num["ndof"] == 16 and len(num["boundary_dofs"]) == 12
+
+
+def test_stiffness_matches_the_papers_2d_setup_formula():
+    """The paper's 2D diffusion setup (Sec. 5.3, the PA setup listing) stores,
+    per point, c = alpha W / det J and the three symmetric entries
+    c (J12^2 + J22^2), -c (J12 J11 + J22 J21), c (J11^2 + J21^2) of
+    c adj(J) adj(J)^T, applied to reference gradients. The oracle's element
+    stiffness (built from J^-1, J^-T and det J) must equal the stiffness
+    assembled from those entries."""
+    from fem_inputs import lognormal, quad_lattice
+    from oracle import twod
+    c, q = quad_lattice(3, 0.15, seed=12, shuffle=True)
+    kap = lognormal(13, q.shape[0])
+    for p in (1, 2, 4):
+        ref = twod.Reference2(p, p + 2)
+        X = c[q.astype(np.int64)]
+        _, J, det, _ = twod.geometry2(ref, X)
+        J11, J12, J21, J22 = J[..., 0, 0], J[..., 0, 1], J[..., 1, 0], J[..., 1, 1]
+        cq = kap[:, None] * ref.w[None, :] / det
+        Y = np.empty(J.shape)
+        Y[..., 0, 0] = cq * (J12 ** 2 + J22 ** 2)
+        Y[..., 0, 1] = Y[..., 1, 0] = -cq * (J12 * J11 + J22 * J21)
+        Y[..., 1, 1] = cq * (J11 ** 2 + J21 ** 2)
+        K_listing = np.einsum("qai,eqab,qbj->eij", ref.dphi, Y, ref.dphi, optimize=True)
+        K = twod.stiffness2(ref, X, kap)
+        assert np.abs(K - K_listing).max() <= 1e-13 * np.abs(K).max()
