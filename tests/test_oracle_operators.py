@@ -220,3 +220,18 @@ def test_dof_coords_on_lattice():
     g = np.round(X * p * N)
     np.testing.assert_allclose(X * p * N, g, atol=1e-12)          # GLL p=2 nodes are uniform
     assert np.unique(g, axis=0).shape[0] == P.ndof
+
+
+def test_geometry_inverse_and_determinant():
+    """The oracle's cofactor J^-1 and det J against numpy's inverse and
+    determinant on perturbed, shuffled elements (J^-1 J = I, det J > 0)."""
+    from fem_inputs import hex_lattice
+    from oracle import element
+    c, h = hex_lattice(3, 0.15, seed=21, shuffle=True)
+    ref = element.Reference(2, 4)
+    _, J, det, Jinv = element.geometry(ref, c[h.astype(np.int64)])
+    np.testing.assert_allclose(det, np.linalg.det(J), rtol=1e-13)
+    np.testing.assert_allclose(Jinv, np.linalg.inv(J), rtol=1e-12, atol=1e-12 * np.abs(Jinv).max())
+    eye = np.einsum("eqab,eqbc->eqac", Jinv, J)
+    np.testing.assert_allclose(eye, np.broadcast_to(np.eye(3), eye.shape), atol=1e-13)
+    assert (det > 0).all()
