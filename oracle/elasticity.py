@@ -71,3 +71,33 @@ class ElasticityProblem:
 
     def apply(self, x):
         return self.K @ np.asarray(x, dtype=np.float64)
+
+
+def sampled_apply(coords, hexes, e2l, p, q, lam, mu, x, rows, ref=None):
+    """(K x)_r for the vector rows r = c * ndof + i in `rows` only, each from
+    the rows of the (at most 8) element matrices whose element holds DOF i
+    (component-major vectors). Needs only the element DOF lists, so it works
+    at sizes where no global matrix fits."""
+    coords = np.asarray(coords, dtype=np.float64)
+    hexes = np.asarray(hexes, dtype=np.int64)
+    ref = element.Reference(p, q) if ref is None else ref
+    lam = np.asarray(lam, dtype=np.float64)
+    mu = np.asarray(mu, dtype=np.float64)
+    ndof = int(e2l.max()) + 1
+    D = e2l.shape[1]
+    flat = e2l.ravel()
+    order = np.argsort(flat, kind="stable")
+    sorted_dofs = flat[order]
+    out = np.zeros(len(rows))
+    for r, vi in enumerate(np.asarray(rows, dtype=np.int64)):
+        c, i = divmod(int(vi), ndof)
+        lo = np.searchsorted(sorted_dofs, i, side="left")
+        hi = np.searchsorted(sorted_dofs, i, side="right")
+        acc = 0.0
+        for s in order[lo:hi]:
+            e, k = divmod(int(s), D)
+            Ke = stiffness(ref, coords[hexes[e:e + 1]], lam[e:e + 1], mu[e:e + 1])[0]
+            xe = np.concatenate([x[d * ndof + e2l[e]] for d in range(3)])
+            acc += Ke[c * D + k] @ xe
+        out[r] = acc
+    return out

@@ -268,3 +268,38 @@ def test_deterministic():
     i1 = mg.solve(bc, u1, rtol=1e-10)
     i2 = mg.solve(bc, u2, rtol=1e-10)
     assert i1["iterations"] == i2["iterations"] and torch.equal(u1, u2)
+
+
+def test_sampled_rows_at_bench_size():
+    """The elasticity bench configuration (p = 4, q = 6, 28^3 hexes perturbed
+    0.15h, 4.3M vector DOFs, the bench's seeds): sampled rows of the FP64,
+    double-float and FP32 applies against the oracle's row-by-row apply."""
+    import torch
+    import paper_1911_09220_gb300 as F
+    from fem_inputs import hex_lattice
+    from oracle import numbering
+    p, N = 4, 28
+    c, h = hex_lattice(N, 0.15, seed=60 + p)
+    E = h.shape[0]
+    lam, mu = lognormal(70 + p, E), lognormal(80 + p, E)
+    space = F.Space(F.Mesh(c, h), p)
+    form = F.Form.elasticity(space, cuda(lam), cuda(mu), q1d=p + 2)
+    num = numbering.build(h, p, nv=c.shape[0])
+    assert num["ndof"] == space.ndof
+    x = x_uniform(90 + p, form.n)
+    rng = np.random.default_rng(7)
+    bd = np.asarray(num["boundary_dofs"])
+    rows = np.unique(np.concatenate([rng.integers(0, form.n, 30),
+                                     rng.choice(bd, 6, replace=False) + space.ndof * rng.integers(0, 3, 6)]))
+    ref = oel.sampled_apply(c, h, num["e2l"], p, p + 2, lam, mu, x, rows)
+    scale = np.abs(ref).max()
+    rt = torch.as_tensor(rows, device="cuda")
+    xd = cuda(x)
+    y = torch.empty_like(xd)
+    form.apply(xd, y)
+    assert np.abs(y[rt].cpu().numpy() - ref).max() <= TOL * scale
+    form.apply(xd, y, arith="df64")
+    assert np.abs(y[rt].cpu().numpy() - ref).max() <= TOL * scale
+    y32 = torch.empty(form.n, dtype=torch.float32, device="cuda")
+    form.apply(xd.float(), y32)
+    assert np.abs(y32[rt].double().cpu().numpy() - ref).max() <= 2e-5 * scale

@@ -158,3 +158,16 @@ def test_convergence_smooth_solution(p):
         errs.append(np.abs(uh - uex).max())
     rate = np.log2(errs[0] / errs[1])
     assert rate > p + 0.6, (errs, rate)
+
+
+def test_sampled_apply_matches_assembled():
+    from fem_inputs import x_uniform
+    c, h = hex_lattice(3, 0.15, seed=31, shuffle=True)
+    E = h.shape[0]
+    lam, mu = lognormal(32, E), lognormal(33, E)
+    ep = elasticity.ElasticityProblem(c, h, 2, 4, lam, mu)
+    x = x_uniform(34, 3 * ep.ndof)
+    rows = np.unique(np.random.default_rng(3).integers(0, 3 * ep.ndof, 40))
+    ref = (ep.K @ x)[rows]
+    got = elasticity.sampled_apply(c, h, ep.e2l, 2, 4, lam, mu, x, rows)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ep.K @ x).max()
