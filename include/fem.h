@@ -237,15 +237,27 @@ fem_status fem_scatter(const fem_form* form, int dtype, const void* ye, void* y,
  * scratch buffer -- e.g. an application whose own pool has reserved nearly
  * all GPU memory, or a latency-critical loop where a cudaMalloc (which can
  * synchronise the device and can fail) is not acceptable.
+ * Which fem_apply calls allocate: a constrained call (its zeroed-input work
+ * vector, on first use or growth) and the first FP32 or double-float call
+ * on a form (the form's converted copy of D). An unconstrained FP64
+ * fem_apply reuses the E-vector buffer allocated when the form was created
+ * and allocates nothing either; this entry point guarantees that by
+ * construction and does not touch the form's E-vector buffer.
  * The E-vector scratch is a fixed library-owned device array of 4,194,304
  * doubles (32 MiB), held on every GPU that loads the library until the
- * process exits. Limit: ne * (p+1)^3 <= 4,194,304 (three times that for
- * elasticity), else FEM_EINVAL (use fem_apply). x, y: device float64 [ndof], caller-owned, not aliased.
+ * process exits, in addition to every form's own E-vector buffer.
+ * Limit: vdim * ne * nd <= 4,194,304 entries, with nd = (p+1)^3 on a
+ * hexahedral mesh and (p+1)^2 on a quadrilateral one, and vdim = 3 for
+ * elasticity (1 otherwise), else FEM_EINVAL (use fem_apply).
+ * x, y: device float64 [vdim * ndof], caller-owned, not aliased.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress with that device current); make that first call
- * before any stream capture. Every call shares the one array: calls that
- * overlap on the GPU (other streams or threads) race. The element kernel
- * rewrites every scratch entry the scatter reads, so nothing is cleared. */
+ * (cudaGetSymbolAddress with that device current) and caches it for the
+ * process: the cached address belongs to the device's primary context, so
+ * it is stale after a cudaDeviceReset or under another context on that
+ * device. Make that first call before any stream capture. Every call
+ * shares the one array: calls that overlap on the GPU (other streams or
+ * threads) race. The element kernel rewrites every scratch entry the
+ * scatter reads, so nothing is cleared. */
 fem_status fem_apply_noalloc(const fem_form* form, const double* x, double* y,
                              void* stream);
 
@@ -440,6 +452,19 @@ fem_status fem_mg_restrict(fem_mg* mg, int level, const double* rf, double* rc, 
  * FEM_EBREAKDOWN. */
 fem_status fem_mg_solve(fem_mg* mg, const double* b, double* x, const fem_solve_opts* opts,
                         fem_solve_info* info, void* stream);
+
+/* ---- arithmetic-peak probe (the paper has no counterpart) ---------------
+ * Measures the fused multiply-add rate of the current device in the given
+ * arithmetic: one kernel on every SM at full occupancy, eight independent
+ * FMA chains per thread, `iters` steps per chain, timed with CUDA events on
+ * `stream` (best of three after one warm-up launch). *tflops receives
+ * 2 * chains * iters * threads / seconds / 1e12 (an FMA counts two flops).
+ * These are the denominators of the roofline fractions of the kernels bound
+ * by their arithmetic pipe (the FP64 element kernels; double-float and FP32
+ * run on the FP32 pipe). dtype: FEM_F64 or FEM_F32. Synchronises `stream`.
+ * A run of about 20 ms: iters ~ 5,000 (FP64), ~ 300,000 (FP32) on GB300.
+ * Errors: FEM_EINVAL (dtype, iters <= 0, NULL tflops), FEM_ECUDA. */
+fem_status fem_probe_fma_peak(int dtype, int iters, double* tflops, void* stream);
 
 #ifdef __cplusplus
 }

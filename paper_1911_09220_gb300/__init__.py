@@ -40,6 +40,17 @@ def supported(p, q1d):
     return bool(B.lib().fem_supported(int(p), int(q1d)))
 
 
+def probe_fma_peak(dtype="f64", iters=None, stream=None):
+    """Measured FMA rate (TFLOP/s) of the current device in FP64 or FP32
+    (fem_probe_fma_peak); about 20 ms of device time by default."""
+    code = FEM_F64 if dtype == "f64" else FEM_F32
+    if iters is None:
+        iters = 5000 if dtype == "f64" else 300000
+    out = C.c_double()
+    B.check(B.lib().fem_probe_fma_peak(code, int(iters), C.byref(out), _stream(stream)))
+    return out.value
+
+
 def _stream(stream=None):
     """cudaStream_t of a torch.cuda.Stream, a raw handle, or the current stream."""
     if stream is not None:

@@ -99,6 +99,7 @@ SIGNATURES = {
     "fem_mg_prolong": (I, [P, I, P, P, P]),
     "fem_mg_restrict": (I, [P, I, P, P, P]),
     "fem_mg_solve": (I, [P, P, P, C.POINTER(SolveOpts), C.POINTER(SolveInfo), P]),
+    "fem_probe_fma_peak": (I, [I, I, C.POINTER(C.c_double), P]),
 }
 
 _lib = None

@@ -120,7 +120,7 @@ struct fem_form {
   int geo_k = 0;
 };
 
-// Length of the form's vectors: vdim * ndof (component-major).
+// Length of the form's vectors: vdim * ndof (component-major).// Length of the form's vectors: vdim * ndof (component-major).
 inline int64_t fem_form_len(const fem_form* f) { return (int64_t)f->vdim * f->space->ndof; }
 
 // ---------------------------------------------------------------- basis -----

@@ -19,14 +19,6 @@ fem_status prepare_smem(K kernel, size_t bytes) {
   return FEM_OK;
 }
 
-// Whether the block stages its D tile through shared memory with a bulk
-// copy (cp.async.bulk + mbarrier) instead of prefetching it to L2. Measured
-// on GB300 (p = 4, 20.3M DOFs) the staged FP32 kernel was slower (0.586 vs
-// 0.519 ms: the tile cuts residency from 4 to 3 blocks per SM while the
-// dependent x gather stays exposed), so every type uses the L2 prefetch.
-template <typename T>
-constexpr bool stages_D() { return false; }
-
 template <typename T, int P, int Q, typename TX = T>
 fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G, const TX* x, TX* ye,
                            const int* skip, cudaStream_t s) {
@@ -34,25 +26,21 @@ fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G
   const int ne = (int)f->space->ne;
   const dim3 block(Q, Q, NE);
   const int grid = (ne + NE - 1) / NE;
-  constexpr bool ST = stages_D<T>();
   (void)B;
   (void)G;
-  int* err = f->d_flag + 3;
+  const size_t bytes = BlockSmem<T, D1, Q, NE>::bytes;
   if (f->kind == FEM_CONVECTION) {
-    const size_t bytes = BlockSmem<T, D1, Q, NE, 3, false>::bytes;
     auto kern = k_convection_apply<T, D1, Q, NE, TX>;
     FEM_TRY(prepare_smem(kern, bytes));
     kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, x, ye);
   } else if (f->kind == FEM_DIFFUSION) {
-    const size_t bytes = BlockSmem<T, D1, Q, NE, 6, ST>::bytes;
-    auto kern = k_diffusion_apply<T, D1, Q, NE, TX, ST>;
+    auto kern = k_diffusion_apply<T, D1, Q, NE, TX>;
     FEM_TRY(prepare_smem(kern, bytes));
-    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, x, ye, err);
+    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, x, ye);
   } else {
-    const size_t bytes = BlockSmem<T, D1, Q, NE, 1, ST>::bytes;
-    auto kern = k_mass_apply<T, D1, Q, NE, TX, ST>;
+    auto kern = k_mass_apply<T, D1, Q, NE, TX>;
     FEM_TRY(prepare_smem(kern, bytes));
-    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, x, ye, err);
+    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, x, ye);
   }
   FEM_LAUNCHED();
   return FEM_OK;
@@ -74,7 +62,8 @@ __global__ void k_scatter(const int* __restrict__ skip, int64_t ndof, const int3
   constexpr int kU = 4;
   __shared__ double red[32];
   if (skip && *skip) return;
-  double acc = 0.0;
+  using A = typename DotAcc<T>::type;
+  A acc = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t n = VD * ndof;
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < n; base += stride * kU) {
@@ -113,12 +102,12 @@ __global__ void k_scatter(const int* __restrict__ skip, int64_t ndof, const int3
         T v = sum[u];
         if (mask && mask[i]) v = xin[i];
         y[i] = v;
-        if (pdot) acc += (double)xin[i] * (double)v;
+        if (pdot) acc += (A)xin[i] * (A)v;
       }
     }
   }
   if (pdot) {
-    const double tot = block_sum(acc, red);
+    const double tot = block_sum((double)acc, red);
     if (threadIdx.x == 0) pdot[blockIdx.x] = tot;
   }
 }
@@ -171,7 +160,7 @@ fem_status fem_form_ensure_f32(const fem_form* fc, cudaStream_t s) {
   fem_form* f = const_cast<fem_form*>(fc);
   if (f->d_D32) return FEM_OK;
   const size_t n = (size_t)f->space->ne * f->ncomp * f->nq;
-  FEM_TRY(dev_alloc(&f->d_D32, n + 4));  // +16 bytes: bulk copies of the last tile round up
+  FEM_TRY(dev_alloc(&f->d_D32, n + 4));  // 16 bytes of tail padding
   k_to_f32<<<grid_for((int64_t)n, 256), 256, 0, s>>>((int64_t)n, f->d_D, f->d_D32);
   FEM_LAUNCHED();
   return FEM_OK;

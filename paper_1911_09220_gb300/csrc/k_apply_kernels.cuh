@@ -31,82 +31,46 @@ constexpr int ne_for(int Q) {
   return (Q == 3 || Q == 5 || Q == 8) ? ne_small(Q) : ne_large(Q);  // double-float
 }
 
-// Shared-memory plan of a block: NE element slabs, then (STAGE) the staged D
-// tile of the block's elements (+16 bytes for the alignment shift), then the
-// mbarrier.
-template <typename T, int D1, int Q, int NE, int NCOMP, bool STAGE>
+// Shared-memory plan of a block: NE element slabs.
+template <typename T, int D1, int Q, int NE>
 struct BlockSmem {
-  static constexpr size_t slabs = (sizeof(T) * NE * ElemSmem<T, D1, Q>::SE + 15) / 16 * 16;
-  static constexpr size_t tile = STAGE ? (sizeof(T) * NE * NCOMP * Q * Q * Q + 16 + 15) / 16 * 16 : 0;
-  static constexpr size_t bytes = slabs + tile + (STAGE ? 16 : 0);
+  static constexpr size_t bytes = (sizeof(T) * NE * ElemSmem<T, D1, Q>::SE + 15) / 16 * 16;
 };
 
-// Issue the bulk copy of the block's D tile (elements e0 .. e0+nel-1) and
-// return where element 0 of the tile lands in shared memory. The source is
-// rounded down to 16 bytes (the array is padded by 16 bytes at the end).
-template <typename T, int NCOMP, int NQ>
-__device__ __forceinline__ const T* stage_tile(unsigned char* tile, uint64_t* bar, const T* Dq, int e0, int nel,
-                                               bool issuer) {
-  const uintptr_t src = reinterpret_cast<uintptr_t>(Dq + (size_t)e0 * NCOMP * NQ);
-  const uintptr_t src_al = src & ~(uintptr_t)15;
-  const unsigned shift = (unsigned)(src - src_al);
-  if (issuer) {
-    const unsigned bytes = (unsigned)(sizeof(T) * (size_t)nel * NCOMP * NQ);
-    const unsigned total = (bytes + shift + 15u) & ~15u;
-    stage_issue(bar, tile, reinterpret_cast<const void*>(src_al), total);
-  }
-  return reinterpret_cast<const T*>(tile + shift);
-}
-
-template <typename T, int D1, int Q, int NE, typename TX, bool STAGE>
+// The block's D range (its elements are consecutive, so the range is one
+// contiguous run) is read in stage S3; thread 0 asks the L2 for it at the
+// start with one bulk prefetch, so the fetch overlaps the gather and the
+// first two contraction stages. (Staging the range into shared memory with a
+// bulk copy instead measured slower: the tile lowered the resident blocks
+// per SM while the dependent map -> x gather stayed exposed.)
+template <typename T, int D1, int Q, int NE, typename TX>
 __global__ void __launch_bounds__(Q * Q * NE)
 k_diffusion_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
-                  const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye, int* __restrict__ err) {
+                  const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye) {
   constexpr int NQ = Q * Q * Q;
-  using BS = BlockSmem<T, D1, Q, NE, 6, STAGE>;
   if (skip && *skip) return;  // a captured solver iteration after convergence
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x + Q * (threadIdx.y + Q * threadIdx.z);
   const int e0 = blockIdx.x * NE;
   const int nel = min(NE, ne - e0);
-  if constexpr (STAGE) {
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + BS::slabs + BS::tile);
-    const bool issuer = tid == 0;
-    if (issuer) stage_init(bar);
-    __syncthreads();
-    const T* tileD = stage_tile<T, 6, NQ>(smem_raw + BS::slabs, bar, Dq, e0, nel, issuer);
-    diffusion_block<T, D1, Q, TX, true>(tid, e0, nel, e2l, tileD, sm, x, ye, bar, err);
-  } else {
-    if (tid == 0)  // D of the block's elements: read in stage S3, fetch into L2 now
-      l2_prefetch_range(Dq + (size_t)e0 * 6 * NQ, sizeof(T) * (size_t)nel * 6 * NQ);
-    diffusion_block<T, D1, Q, TX>(tid, e0, nel, e2l, Dq, sm, x, ye);
-  }
+  if (tid == 0) l2_prefetch_range(Dq + (size_t)e0 * 6 * NQ, sizeof(T) * (size_t)nel * 6 * NQ);
+  diffusion_block<T, D1, Q, TX>(tid, e0, nel, e2l, Dq, sm, x, ye);
 }
 
-template <typename T, int D1, int Q, int NE, typename TX, bool STAGE>
+template <typename T, int D1, int Q, int NE, typename TX>
 __global__ void __launch_bounds__(Q * Q * NE)
 k_mass_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
-             const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye, int* __restrict__ err) {
+             const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye) {
   constexpr int NQ = Q * Q * Q;
-  using BS = BlockSmem<T, D1, Q, NE, 1, STAGE>;
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x + Q * (threadIdx.y + Q * threadIdx.z);
   const int e0 = blockIdx.x * NE;
   const int nel = min(NE, ne - e0);
-  if constexpr (STAGE) {
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + BS::slabs + BS::tile);
-    const bool issuer = tid == 0;
-    if (issuer) stage_init(bar);
-    __syncthreads();
-    const T* tileD = stage_tile<T, 1, NQ>(smem_raw + BS::slabs, bar, Dq, e0, nel, issuer);
-    mass_block<T, D1, Q, TX, true>(tid, e0, nel, e2l, tileD, sm, x, ye, bar, err);
-  } else {
-    if (tid == 0) l2_prefetch_range(Dq + (size_t)e0 * NQ, sizeof(T) * (size_t)nel * NQ);
-    mass_block<T, D1, Q, TX>(tid, e0, nel, e2l, Dq, sm, x, ye);
-  }
+  if (tid == 0) l2_prefetch_range(Dq + (size_t)e0 * NQ, sizeof(T) * (size_t)nel * NQ);
+  mass_block<T, D1, Q, TX>(tid, e0, nel, e2l, Dq, sm, x, ye);
 }
 
 template <typename T, int D1, int Q, int NE, typename TX>

@@ -127,17 +127,18 @@ k_batch_scatter(const BProb* __restrict__ probs, const VItem* __restrict__ items
       if (done && done[P.sys0 + r]) continue;
       const T* ye = YE + P.yeoff + (int64_t)r * P.ne * P.nd;
       const int64_t xo = P.xoff + (int64_t)r * P.ndof;
-      double acc = 0.0;
+      using A = typename DotAcc<T>::type;
+      A acc = 0;
       for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const int32_t a = P.off[i], b = P.off[i + 1];
         T s = 0;
         for (int32_t k = a; k < b; ++k) s += ye[P.idx[k]];
         if (constrained && P.mask && P.mask[i]) s = Xin[xo + i];
         Y[xo + i] = s;
-        if (part) acc += (double)Xin[xo + i] * (double)s;
+        if (part) acc += (A)Xin[xo + i] * (A)s;
       }
       if (part) {
-        const double tot = block_sum(acc, red);
+        const double tot = block_sum((double)acc, red);
         if (threadIdx.x == 0) part[P.poff + (int64_t)r * P.nchunks + v.chunk] = tot;
       }
     }
@@ -188,20 +189,22 @@ k_bcg_init(const BProb* __restrict__ probs, const VItem* __restrict__ items, int
     for (int r = 0; r < nrhs; ++r) {
       if (done && done[P.sys0 + r]) continue;
       const int64_t xo = P.xoff + (int64_t)r * P.ndof;
-      double rz = 0, rr = 0, bb = 0;
+      using A = typename DotAcc<T>::type;
+      A rz = 0, rr = 0;
+      double bb = 0;
       for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const T ri = R[xo + i];
         const T zi = ri / diag[i];
         Z[xo + i] = zi;
         Pv[xo + i] = zi;
-        rz += (double)ri * (double)zi;
-        rr += (double)ri * (double)ri;
+        rz += (A)ri * (A)zi;
+        rr += (A)ri * (A)ri;
         if (Bv) bb += Bv[xo + i] * Bv[xo + i];
       }
       const int64_t slot = P.poff + (int64_t)r * P.nchunks + v.chunk;
-      double s = block_sum(rz, red);
+      double s = block_sum((double)rz, red);
       if (threadIdx.x == 0) part[slot] = s;
-      s = block_sum(rr, red);
+      s = block_sum((double)rr, red);
       if (threadIdx.x == 0) part[pstride + slot] = s;
       s = block_sum(bb, red);
       if (threadIdx.x == 0) part[2 * pstride + slot] = s;
@@ -273,20 +276,21 @@ k_bcg_update(const BProb* __restrict__ probs, const VItem* __restrict__ items, i
       if (sc.done[s]) continue;
       const T a = (T)sc.alpha[s];
       const int64_t xo = P.xoff + (int64_t)r * P.ndof;
-      double rz = 0, rr = 0;
+      using A = typename DotAcc<T>::type;
+      A rz = 0, rr = 0;
       for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         X[xo + i] += a * Pv[xo + i];
         const T ri = R[xo + i] - a * Qv[xo + i];
         R[xo + i] = ri;
         const T zi = ri / diag[i];
         Z[xo + i] = zi;
-        rz += (double)ri * (double)zi;
-        rr += (double)ri * (double)ri;
+        rz += (A)ri * (A)zi;
+        rr += (A)ri * (A)ri;
       }
       const int64_t slot = P.poff + (int64_t)r * P.nchunks + v.chunk;
-      double t = block_sum(rz, red);
+      double t = block_sum((double)rz, red);
       if (threadIdx.x == 0) part[pstride + slot] = t;
-      t = block_sum(rr, red);
+      t = block_sum((double)rr, red);
       if (threadIdx.x == 0) part[2 * pstride + slot] = t;
     }
   }

@@ -34,6 +34,20 @@ __device__ inline double block_sum(double v, double* red) {
   return s;
 }
 
+// Per-thread accumulator of a dot product over vectors of type T. A thread
+// sums a few tens of terms before the FP64 block and grid sums; FP32 vectors
+// accumulate those terms in FP32 on the FP32 pipe (converting every term to
+// FP64 put two conversions and a DFMA per term on the FP64 pipe, which then
+// bound the FP32 solver's vector kernels), FP64 vectors in FP64.
+template <typename T>
+struct DotAcc {
+  using type = double;
+};
+template <>
+struct DotAcc<float> {
+  using type = float;
+};
+
 // Compiled (p, q1d) set: q1d = p + 2 (the Gauss rule of the benchmark
 // workloads) and q1d = p + 1, for p = 1..8.
 #define FEM_FOR_EACH_PQ(X) \

@@ -86,69 +86,34 @@ __device__ __forceinline__ void eo_line(const T* x, T* y) {
   eo_apply<T, M, K, S, OFF>(e, o, y);
 }
 
-// D read from shared memory (a staged tile) or from global memory.
-template <bool DS>
-__device__ __forceinline__ double d_load(const double* p) {
-  if constexpr (DS) return *p;
-  else return fe_ldg(p);
-}
-template <bool DS>
-__device__ __forceinline__ float d_load(const float* p) {
-  if constexpr (DS) return *p;
-  else return fe_ldg(p);
-}
-template <bool DS>
-__device__ __forceinline__ df64 d_load(const df64* p) {
-  if constexpr (DS) return *p;
-  else return fe_ldg(p);
-}
-
 // The six D components of one point (point-major layout, 16-byte aligned
 // for double and df64 records of 48 bytes, 8-byte aligned for float records
 // of 24 bytes): three vector loads instead of six scalar ones.
-template <bool DS>
 __device__ __forceinline__ void d_load6(const double* p, double* d) {
-  if constexpr (DS) {
+  const double2* v = reinterpret_cast<const double2*>(p);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) d[c] = p[c];
-  } else {
-    const double2* v = reinterpret_cast<const double2*>(p);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const double2 w = __ldg(v + k);
-      d[2 * k] = w.x;
-      d[2 * k + 1] = w.y;
-    }
+  for (int k = 0; k < 3; ++k) {
+    const double2 w = __ldg(v + k);
+    d[2 * k] = w.x;
+    d[2 * k + 1] = w.y;
   }
 }
-template <bool DS>
 __device__ __forceinline__ void d_load6(const float* p, float* d) {
-  if constexpr (DS) {
+  const float2* v = reinterpret_cast<const float2*>(p);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) d[c] = p[c];
-  } else {
-    const float2* v = reinterpret_cast<const float2*>(p);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float2 w = __ldg(v + k);
-      d[2 * k] = w.x;
-      d[2 * k + 1] = w.y;
-    }
+  for (int k = 0; k < 3; ++k) {
+    const float2 w = __ldg(v + k);
+    d[2 * k] = w.x;
+    d[2 * k + 1] = w.y;
   }
 }
-template <bool DS>
 __device__ __forceinline__ void d_load6(const df64* p, df64* d) {
-  if constexpr (DS) {
+  const float4* v = reinterpret_cast<const float4*>(p);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) d[c] = p[c];
-  } else {
-    const float4* v = reinterpret_cast<const float4*>(p);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float4 w = __ldg(v + k);
-      d[2 * k] = df64(w.x, w.y);
-      d[2 * k + 1] = df64(w.z, w.w);
-    }
+  for (int k = 0; k < 3; ++k) {
+    const float4 w = __ldg(v + k);
+    d[2 * k] = df64(w.x, w.y);
+    d[2 * k + 1] = df64(w.z, w.w);
   }
 }
 
@@ -183,45 +148,6 @@ __device__ __forceinline__ void d_load12(const df64* p, df64* d) {
     d[2 * k] = df64(w.x, w.y);
     d[2 * k + 1] = df64(w.z, w.w);
   }
-}
-
-// ------------------------------------------------ staged D (bulk copy) ----
-// One thread of the block copies the block's contiguous D tile from global
-// to shared memory with a single cp.async.bulk whose completion is counted on
-// an mbarrier (transaction bytes); every thread later waits on the barrier's
-// phase 0 before reading the tile. The wait is bounded: after `limit`
-// unsuccessful polls the block records the failure in *err and goes on (its
-// results are then wrong and the caller reports the flag), so no thread can
-// spin forever.
-__device__ __forceinline__ void stage_init(uint64_t* bar) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// src, dst 16-byte aligned; bytes a multiple of 16.
-__device__ __forceinline__ void stage_issue(uint64_t* bar, void* dst, const void* src, unsigned bytes) {
-  const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
-               "l"(src), "r"(bytes), "r"(b)
-               : "memory");
-}
-
-__device__ __forceinline__ void stage_wait(uint64_t* bar, int* err) {
-  const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
-  const unsigned limit = 1u << 22;
-  for (unsigned it = 0; it < limit; ++it) {
-    unsigned ok = 0;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(b)
-        : "memory");
-    if (ok) return;
-  }
-  if (err) atomicOr(err, 1);
 }
 
 // Gather the element's DOF values x[map[k]] into the padded X rows: each
@@ -429,9 +355,7 @@ struct Lines {
   }
   // S3: line t = (qy, qx) along z, D at every point, back along z; results
   // stay in registers until phase A is dead
-  template <bool DS>
-  __device__ static void d3(int t, bool valid, const T* __restrict__ De, T* s, T* t0, T* t1, T* t2, uint64_t* bar,
-                            int* err) {
+  __device__ static void d3(int t, bool valid, const T* __restrict__ De, T* s, T* t0, T* t1, T* t2) {
     const int qy = t / Q, qx = t % Q;
     T rbb[D1], rgb[D1], rbg[D1], g0[Q], g1[Q], g2[Q];
     const T *sbb = BB(s) + qy * RC + qx, *sgb = GB(s) + qy * RC + qx, *sbg = BG(s) + qy * RC + qx;
@@ -444,13 +368,12 @@ struct Lines {
     eo_line<T, Q, D1, 1, BF>(rgb, g0);
     eo_line<T, Q, D1, 1, BF>(rbg, g1);
     eo_line<T, Q, D1, -1, GF>(rbb, g2);
-    if (DS) stage_wait(bar, err);
     const T* Dp = De + (size_t)t * 6;  // point-major: [q][6]
 #pragma unroll
     for (int qz = 0; qz < Q; ++qz) {
       T dd[6];
       if (valid) {
-        d_load6<DS>(Dp + (size_t)qz * QQ * 6, dd);
+        d_load6(Dp + (size_t)qz * QQ * 6, dd);
       } else {
 #pragma unroll
         for (int c = 0; c < 6; ++c) dd[c] = 0;
@@ -515,7 +438,6 @@ struct Lines {
   // ---- convection: the diffusion forward stages (d1, d2), then one value
   // per point v = D_q . gradhat (D_q = w adj(J) beta, point-major [q][3]),
   // then the mass backward stages (m3_store, m4, m5)
-  template <bool DS>
   __device__ static void c3(int t, bool valid, const T* __restrict__ De, T* s, T* t0) {
     const int qy = t / Q, qx = t % Q;
     T rbb[D1], rgb[D1], rbg[D1], g0[Q], g1[Q], g2[Q];
@@ -535,7 +457,7 @@ struct Lines {
       T v = 0;
       if (valid) {
         const T* d = Dp + (size_t)qz * QQ * 3;
-        v = fe_norm(d_load<DS>(d) * g0[qz] + d_load<DS>(d + 1) * g1[qz] + d_load<DS>(d + 2) * g2[qz]);
+        v = fe_norm(fe_ldg(d) * g0[qz] + fe_ldg(d + 1) * g1[qz] + fe_ldg(d + 2) * g2[qz]);
       }
       g0[qz] = v;
     }
@@ -627,17 +549,15 @@ struct Lines {
 #pragma unroll
     for (int qy = 0; qy < Q; ++qy) o[qy * RC + t] = bb[qy];
   }
-  template <bool DS>
-  __device__ static void m3(int t, bool valid, const T* __restrict__ De, T* s, T* t0, uint64_t* bar, int* err) {
+  __device__ static void m3(int t, bool valid, const T* __restrict__ De, T* s, T* t0) {
     const int qy = t / Q, qx = t % Q;
     T rbb[D1], u[Q];
     const T* sbb = BB(s) + qy * RC + qx;
 #pragma unroll
     for (int z = 0; z < D1; ++z) rbb[z] = sbb[z * Q];
     eo_line<T, Q, D1, 1, BF>(rbb, u);
-    if (DS) stage_wait(bar, err);
 #pragma unroll
-    for (int qz = 0; qz < Q; ++qz) u[qz] = valid ? fe_norm(d_load<DS>(De + t + qz * QQ) * u[qz]) : T(0);
+    for (int qz = 0; qz < Q; ++qz) u[qz] = valid ? fe_norm(fe_ldg(De + t + qz * QQ) * u[qz]) : T(0);
     eo_line<T, D1, Q, 1, BT>(u, t0);
   }
   __device__ static void m3_store(int t, T* s, const T* t0) {
@@ -677,14 +597,13 @@ struct Lines {
 // fewer lines (S1, S5: D1^2; S2, S4: D1*Q) pack the lines of the nel
 // elements onto the lowest thread ids, so warps are full and the arithmetic
 // pipe issues no instructions for idle lanes. Element e's DOF list is
-// e2l + e*D1^3, its D block Dq + e*NC*Q^3 (NC = 6 diffusion, 1 mass; with
-// DS, Dq is the block's staged tile and element el's block starts at
-// el*NC*Q^3), its E-vector slice ye + e*D1^3; its slab sm + el*SE. Every
-// thread of the block must call the driver (it contains __syncthreads).
-template <typename T, int D1, int Q, typename TX = T, bool DS = false>
+// e2l + e*D1^3, its D block Dq + e*NC*Q^3 (NC = 6 diffusion, 1 mass), its
+// E-vector slice ye + e*D1^3; its slab sm + el*SE. Every thread of the block
+// must call the driver (it contains __syncthreads).
+template <typename T, int D1, int Q, typename TX = T>
 __device__ __forceinline__ void diffusion_block(int tid, int e0, int nel, const int32_t* __restrict__ e2l,
                                                 const T* __restrict__ Dq, T* sm, const TX* __restrict__ x,
-                                                TX* __restrict__ ye, uint64_t* bar = nullptr, int* err = nullptr) {
+                                                TX* __restrict__ ye) {
   using Ln = Lines<T, D1, Q>;
   constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
   constexpr int N1 = D1 * D1, N2 = D1 * Q;
@@ -698,8 +617,7 @@ __device__ __forceinline__ void diffusion_block(int tid, int e0, int nel, const 
   if (tid < nel * N2) Ln::d2(tid % N2, sm + (tid / N2) * SE);
   __syncthreads();
   T t0[D1], t1[D1], t2[D1];
-  const T* De = DS ? Dq + (size_t)el * 6 * NQ : Dq + ev * 6 * NQ;
-  Ln::template d3<DS>(t, valid, De, sm + el * SE, t0, t1, t2, bar, err);
+  Ln::d3(t, valid, Dq + ev * 6 * NQ, sm + el * SE, t0, t1, t2);
   __syncthreads();
   Ln::d3_store(t, sm + el * SE, t0, t1, t2);
   __syncthreads();
@@ -727,7 +645,7 @@ __device__ __forceinline__ void convection_block(int tid, int e0, int nel, const
   if (tid < nel * N2) Ln::d2(tid % N2, sm + (tid / N2) * SE);
   __syncthreads();
   T t0[D1];
-  Ln::template c3<false>(t, valid, Dq + ev * 3 * NQ, sm + el * SE, t0);
+  Ln::c3(t, valid, Dq + ev * 3 * NQ, sm + el * SE, t0);
   __syncthreads();
   Ln::m3_store(t, sm + el * SE, t0);
   __syncthreads();
@@ -736,10 +654,10 @@ __device__ __forceinline__ void convection_block(int tid, int e0, int nel, const
   if (tid < nel * N1) Ln::template m5<TX>(tid % N1, sm + (tid / N1) * SE, ye + (size_t)(e0 + tid / N1) * ND);
 }
 
-template <typename T, int D1, int Q, typename TX = T, bool DS = false>
+template <typename T, int D1, int Q, typename TX = T>
 __device__ __forceinline__ void mass_block(int tid, int e0, int nel, const int32_t* __restrict__ e2l,
                                            const T* __restrict__ Dq, T* sm, const TX* __restrict__ x,
-                                           TX* __restrict__ ye, uint64_t* bar = nullptr, int* err = nullptr) {
+                                           TX* __restrict__ ye) {
   using Ln = Lines<T, D1, Q>;
   constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
   constexpr int N1 = D1 * D1, N2 = D1 * Q;
@@ -753,8 +671,7 @@ __device__ __forceinline__ void mass_block(int tid, int e0, int nel, const int32
   if (tid < nel * N2) Ln::m2(tid % N2, sm + (tid / N2) * SE);
   __syncthreads();
   T t0[D1];
-  const T* De = DS ? Dq + (size_t)el * NQ : Dq + ev * NQ;
-  Ln::template m3<DS>(t, valid, De, sm + el * SE, t0, bar, err);
+  Ln::m3(t, valid, Dq + ev * NQ, sm + el * SE, t0);
   __syncthreads();
   Ln::m3_store(t, sm + el * SE, t0);
   __syncthreads();

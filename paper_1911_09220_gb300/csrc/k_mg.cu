@@ -258,7 +258,8 @@ __global__ void k_cc_init(int64_t n, const T* __restrict__ rin, const T* __restr
     if (blockIdx.x == 0 && threadIdx.x == 0) *stop = 1;
     return;
   }
-  double rz = 0;
+  using A = typename DotAcc<T>::type;
+  A rz = 0;
   GRID_LOOP(i, n) {
     const T ri = rin[i];
     const T zi = ri / D[i];
@@ -266,9 +267,9 @@ __global__ void k_cc_init(int64_t n, const T* __restrict__ rin, const T* __restr
     z[i] = zi;
     p[i] = zi;
     x[i] = T(0);
-    rz += (double)ri * (double)zi;
+    rz += (A)ri * (A)zi;
   }
-  const double s = block_sum(rz, red);
+  const double s = block_sum((double)rz, red);
   if (threadIdx.x == 0) {
     part_rz[blockIdx.x] = s;
     if (blockIdx.x == 0) *stop = 0;
@@ -295,16 +296,17 @@ __global__ void k_cc_update(int64_t n, int nb, const double* __restrict__ part_p
     return;
   }
   const T a = (T)(sh[1] / sh[0]);
-  double acc = 0;
+  using A = typename DotAcc<T>::type;
+  A acc = 0;
   GRID_LOOP(i, n) {
     x[i] += a * p[i];
     const T ri = r[i] - a * q[i];
     r[i] = ri;
     const T zi = ri / D[i];
     z[i] = zi;
-    acc += (double)ri * (double)zi;
+    acc += (A)ri * (A)zi;
   }
-  const double s = block_sum(acc, red);
+  const double s = block_sum((double)acc, red);
   if (threadIdx.x == 0) part_new[blockIdx.x] = s;
 }
 

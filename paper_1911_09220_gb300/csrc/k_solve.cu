@@ -3,14 +3,20 @@
 // Sec. 4.4: with PA there are no matrix entries, so the preconditioner is the
 // assembled diagonal), FP64 or FP32-inner / FP64-outer iterative refinement.
 //
-// One iteration is six launches on the solver stream:
+// One iteration is four launches on the solver stream:
 //   element kernel (p -> E-vector), scatter (q = A_c p, partials of p.q),
-//   alpha (1 block), update (x += a p, r -= a q, z = r / diag, partials of
-//   r.z and r.r), beta (1 block: convergence test, iteration count), p update.
-// Scalars live in device memory; every kernel returns at once when the device
-// `done` word is set, so a CUDA graph of `check_every` iterations can be
-// replayed and the host only polls between replays. Reductions are block
-// partials summed in a fixed order: results are bitwise reproducible.
+//   update (every block sums the p.q partials to alpha; x += a p, r -= a q,
+//   z = r / diag, partials of r.z and r.r), direction (every block sums the
+//   r.z and r.r partials: convergence test, beta; p = z + beta p).
+// The scalar steps run redundantly in every block from the same partials in
+// the same order, so every block takes the same decision and no single-block
+// kernel sits between the vector kernels; block 0 alone writes the solver
+// state, into fields no other block of that launch reads (r.z alternates
+// between two slots by iteration parity). Scalars live in device memory;
+// every kernel returns at once when the device `done` word is set, so a CUDA
+// graph of `check_every` iterations can be replayed and the host only polls
+// between replays. Reductions are block partials summed in a fixed order:
+// results are bitwise reproducible.
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -21,10 +27,12 @@
 namespace {
 
 struct CgScalars {
-  double rz, alpha, beta, rr, bb, tol2, pq;
+  double rzb[2];    // r.z of the current residual in slot it & 1
+  double beta, rr, bb, tol2;
   double upd2;      // reliable updates: stop for an FP64 update once r.r <= upd2
   double rz_new;    // r.z of the iteration that stopped for an update
-  int it, done, status, maxit;
+  int it, done, status, maxit;  // read by the host as four ints
+  int it1;          // it + 1, written by the update kernel for the direction kernel
   int ru;           // 1: reliable-update mode
 };
 enum { ST_RUN = 0, ST_CONV = 1, ST_NOCONV = 2, ST_BREAK = 3, ST_UPDATE = 4 };
@@ -37,26 +45,44 @@ __device__ double sum_partials(const double* part, int n, double* red) {
   return block_sum(v, red);
 }
 
+// The update and direction kernels read and write their vectors with 16-byte
+// accesses (four floats or two doubles per thread and step); the solver's
+// vectors start at multiples of 4 entries of one workspace, so every one of
+// them is 16-byte aligned, and the last n % W entries run in a scalar tail.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using V = float4;
+  static constexpr int W = 4;
+};
+template <>
+struct Vec16<double> {
+  using V = double2;
+  static constexpr int W = 2;
+};
+
 template <typename T>
 __global__ void k_cg_init(int64_t n, const T* __restrict__ r, const T* __restrict__ diag, T* __restrict__ z,
                           T* __restrict__ p, const T* __restrict__ b, double* __restrict__ part) {
   __shared__ double red[32];
-  double rz = 0, rr = 0, bb = 0;
+  using A = typename DotAcc<T>::type;
+  A rz = 0, rr = 0, bb = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const T ri = r[i];
     const T zi = ri / diag[i];
     z[i] = zi;
     p[i] = zi;
-    rz += (double)ri * (double)zi;
-    rr += (double)ri * (double)ri;
-    if (b) bb += (double)b[i] * (double)b[i];
+    rz += (A)ri * (A)zi;
+    rr += (A)ri * (A)ri;
+    if (b) bb += (A)b[i] * (A)b[i];
   }
   double s;
-  s = block_sum(rz, red);
+  s = block_sum((double)rz, red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
-  s = block_sum(rr, red);
+  s = block_sum((double)rr, red);
   if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = s;
-  s = block_sum(bb, red);
+  s = block_sum((double)bb, red);
   if (threadIdx.x == 0) part[2 * gridDim.x + blockIdx.x] = s;
 }
 
@@ -69,11 +95,12 @@ __global__ void k_cg_init_scalars(CgScalars* sc, const double* __restrict__ part
   const double rr = sum_partials(part + nb, nb, red);
   const double bb = sum_partials(part + 2 * nb, nb, red);
   if (threadIdx.x == 0) {
-    sc->rz = rz;
+    sc->rzb[0] = rz;
     sc->rr = rr;
     sc->bb = bb_given >= 0 ? bb_given : bb;
     sc->tol2 = rtol * rtol * sc->bb;
     sc->it = 0;
+    sc->it1 = 0;
     sc->maxit = maxit;
     sc->status = ST_RUN;
     sc->done = 0;
@@ -90,72 +117,142 @@ __global__ void k_cg_init_scalars(CgScalars* sc, const double* __restrict__ part
   }
 }
 
-__global__ void k_cg_alpha(CgScalars* sc, const double* __restrict__ part, int nb) {
+// x += a p, r -= a q, z = r / diag with a = (r.z) / (p.q), the p.q partials
+// (pq_part, written by the scatter) summed by every block; partials of r.z
+// and r.r to part_out[0, nb) and part_out[nb, 2 nb). A non-positive or
+// non-finite p.q stops the solve (breakdown) in every block alike.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+k_cg_update(int64_t n, CgScalars* __restrict__ sc, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
+            const T* __restrict__ p, const T* __restrict__ q, const T* __restrict__ diag,
+            const double* __restrict__ pq_part, double* __restrict__ part_out, int nb) {
   __shared__ double red[32];
+  __shared__ double s_alpha;
+  __shared__ int s_ok;
   if (sc->done) return;
-  const double pq = sum_partials(part, nb, red);
+  const double pq = sum_partials(pq_part, nb, red);
   if (threadIdx.x == 0) {
-    sc->pq = pq;
-    if (!(pq > 0.0) || !isfinite(pq)) {
-      sc->done = 1;
-      sc->status = ST_BREAK;
-    } else {
-      sc->alpha = sc->rz / pq;
+    const int it = sc->it;
+    const bool ok = pq > 0.0 && isfinite(pq);
+    s_ok = ok;
+    s_alpha = ok ? sc->rzb[it & 1] / pq : 0.0;
+    if (blockIdx.x == 0) {
+      if (ok) {
+        sc->it1 = it + 1;
+      } else {
+        sc->done = 1;
+        sc->status = ST_BREAK;
+      }
     }
   }
-}
-
-template <typename T>
-__global__ void k_cg_update(int64_t n, const CgScalars* __restrict__ sc, T* __restrict__ x, T* __restrict__ r,
-                            T* __restrict__ z, const T* __restrict__ p, const T* __restrict__ q,
-                            const T* __restrict__ diag, double* __restrict__ part) {
-  __shared__ double red[32];
-  if (sc->done) return;
-  const T a = (T)sc->alpha;
-  double rz = 0, rr = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  __syncthreads();
+  if (!s_ok) return;
+  const T a = (T)s_alpha;
+  using A = typename DotAcc<T>::type;
+  using V = typename Vec16<T>::V;
+  constexpr int W = Vec16<T>::W;
+  A rz = 0, rr = 0;
+  const int64_t nv = n / W, stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t j = tid; j < nv; j += stride) {
+    V xv = reinterpret_cast<const V*>(x)[j], rv = reinterpret_cast<const V*>(r)[j];
+    const V pv = reinterpret_cast<const V*>(p)[j], qv = reinterpret_cast<const V*>(q)[j];
+    const V dv = reinterpret_cast<const V*>(diag)[j];
+    V zv;
+    T* xs = reinterpret_cast<T*>(&xv);
+    T* rs = reinterpret_cast<T*>(&rv);
+    T* zs = reinterpret_cast<T*>(&zv);
+    const T* ps = reinterpret_cast<const T*>(&pv);
+    const T* qs = reinterpret_cast<const T*>(&qv);
+    const T* ds = reinterpret_cast<const T*>(&dv);
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      xs[u] += a * ps[u];
+      const T ri = rs[u] - a * qs[u];
+      rs[u] = ri;
+      const T zi = ri / ds[u];
+      zs[u] = zi;
+      rz += (A)ri * (A)zi;
+      rr += (A)ri * (A)ri;
+    }
+    reinterpret_cast<V*>(x)[j] = xv;
+    reinterpret_cast<V*>(r)[j] = rv;
+    reinterpret_cast<V*>(z)[j] = zv;
+  }
+  for (int64_t i = nv * W + tid; i < n; i += stride) {
     x[i] += a * p[i];
     const T ri = r[i] - a * q[i];
     r[i] = ri;
     const T zi = ri / diag[i];
     z[i] = zi;
-    rz += (double)ri * (double)zi;
-    rr += (double)ri * (double)ri;
+    rz += (A)ri * (A)zi;
+    rr += (A)ri * (A)ri;
   }
-  double s = block_sum(rz, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
-  s = block_sum(rr, red);
-  if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = s;
+  double s = block_sum((double)rz, red);
+  if (threadIdx.x == 0) part_out[blockIdx.x] = s;
+  s = block_sum((double)rr, red);
+  if (threadIdx.x == 0) part_out[gridDim.x + blockIdx.x] = s;
 }
 
-__global__ void k_cg_beta(CgScalars* sc, const double* __restrict__ part, int nb) {
+// Convergence test and the next search direction: r.z and r.r summed by every
+// block from part[0, nb) and part[nb, 2 nb); unless the solve stops,
+// beta = (r.z)_new / (r.z)_old and p = z + beta p.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+k_cg_direction(int64_t n, CgScalars* __restrict__ sc, const T* __restrict__ z, T* __restrict__ p,
+               const double* __restrict__ part, int nb) {
   __shared__ double red[32];
+  __shared__ double s_beta;
+  __shared__ int s_go;
   if (sc->done) return;
   const double rz = sum_partials(part, nb, red);
   const double rr = sum_partials(part + nb, nb, red);
   if (threadIdx.x == 0) {
-    sc->it += 1;
-    sc->rr = rr;
+    const int it = sc->it1;
+    int status = ST_RUN;
     if (!isfinite(rz) || !isfinite(rr)) {
-      sc->done = 1;
-      sc->status = ST_BREAK;
+      status = ST_BREAK;
     } else if (sc->ru && (rr <= sc->upd2 || rr <= sc->tol2)) {
       // reliable-update mode: hand over to the host for an FP64 update (the
       // true residual decides convergence); beta waits for the new residual
-      sc->done = 1;
-      sc->status = ST_UPDATE;
-      sc->rz_new = rz;
+      status = ST_UPDATE;
     } else if (rr <= sc->tol2) {
-      sc->done = 1;
-      sc->status = ST_CONV;
-    } else if (sc->it >= sc->maxit) {
-      sc->done = 1;
-      sc->status = ST_NOCONV;
-    } else {
-      sc->beta = rz / sc->rz;
-      sc->rz = rz;
+      status = ST_CONV;
+    } else if (it >= sc->maxit) {
+      status = ST_NOCONV;
+    }
+    s_go = status == ST_RUN;
+    s_beta = rz / sc->rzb[(it - 1) & 1];
+    if (blockIdx.x == 0) {
+      sc->it = it;
+      sc->rr = rr;
+      if (status == ST_RUN) {
+        sc->rzb[it & 1] = rz;
+        sc->beta = s_beta;
+      } else {
+        sc->status = status;
+        sc->done = 1;
+        if (status == ST_UPDATE) sc->rz_new = rz;
+      }
     }
   }
+  __syncthreads();
+  if (!s_go) return;
+  const T b = (T)s_beta;
+  using V = typename Vec16<T>::V;
+  constexpr int W = Vec16<T>::W;
+  const int64_t nv = n / W, stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t j = tid; j < nv; j += stride) {
+    const V zv = reinterpret_cast<const V*>(z)[j];
+    V pv = reinterpret_cast<const V*>(p)[j];
+    const T* zs = reinterpret_cast<const T*>(&zv);
+    T* ps = reinterpret_cast<T*>(&pv);
+#pragma unroll
+    for (int u = 0; u < W; ++u) ps[u] = zs[u] + b * ps[u];
+    reinterpret_cast<V*>(p)[j] = pv;
+  }
+  for (int64_t i = nv * W + tid; i < n; i += stride) p[i] = z[i] + b * p[i];
 }
 
 // After a reliable update replaced r: z = r / diag and partials of r.z.
@@ -163,14 +260,15 @@ template <typename T>
 __global__ void k_cg_rz(int64_t n, const T* __restrict__ r, const T* __restrict__ diag, T* __restrict__ z,
                         double* __restrict__ part) {
   __shared__ double red[32];
-  double rz = 0;
+  using A = typename DotAcc<T>::type;
+  A rz = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const T ri = r[i];
     const T zi = ri / diag[i];
     z[i] = zi;
-    rz += (double)ri * (double)zi;
+    rz += (A)ri * (A)zi;
   }
-  const double s = block_sum(rz, red);
+  const double s = block_sum((double)rz, red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -180,8 +278,10 @@ __global__ void k_cg_resume(CgScalars* sc, const double* __restrict__ part, int 
   __shared__ double red[32];
   const double rz = sum_partials(part, nb, red);
   if (threadIdx.x == 0) {
-    sc->beta = rz / sc->rz;
-    sc->rz = rz;
+    // the stopped iteration advanced `it` but kept its old r.z in slot it - 1
+    const int it = sc->it;
+    sc->beta = rz / sc->rzb[(it - 1) & 1];
+    sc->rzb[it & 1] = rz;
     sc->upd2 = upd2;
     sc->status = ST_RUN;
     sc->done = 0;
@@ -287,25 +387,28 @@ struct Work {
 
 fem_status get_work(fem_form* f, bool mixed, Work& w) {
   const int64_t n = fem_form_len(f);
+  const int64_t np = (n + 3) & ~(int64_t)3;  // vector stride: every vector 16-byte aligned
   w.n = n;
   w.nb = fem_scatter_blocks(n);
-  const size_t need64 = (size_t)7 * n;
+  const size_t need64 = (size_t)7 * np;
   if (f->work64_len < need64) {
     dev_free(f->d_work64);
     FEM_TRY(dev_alloc(&f->d_work64, need64));
     f->work64_len = need64;
   }
   double* b = f->d_work64;
-  w.x = b; w.r = b + n; w.z = b + 2 * n; w.p = b + 3 * n; w.q = b + 4 * n; w.diag = b + 5 * n; w.t = b + 6 * n;
+  w.x = b; w.r = b + np; w.z = b + 2 * np; w.p = b + 3 * np; w.q = b + 4 * np; w.diag = b + 5 * np;
+  w.t = b + 6 * np;
   if (mixed) {
-    const size_t need32 = (size_t)6 * n;
+    const size_t need32 = (size_t)6 * np;
     if (f->work32_len < need32) {
       dev_free(f->d_work32);
       FEM_TRY(dev_alloc(&f->d_work32, need32));
       f->work32_len = need32;
     }
     float* a = f->d_work32;
-    w.x32 = a; w.r32 = a + n; w.z32 = a + 2 * n; w.p32 = a + 3 * n; w.q32 = a + 4 * n; w.diag32 = a + 5 * n;
+    w.x32 = a; w.r32 = a + np; w.z32 = a + 2 * np; w.p32 = a + 3 * np; w.q32 = a + 4 * np;
+    w.diag32 = a + 5 * np;
   }
   const size_t red_need = (size_t)3 * w.nb + 16 + (sizeof(CgScalars) + 7) / 8;
   if (f->red_len < red_need) {
@@ -328,10 +431,8 @@ fem_status cg_iteration(const fem_form* f, const Work& w, int dtype, T* x, T* r,
   const int vt = std::is_same<T, float>::value ? FEM_F32 : FEM_F64;
   FEM_TRY(fem_launch_apply_element(f, dtype, p, f->d_ye, s, skip));
   FEM_TRY(fem_launch_scatter(f, vt, f->d_ye, q, f->d_ess_mask, p, w.part, w.nb, s, skip));
-  k_cg_alpha<<<1, kRedThreads, 0, s>>>(w.sc, w.part, w.nb);
-  k_cg_update<T><<<w.nb, 256, 0, s>>>(w.n, w.sc, x, r, z, p, q, diag, w.part);
-  k_cg_beta<<<1, kRedThreads, 0, s>>>(w.sc, w.part, w.nb);
-  k_cg_p<T><<<w.nb, 256, 0, s>>>(w.n, w.sc, z, p);
+  k_cg_update<T><<<w.nb, kRedThreads, 0, s>>>(w.n, w.sc, x, r, z, p, q, diag, w.part, w.part + w.nb, w.nb);
+  k_cg_direction<T><<<w.nb, kRedThreads, 0, s>>>(w.n, w.sc, z, p, w.part + w.nb, w.nb);
   FEM_LAUNCHED();
   return FEM_OK;
 }
