@@ -453,6 +453,130 @@ fem_status fem_mg_restrict(fem_mg* mg, int level, const double* rf, double* rc, 
 fem_status fem_mg_solve(fem_mg* mg, const double* b, double* x, const fem_solve_opts* opts,
                         fem_solve_info* info, void* stream);
 
+/* ---- sharded operator: element partition with an owned + halo L-vector --
+ * The paper's parallel operator is A = P^T G^T B^T D B G P (Sec. 4.3
+ * "Operator Decomposition"): every rank applies G^T B^T D B G to the
+ * elements it owns, and P / P^T move values between the global true-DOF
+ * vector and the ranks' local L-vectors -- the parallel assembly step that
+ * FormLinearSystem performs (Sec. 5.1). Here a rank's L-vector holds every
+ * DOF of its elements (owned ones and a halo of DOFs shared with other
+ * ranks), and vectors are kept consistent: each shared DOF has the same value
+ * on every rank that holds it. After a rank's element kernel and scatter,
+ * each shared DOF holds this rank's partial sum only; one exchange with the
+ * neighbouring ranks (each sends its partials of the DOFs it shares with that
+ * neighbour) and a combine step that adds the partials of all sharing ranks
+ * in ascending rank order give every holder the same assembled value (P^T
+ * then P in one round). Dot products count each DOF once, on its owner (the
+ * lowest rank holding it), and sum the ranks' results with an all-reduce.
+ *
+ * Communication belongs to the caller (NCCL, gloo, MPI ...), through the
+ * callbacks of fem_comm. Exchange buffers are device float64 arrays owned by
+ * the shard, laid out neighbour after neighbour; for neighbour k the
+ * vdim * count_k values run from off[k] to off[k+1], component-major inside
+ * that range, DOFs in ascending global number (the same order on both ends).
+ * The library synchronises `stream` before a callback when host_sync != 0
+ * (transports that read device memory from the host); otherwise the callback
+ * must order its work after the work already on `stream` and before work
+ * enqueued later (as torch.distributed's NCCL backend does on the current
+ * stream). A callback returns 0 on success; anything else makes the calling
+ * entry point fail with FEM_ECUDA. */
+typedef struct fem_comm {
+  void* ctx;
+  int host_sync;
+  /* Send send[off[k], off[k+1]) to rank nbr[k] and receive the same number
+   * of values from it into recv[off[k], off[k+1]), for k < nnbr. nbr and off
+   * are host arrays owned by the shard; send and recv are device pointers. */
+  int (*exchange)(void* ctx, int nnbr, const int32_t* nbr, const int64_t* off, double* send, double* recv,
+                  void* stream);
+  /* Sum vals[0, n) (device float64) over all ranks, in place. */
+  int (*allreduce)(void* ctx, double* vals, int n, void* stream);
+} fem_comm;
+
+typedef struct fem_shard fem_shard;
+
+/* Element partition into nparts slabs: elements sorted by the centroid of
+ * their vertices along the coordinate axis in which the centroids spread
+ * widest (ties by element number), then cut into nparts runs of consecutive
+ * elements, the first ne % nparts runs one element longer. part_host[ne]
+ * (host, caller-owned) receives each element's part. The same mesh gives
+ * the same partition on every rank. Errors: FEM_EINVAL (nparts < 1 or
+ * nparts > ne). */
+fem_status fem_partition_slabs(const fem_mesh* mesh, int nparts, int32_t* part_host);
+
+/* Rank `rank`'s shard of the global space gspace under the element
+ * partition part_host[ne] (values in [0, nparts), nparts <= 64): its
+ * elements in ascending global number, a local mesh of their vertices
+ * (ascending global vertex number), the local space of order p on it (its
+ * own numbering, Sec. 3.4), the local -> global DOF map, ownership, the
+ * neighbour ranks, and the exchange and combine tables (uploaded to the
+ * device). Forms for the shard are created on fem_shard_space(). Every rank
+ * builds the same global space to agree on global DOF numbers. Errors:
+ * FEM_EINVAL (arguments, a rank without elements), FEM_EUNSUPPORTED
+ * (curved meshes), FEM_ENOMEM. */
+fem_status fem_shard_create(const fem_space* gspace, const int32_t* part_host, int nparts, int rank,
+                            fem_shard** out);
+void fem_shard_destroy(fem_shard* sh);
+/* The shard's local space (owned by the shard; valid until it is
+ * destroyed). */
+const fem_space* fem_shard_space(const fem_shard* sh);
+/* Sizes: local elements, local DOFs, owned local DOFs, neighbour ranks,
+ * exchange slots (DOFs shared with a neighbour, summed over neighbours),
+ * and global DOFs; any pointer may be NULL. */
+fem_status fem_shard_info(const fem_shard* sh, int64_t* ne_local, int64_t* ndof_local, int64_t* ndof_owned,
+                          int* nnbr, int64_t* nslots, int64_t* ndof_global);
+/* Host copies of the plan (any pointer may be NULL): elems[ne_local] global
+ * element numbers; l2g[ndof_local] global DOF of each local DOF;
+ * owned[ndof_local] 1 where this rank owns the DOF; nbr[nnbr] neighbour
+ * ranks, ascending; slot_off[nnbr + 1] slot ranges per neighbour;
+ * slot_dof[nslots] local DOF of each slot (per neighbour in ascending
+ * global DOF order). */
+fem_status fem_shard_tables(const fem_shard* sh, int64_t* elems, int64_t* l2g, uint8_t* owned, int32_t* nbr,
+                            int64_t* slot_off, int32_t* slot_dof);
+/* Combine table (host copies): for the nshared local DOFs held by more than
+ * one rank, comb_dof[j] is the local DOF and comb_off[j] .. comb_off[j+1]
+ * its entries in ascending rank order, comb_src[t] = -1 for this rank's own
+ * partial, else the slot holding the partial received from that rank. Any
+ * pointer may be NULL; *nshared and *nentries give the sizes. */
+fem_status fem_shard_combine_table(const fem_shard* sh, int64_t* nshared, int64_t* nentries, int32_t* comb_dof,
+                                   int32_t* comb_off, int32_t* comb_src);
+/* Map global DOF numbers (host, n) to local ones: out_host[i] = local DOF of
+ * global_host[i], or -1 when this shard does not hold it. */
+fem_status fem_shard_localize(const fem_shard* sh, const int32_t* global_host, int64_t n, int32_t* out_host);
+/* Device gathers between a global vector (length vdim * ndof_global,
+ * component-major) and the local one (vdim * ndof_local): to_local copies
+ * every local entry from its global DOF; to_global writes the owned local
+ * entries into the global vector (other entries untouched). */
+fem_status fem_shard_to_local(const fem_shard* sh, int vdim, const double* xg, double* xl, void* stream);
+fem_status fem_shard_to_global(const fem_shard* sh, int vdim, const double* xl, double* xg, void* stream);
+/* y = A x on consistent local L-vectors (float64, vdim * ndof_local) with
+ * the form `form` created on fem_shard_space(sh): element kernel and scatter
+ * of the local elements, exchange of the shared DOFs' partials, combine;
+ * constrained != 0 applies A_c as fem_apply does (needs the form's essential
+ * DOFs: the local numbers of the global essential set, fem_shard_localize).
+ * Errors: as fem_apply, FEM_ECUDA when a callback fails. */
+fem_status fem_shard_apply(const fem_shard* sh, const fem_form* form, const double* x, double* y, int constrained,
+                           const fem_comm* comm, void* stream);
+/* Assembled diagonal (consistent), constrained as fem_assemble_diagonal. */
+fem_status fem_shard_diagonal(const fem_shard* sh, const fem_form* form, double* diag, int constrained,
+                              const fem_comm* comm, void* stream);
+/* Load vector b from quadrature-point values of the local elements
+ * (fq [ne_local][q1d^3], as fem_rhs), assembled across ranks. */
+fem_status fem_shard_rhs(const fem_shard* sh, const fem_form* form, const double* fq, double* b,
+                         const fem_comm* comm, void* stream);
+/* *out_host = sum over owned entries of a . b, summed over ranks (all
+ * vectors consistent, vdim * ndof_local). Synchronises `stream`. */
+fem_status fem_shard_dot(const fem_shard* sh, int vdim, const double* a, const double* b, double* out_host,
+                         const fem_comm* comm, void* stream);
+/* Jacobi-PCG (FP64) on the sharded constrained operator, the iteration of
+ * fem_solve: x0 = x (its essential entries are the Dirichlet values), stop
+ * when the true residual ||b - A_c x|| <= rtol ||b|| (confirmed at exit).
+ * Per iteration: one sharded apply (one exchange) and two all-reduces (p.q;
+ * then r.z and r.r together). opts: rtol, maxit, max_outer (restarts from
+ * the true residual), precond; other fields are ignored (FP64 only).
+ * Synchronises `stream`; fills info. Errors: as fem_solve. */
+fem_status fem_shard_solve(const fem_shard* sh, const fem_form* form, const double* b, double* x,
+                           const fem_solve_opts* opts, fem_solve_info* info, const fem_comm* comm, void* stream);
+
 /* ---- arithmetic-peak probe (the paper has no counterpart) ---------------
  * Measures the fused multiply-add rate of the current device in the given
  * arithmetic: one kernel on every SM at full occupancy, eight independent

@@ -99,6 +99,21 @@ SIGNATURES = {
     "fem_mg_prolong": (I, [P, I, P, P, P]),
     "fem_mg_restrict": (I, [P, I, P, P, P]),
     "fem_mg_solve": (I, [P, P, P, C.POINTER(SolveOpts), C.POINTER(SolveInfo), P]),
+    "fem_partition_slabs": (I, [P, I, P]),
+    "fem_shard_create": (I, [P, P, I, I, C.POINTER(P)]),
+    "fem_shard_destroy": (None, [P]),
+    "fem_shard_space": (P, [P]),
+    "fem_shard_info": (I, [P, P, P, P, P, P, P]),
+    "fem_shard_tables": (I, [P, P, P, P, P, P, P]),
+    "fem_shard_combine_table": (I, [P, P, P, P, P, P]),
+    "fem_shard_localize": (I, [P, P, I64, P]),
+    "fem_shard_to_local": (I, [P, I, P, P, P]),
+    "fem_shard_to_global": (I, [P, I, P, P, P]),
+    "fem_shard_apply": (I, [P, P, P, P, I, P, P]),
+    "fem_shard_diagonal": (I, [P, P, P, I, P, P]),
+    "fem_shard_rhs": (I, [P, P, P, P, P, P]),
+    "fem_shard_dot": (I, [P, I, P, P, P, P, P]),
+    "fem_shard_solve": (I, [P, P, P, P, C.POINTER(SolveOpts), C.POINTER(SolveInfo), P, P]),
     "fem_probe_fma_peak": (I, [I, I, C.POINTER(C.c_double), P]),
 }
 

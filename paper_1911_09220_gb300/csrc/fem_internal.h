@@ -120,6 +120,43 @@ struct fem_form {
   int geo_k = 0;
 };
 
+// Rank `rank`'s part of an element-partitioned space (fem_shard.cpp builds
+// the plan on the host; k_shard.cu runs the exchange-side kernels and the
+// sharded solver).
+struct fem_shard {
+  int nparts = 1, rank = 0;
+  int64_t ndof_global = 0;
+  fem_mesh* lmesh = nullptr;            // owned local mesh and space
+  fem_space* lspace = nullptr;
+  std::vector<int64_t> elems;           // global element numbers, ascending
+  std::vector<int64_t> l2g;             // [ndof_local] global DOF
+  std::vector<uint8_t> owned;           // [ndof_local]
+  int64_t n_owned = 0;
+  std::vector<int32_t> nbr;             // neighbour ranks, ascending
+  std::vector<int64_t> slot_off;        // [nnbr + 1] slot ranges per neighbour
+  std::vector<int32_t> slot_dof;        // [nslots] local DOF per slot
+  std::vector<int32_t> comb_dof, comb_off, comb_src;  // combine table (see fem.h)
+  // exchange buffer offsets for vdim = 1 and 3: [nnbr + 1] in doubles
+  std::vector<int64_t> xoff1, xoff3;
+  // device copies
+  int64_t* d_l2g = nullptr;
+  uint8_t* d_owned = nullptr;
+  int32_t* d_slot_dof = nullptr;
+  int32_t* d_slot_nbr = nullptr;        // [nslots] neighbour index of each slot
+  int64_t* d_slot_off = nullptr;        // [nnbr + 1]
+  int32_t* d_comb_dof = nullptr;
+  int32_t* d_comb_off = nullptr;
+  int32_t* d_comb_src = nullptr;
+  double* d_send = nullptr;             // 3 * nslots (room for vector forms)
+  double* d_recv = nullptr;
+  // solver workspace (lazy, k_shard.cu)
+  mutable double* d_work = nullptr;
+  mutable size_t work_len = 0;
+  mutable double* d_red = nullptr;
+  mutable size_t red_len = 0;
+  mutable double* h_pinned = nullptr;
+};
+
 // Length of the form's vectors: vdim * ndof (component-major).// Length of the form's vectors: vdim * ndof (component-major).
 inline int64_t fem_form_len(const fem_form* f) { return (int64_t)f->vdim * f->space->ndof; }
 
