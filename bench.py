@@ -10,9 +10,13 @@ so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-With torchrun (N > 1) every rank applies the operator of its own
-independent problem (seed offset by rank; no collective in the data path)
-and `value` is the aggregate DOFs/s over all ranks (weak scaling).
+With torchrun (N > 1) the default is the sharded operator: one problem
+partitioned into element slabs, one per rank, with a halo exchange over
+NCCL after every apply (`--scaling weak`: about N^3 elements per rank;
+`--scaling strong`: the N^3 problem split over the ranks); `value` is the
+global DOFs over the slowest rank's apply time. `--parallel replicas` runs
+one independent problem per rank instead (seed offset by rank; no
+collective in the data path; aggregate DOFs/s).
 The reference arm (`--impl reference`) times the CPU oracle (assembled CSR
 SpMV, scipy, one core) on a bounded sample of the same workload.
 """
@@ -161,6 +165,8 @@ def reduce_max(value, device=None):
     import torch.distributed as dist
     if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
         return float(value)
+    if dist.get_backend() != "nccl":
+        device = None
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
@@ -185,17 +191,32 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+_ORACLE_SAMPLES = {}
+
+
+def cpu_oracle_problem(p, N_sample):
+    """The oracle's assembled sub-problem of the same recipe (cached: the
+    SpMV and PCG baselines share one assembly). Returns (problem, K,
+    assembly seconds, x generator)."""
+    key = (p, N_sample)
+    if key not in _ORACLE_SAMPLES:
+        from oracle import assemble
+        c, h, kappa, xgen = make_problem(p, N_sample)
+        t0 = time.perf_counter()
+        prob = assemble.Problem(c, h, p, p + 2, kappa=kappa)
+        K = prob.K
+        _ORACLE_SAMPLES[key] = (prob, K, time.perf_counter() - t0, xgen)
+    return _ORACLE_SAMPLES[key]
+
+
 def cpu_oracle_spmv(p, N_sample, reps, deadline_s=30.0):
     """Time the oracle's apply (its assembled CSR matrix) on a sub-problem of
     the same recipe: scipy's product on one thread, and the oracle's C loop
     (OpenMP over rows) on every host core. Returns dict; `gdofs`, `times`
     and `cores` are the all-cores figures."""
-    from oracle import assemble, cspmv
-    c, h, kappa, xgen = make_problem(p, N_sample)
-    t0 = time.perf_counter()
-    prob = assemble.Problem(c, h, p, p + 2, kappa=kappa)
-    K = prob.K
-    t_asm = time.perf_counter() - t0
+    from oracle import cspmv
+    prob, K, t_asm, xgen = cpu_oracle_problem(p, N_sample)
+    h = prob.hexes
     x = xgen(prob.ndof)
 
     def timed(fn, budget):
@@ -223,6 +244,60 @@ def cpu_oracle_spmv(p, N_sample, reps, deadline_s=30.0):
                             "kind": "scipy CSR product, one thread"}}
 
 
+class _ThreadedCSR:
+    """The oracle's assembled matrix with its product on `threads` host cores
+    (the oracle's C loop): what the oracle's PCG multiplies by."""
+
+    def __init__(self, K, threads):
+        from oracle import cspmv
+        self.K, self.C, self.threads, self.shape = K, cspmv.CSR(K), int(threads), K.shape
+
+    def __matmul__(self, x):
+        return self.C.apply(x, self.threads)
+
+    def diagonal(self):
+        return self.K.diagonal()
+
+
+def cpu_oracle_pcg(p, N_sample, iters_full=None, ndof_full=None, one_core_iters=20):
+    """The oracle's Jacobi-PCG to the 1e-10 true residual on a sub-problem of
+    the same recipe (sin sin sin source, homogeneous Dirichlet boundary):
+    all host cores for the C product, then `one_core_iters` iterations on one
+    core (time per iteration). With iters_full / ndof_full, the all-cores and
+    one-core solve times are extrapolated to the full problem as time per
+    iteration per DOF x DOFs x iterations (labelled as extrapolated)."""
+    from oracle import solve as osolve
+    prob, K, t_asm0, _ = cpu_oracle_problem(p, N_sample)
+    h = prob.hexes
+    t0 = time.perf_counter()
+    ess = prob.num["boundary_dofs"]
+    f = lambda x: 3 * np.pi ** 2 * np.sin(np.pi * x[..., 0]) * np.sin(np.pi * x[..., 1]) * np.sin(np.pi * x[..., 2])
+    Ac = osolve.constrain(K, ess)
+    bc = osolve.constrain_rhs(K, prob.load(f), ess)
+    t_asm = t_asm0 + time.perf_counter() - t0
+    cores = host_cores()
+    A_all = _ThreadedCSR(Ac, cores)
+    t0 = time.perf_counter()
+    _, info = osolve.pcg(A_all, bc, rtol=1e-10, maxit=20000)
+    t_all = time.perf_counter() - t0
+    A_one = _ThreadedCSR(Ac, 1)
+    t0 = time.perf_counter()
+    osolve.pcg(A_one, bc, rtol=1e-30, maxit=one_core_iters)
+    t_one_it = (time.perf_counter() - t0) / one_core_iters
+    n, its = prob.ndof, info["iterations"]
+    out = {"ndof": n, "elements": int(h.shape[0]), "iterations": its, "converged": bool(info["converged"]),
+           "true_relres": float(info["true_relres"]), "solve_s": t_all, "cores": cores,
+           "one_core_s_per_iteration": t_one_it, "one_core_solve_s_est": t_one_it * its,
+           "assembly_s": t_asm, "kind": "oracle Jacobi-PCG (Saad Alg. 9.1), assembled CSR, C product"}
+    if iters_full and ndof_full:
+        scale = (ndof_full / n) * (iters_full / max(its, 1))
+        out["extrapolated"] = {"ndof": ndof_full, "iterations": iters_full, "solve_s_all_cores": t_all * scale,
+                               "solve_s_one_core": t_one_it * its * scale,
+                               "how": "sample time per iteration per DOF x full DOFs x the full problem's "
+                                      "iteration count (measured by the GPU FP64 solve)"}
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -230,6 +305,8 @@ def run_reference(args):
     p = args.p
     r = cpu_oracle_spmv(p, args.cpu_n, max(args.steps, 1), deadline_s=60.0)
     total = sum(r["times"][: args.steps]) if len(r["times"]) >= args.steps else sum(r["times"])
+    pcg = None if args.no_solve else cpu_oracle_pcg(p, args.cpu_n, iters_full=FP64_PCG_ITERS.get((p, args.N)),
+                                                    ndof_full=(p * args.N + 1) ** 3)
     value = r["gdofs"]
     line = {
         "impl": "reference", "metric": "PA diffusion apply GDOF/s", "value": value, "unit": "GDOF/s",
@@ -242,13 +319,17 @@ def run_reference(args):
                          "sample": f"the oracle's assembled CSR matrix applied by its C loop (OpenMP over rows, "
                                    f"{r['cores']} threads), {r['ndof']} DOFs (nnz {r['nnz']}), median of "
                                    f"{len(r['times'])}; assembly {r['t_assembly']:.1f} s untimed",
-                         "single_core": r["single_core"]},
+                         "single_core": r["single_core"], "pcg": pcg},
         "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "total_s": total,
     }
     print(json.dumps(line))
     return 0
 
+
+# FP64 Jacobi-PCG iterations of the GPU solve at full size (p, N), for the
+# per-DOF extrapolation of the CPU oracle's solve time
+FP64_PCG_ITERS = {(4, 68): 1870, (6, 45): 2256}
 
 SWEEP_N = {"1e6": {1: 99, 2: 49, 3: 33, 4: 25, 5: 20, 6: 16, 7: 14, 8: 12},
            "4e6": {1: 158, 2: 79, 3: 53, 4: 39, 5: 32, 6: 26, 7: 23, 8: 20},
@@ -831,6 +912,104 @@ def run_grad(args):
     return 0
 
 
+def run_sharded(args, world, rank, local, dev):
+    """N > 1: one problem element-partitioned over the ranks (slab
+    partition, owned + halo L-vector, one halo exchange per apply over NCCL;
+    include/fem.h fem_shard_*). Weak scaling keeps ~N^3 elements per rank
+    (global mesh round(N * world^(1/3))^3); strong scaling splits the N^3
+    problem. One step = one sharded apply y = A x (element kernel, scatter,
+    pack, exchange, combine); value = global DOFs / the slowest rank's step
+    time."""
+    import torch
+    import torch.distributed as dist
+    import paper_1911_09220_gb300 as F
+    from paper_1911_09220_gb300 import shard as S
+    from fem_inputs import hex_lattice, lognormal, x_uniform
+    p, q = args.p, args.p + 2
+    Ng = int(round(args.N * world ** (1.0 / 3.0))) if args.scaling == "weak" else args.N
+    c, h = hex_lattice(Ng, 0.15, seed=10 + p)
+    kappa = lognormal(20 + p, h.shape[0])
+    t0 = time.perf_counter()
+    gmesh = F.Mesh(c, h)
+    gspace = F.Space(gmesh, p)
+    part = S.partition_slabs(gmesh, world)
+    sh = S.Shard(gspace, part, world, rank)
+    tab = sh.tables()
+    t_setup = time.perf_counter() - t0
+    form = F.Form(sh.space, "diffusion", q, coef=torch.as_tensor(kappa[tab["elems"]], device=dev))
+    comm = S.TorchComm()
+    xg = x_uniform(30 + p, gspace.ndof)
+    x_host = torch.as_tensor(np.ascontiguousarray(xg[tab["l2g"]])).pin_memory()
+    x = x_host.to(dev)
+    y = torch.empty_like(x)
+    del xg
+    stream = torch.cuda.current_stream()
+    dist.barrier()
+    for _ in range(args.warmup):
+        sh.apply(form, x, y, comm)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sh.apply(form, x, y, comm)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    ms_step = reduce_max(e0.elapsed_time(e1) / args.steps, dev)
+    value = gspace.ndof / (ms_step * 1e-3) / 1e9
+    # the rank's element kernel alone (FP64 roofline of the local work)
+    ye = torch.empty((sh.ne, (p + 1) ** 3), dtype=torch.float64, device=dev)
+    t_el = time_events(lambda: form.apply_element(x, ye), args.steps, 2)
+    flops, bytes_alg = alg_counts(p, q, sh.ne, sh.ndof)
+    achieved = flops / (t_el * 1e-3) / 1e12
+    # end to end: the rank's local input from pinned host memory, the sharded
+    # apply, the result back to pinned host memory, every step
+    y_host = torch.empty_like(x_host).pin_memory()
+    xb = torch.empty_like(x)
+
+    def e2e_step():
+        xb.copy_(x_host, non_blocking=True)
+        sh.apply(form, xb, y, comm)
+        y_host.copy_(y, non_blocking=True)
+
+    e2e_step()
+    dist.barrier()
+    torch.cuda.synchronize()
+    t_e2e = reduce_max(time_events(e2e_step, args.steps, 1), dev)
+    if rank == 0:
+        line = {
+            "metric": "PA diffusion apply GDOF/s", "value": value, "unit": "GDOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": args.scaling, "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"FP64 PA diffusion apply y=Ax, p={p}, q={q}, {Ng}^3 hex mesh perturbed 0.15h, "
+                                   f"lognormal kappa, {gspace.ndof} DOFs, element slabs over {world} ranks",
+                       "p": p, "q1d": q, "N": Ng, "ndof": gspace.ndof, "elements": int(h.shape[0]),
+                       "parallelism": f"element-partitioned x{world} (halo exchange over NCCL)",
+                       "rank0_local_dofs": sh.ndof, "rank0_neighbours": sh.nnbr, "rank0_shared_slots": sh.nslots,
+                       "l2": "inputs larger than L2; no flush"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": f"k_diffusion_apply<double,{p + 1},{q},NE> on rank 0's elements",
+                         "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"},
+            "cpu_baseline": None,
+            "e2e": {"value": gspace.ndof / (t_e2e * 1e-3) / 1e9, "unit": "GDOF/s",
+                    "h2d_bytes_per_step": 8 * sh.ndof * world, "d2h_bytes_per_step": 8 * sh.ndof * world,
+                    "ms_per_step": t_e2e},
+            "gpu_launches": 4 * args.steps, "clocks": clk, "setup_s": {"global_and_shard_host": t_setup},
+        }
+        print(json.dumps(line))
+    dist.barrier()
+    dist.destroy_process_group()
+    return 0
+
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -852,6 +1031,10 @@ def main():
     ap.add_argument("--nrhs", type=int, default=8)
     ap.add_argument("--batch-f64-solve", action="store_true")
     ap.add_argument("--mg-coarse-its", type=int, default=30)
+    ap.add_argument("--parallel", default="shard", choices=["shard", "replicas"],
+                    help="N > 1: one element-partitioned problem (shard) or independent problems per rank")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="shard mode: ~N^3 elements per rank (weak) or one N^3 problem split over the ranks")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -879,13 +1062,18 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        dist.init_process_group("nccl")
+        # FEM_BENCH_BACKEND=gloo runs the ranks' exchanges through host copies
+        # (several ranks sharing one GPU in a test); NCCL otherwise
+        dist.init_process_group(os.environ.get("FEM_BENCH_BACKEND", "nccl"))
+    local = local % max(1, torch.cuda.device_count())
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
     from paper_1911_09220_gb300 import build as fbuild
     fbuild.build()
     import paper_1911_09220_gb300 as F
+    if world > 1 and args.parallel == "shard":
+        return run_sharded(args, world, rank, local, dev)
 
     # measured FMA rates of this GPU (library probe kernel, ~20 ms each):
     # the cross-check of the derived FP64 peak that the roofline is quoted on
@@ -1097,12 +1285,14 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
+        its_full = solve["f64"]["iterations"] if solve else FP64_PCG_ITERS.get((p, N))
+        pcg = None if args.no_solve else cpu_oracle_pcg(p, args.cpu_n, iters_full=its_full, ndof_full=n)
         r = cpu_oracle_spmv(p, args.cpu_n, 20, deadline_s=20.0)
         cpu = {"value": r["gdofs"], "unit": "GDOF/s", "cores": r["cores"], "kind": "oracle",
                "sample": f"the oracle's assembled CSR matrix on a {args.cpu_n}^3-element sample of the same "
                          f"recipe ({r['ndof']} DOFs, nnz {r['nnz']}) applied by its C loop (OpenMP over rows, "
                          f"{r['cores']} threads), median of {r['reps']}; assembly {r['t_assembly']:.1f} s not timed",
-               "single_core": r["single_core"], "host_cpus": os.cpu_count()}
+               "single_core": r["single_core"], "host_cpus": os.cpu_count(), "pcg": pcg}
 
     if rank == 0:
         line = {
