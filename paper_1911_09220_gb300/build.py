@@ -46,9 +46,15 @@ def _sources():
 def _defines():
     """Build options from the environment: FEM_NE_TABLE=large|small selects
     one candidate elements-per-block table for every element type (used to
-    re-measure the choice); unset or `measured` gives the measured table."""
+    re-measure the choice); unset or `measured` gives the measured table.
+    FEM_BATCH_MIN_BLOCKS=k compiles the batched FP32 element kernel for k
+    resident 256-thread blocks per SM (its register budget)."""
     t = os.environ.get("FEM_NE_TABLE", "measured")
-    return {"large": ["-DFEM_NE_TABLE=1"], "small": ["-DFEM_NE_TABLE=2"]}.get(t, [])
+    out = {"large": ["-DFEM_NE_TABLE=1"], "small": ["-DFEM_NE_TABLE=2"]}.get(t, [])
+    mb = os.environ.get("FEM_BATCH_MIN_BLOCKS")
+    if mb:
+        out.append(f"-DFEM_BATCH_MIN_BLOCKS={int(mb)}")
+    return out
 
 
 def _compile(src, obj, nvcc, cuda_home, verbose_ptxas):

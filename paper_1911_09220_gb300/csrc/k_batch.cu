@@ -9,7 +9,7 @@
 // scatter and the CG vector updates. Persistent kernels (grid = SMs x resident
 // blocks) stride over the item lists, which are sorted by decreasing cost. An
 // element item applies its tile to all nrhs right-hand sides in turn, so each
-// D block streams from HBM once and is re-read from L2 for the other
+// D block streams from HBM once and is re-read from L1 / L2 for the other
 // right-hand sides. All launches of an apply (or of `check_every` CG
 // iterations) are captured into one CUDA graph and replayed.
 //
@@ -22,6 +22,7 @@
 #include <map>
 #include <string>
 #include <vector>
+#include <type_traits>
 
 #include "fem_internal.h"
 #include "k_common.cuh"
@@ -91,8 +92,16 @@ __device__ __noinline__ void run_tile(const BProb& P, int e0, int tile, int nrhs
   }
 }
 
+// Resident blocks per SM the FP32 element kernel is compiled for (its
+// register budget: 65536 / (kBT * blocks)); build option FEM_BATCH_MIN_BLOCKS.
+#ifndef FEM_BATCH_MIN_BLOCKS
+#define FEM_BATCH_MIN_BLOCKS 4
+#endif
 template <typename T>
-__global__ void __launch_bounds__(kBT)
+constexpr int batch_min_blocks() { return std::is_same<T, float>::value ? FEM_BATCH_MIN_BLOCKS : 1; }
+
+template <typename T>
+__global__ void __launch_bounds__(kBT, batch_min_blocks<T>())
 k_batch_element(const BProb* __restrict__ probs, const BItem* __restrict__ items, int nitems,
                 const int* __restrict__ tiles, int nrhs, const int* __restrict__ done, const T* __restrict__ X,
                 T* __restrict__ YE) {
@@ -112,34 +121,60 @@ k_batch_element(const BProb* __restrict__ probs, const BItem* __restrict__ items
 }
 
 // y = G^T ye (inverse map), optional constraint (y_ess = xin_ess) and partial
-// dot products xin . y per (system, chunk).
+// dot products xin . y per (system, chunk). Each DOF's inverse-map entries
+// are read once for a group of up to kRG right-hand sides (their E-vector
+// slots are the same, kRG * ne * nd apart); the sums run in the same order
+// as a one-right-hand-side scatter.
+constexpr int kRG = 8;
+
 template <typename T>
 __global__ void __launch_bounds__(kBT)
 k_batch_scatter(const BProb* __restrict__ probs, const VItem* __restrict__ items, int nitems, int nrhs,
                 const int* __restrict__ done, const T* __restrict__ YE, T* __restrict__ Y, const T* __restrict__ Xin,
                 int constrained, double* __restrict__ part) {
   __shared__ double red[32];
+  using A = typename DotAcc<T>::type;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const VItem v = items[it];
     const BProb& P = probs[v.prob];
     const int64_t i0 = (int64_t)v.chunk * kCH, i1 = min(i0 + kCH, P.ndof);
-    for (int r = 0; r < nrhs; ++r) {
-      if (done && done[P.sys0 + r]) continue;
-      const T* ye = YE + P.yeoff + (int64_t)r * P.ne * P.nd;
-      const int64_t xo = P.xoff + (int64_t)r * P.ndof;
-      using A = typename DotAcc<T>::type;
-      A acc = 0;
+    const int64_t es = (int64_t)P.ne * P.nd;  // E-vector stride between right-hand sides
+    for (int r0 = 0; r0 < nrhs; r0 += kRG) {
+      const int nr = min(kRG, nrhs - r0);
+      bool live[kRG];
+#pragma unroll
+      for (int g = 0; g < kRG; ++g) live[g] = g < nr && !(done && done[P.sys0 + r0 + g]);
+      const T* ye = YE + P.yeoff + (int64_t)r0 * es;
+      A acc[kRG];
+#pragma unroll
+      for (int g = 0; g < kRG; ++g) acc[g] = 0;
       for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const int32_t a = P.off[i], b = P.off[i + 1];
-        T s = 0;
-        for (int32_t k = a; k < b; ++k) s += ye[P.idx[k]];
-        if (constrained && P.mask && P.mask[i]) s = Xin[xo + i];
-        Y[xo + i] = s;
-        if (part) acc += (A)Xin[xo + i] * (A)s;
+        T sum[kRG];
+#pragma unroll
+        for (int g = 0; g < kRG; ++g) sum[g] = 0;
+        for (int32_t k = a; k < b; ++k) {
+          const int32_t sl = P.idx[k];
+#pragma unroll
+          for (int g = 0; g < kRG; ++g)
+            if (live[g]) sum[g] += ye[g * es + sl];
+        }
+        const bool ess = constrained && P.mask && P.mask[i];
+#pragma unroll
+        for (int g = 0; g < kRG; ++g) {
+          if (!live[g]) continue;
+          const int64_t xo = P.xoff + (int64_t)(r0 + g) * P.ndof;
+          const T sv = ess ? Xin[xo + i] : sum[g];
+          Y[xo + i] = sv;
+          if (part) acc[g] += (A)Xin[xo + i] * (A)sv;
+        }
       }
       if (part) {
-        const double tot = block_sum((double)acc, red);
-        if (threadIdx.x == 0) part[P.poff + (int64_t)r * P.nchunks + v.chunk] = tot;
+        for (int g = 0; g < nr; ++g) {
+          if (!live[g]) continue;  // uniform over the block
+          const double tot = block_sum((double)acc[g], red);
+          if (threadIdx.x == 0) part[P.poff + (int64_t)(r0 + g) * P.nchunks + v.chunk] = tot;
+        }
       }
     }
   }
