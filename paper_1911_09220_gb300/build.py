@@ -48,12 +48,17 @@ def _defines():
     one candidate elements-per-block table for every element type (used to
     re-measure the choice); unset or `measured` gives the measured table.
     FEM_BATCH_MIN_BLOCKS=k compiles the batched FP32 element kernel for k
-    resident 256-thread blocks per SM (its register budget)."""
+    resident 256-thread blocks per SM (its register budget). FEM_F32_TC=1
+    runs the x-direction stages of the FP32 diffusion kernel (p >= 4) on the
+    tensor cores (split-TF32 mma, k_tc.cuh); FEM_F32_TC=2 with single TF32
+    products."""
     t = os.environ.get("FEM_NE_TABLE", "measured")
     out = {"large": ["-DFEM_NE_TABLE=1"], "small": ["-DFEM_NE_TABLE=2"]}.get(t, [])
     mb = os.environ.get("FEM_BATCH_MIN_BLOCKS")
     if mb:
         out.append(f"-DFEM_BATCH_MIN_BLOCKS={int(mb)}")
+    if os.environ.get("FEM_F32_TC") in ("1", "2"):
+        out.append(f"-DFEM_F32_TC={os.environ['FEM_F32_TC']}")
     return out
 
 

@@ -589,6 +589,8 @@ struct Lines {
   }
 };
 
+#include "k_tc.cuh"
+
 // ------------------------------------------------------------- drivers ----
 // A block works on elements e0 .. e0 + nel - 1. The gather and stage S3
 // (Q*Q lines per element) keep one plane of Q*Q threads per element, thread
@@ -612,7 +614,11 @@ __device__ __forceinline__ void diffusion_block(int tid, int e0, int nel, const 
   const size_t ev = valid ? (size_t)(e0 + el) : 0;
   gather_x<T, D1, Q, TX>(t, valid, e2l + ev * ND, x, Ln::X(sm + el * SE), Ln::XP);
   __syncthreads();
-  if (tid < nel * N1) Ln::d1(tid % N1, sm + (tid / N1) * SE);
+  if constexpr (use_tc<T, D1>()) {
+    tc_s1<D1, Q>(nel * N1, sm, tid, blockDim.x * blockDim.y * blockDim.z);
+  } else {
+    if (tid < nel * N1) Ln::d1(tid % N1, sm + (tid / N1) * SE);
+  }
   __syncthreads();
   if (tid < nel * N2) Ln::d2(tid % N2, sm + (tid / N2) * SE);
   __syncthreads();
@@ -623,7 +629,11 @@ __device__ __forceinline__ void diffusion_block(int tid, int e0, int nel, const 
   __syncthreads();
   if (tid < nel * N2) Ln::d4(tid % N2, sm + (tid / N2) * SE);
   __syncthreads();
-  if (tid < nel * N1) Ln::template d5<TX>(tid % N1, sm + (tid / N1) * SE, ye + (size_t)(e0 + tid / N1) * ND);
+  if constexpr (use_tc<T, D1>()) {
+    tc_s5<D1, Q, TX>(nel * N1, sm, tid, blockDim.x * blockDim.y * blockDim.z, ye + (size_t)e0 * ND);
+  } else {
+    if (tid < nel * N1) Ln::template d5<TX>(tid % N1, sm + (tid / N1) * SE, ye + (size_t)(e0 + tid / N1) * ND);
+  }
 }
 
 // Convection (beta . grad u, v): forward stages of diffusion, backward
