@@ -25,8 +25,23 @@ constexpr int ne_elast() {
   return ne;
 }
 
+// Resident blocks per SM the kernel is compiled for. The FP32 kernel is
+// latency-bound; for p <= 5 it trades registers for up to four resident
+// blocks where its shared memory allows (measured at ~4.2e6 vector entries:
+// element kernel p = 1 0.590 -> 0.520 ms, p = 2 0.203 -> 0.162, p = 3
+// 0.134 -> 0.126, p = 5 0.136 -> 0.097; p = 4 is limited by shared memory,
+// and p >= 6 ran 2-4 % slower with the cap, so it keeps the compiler's
+// register choice).
+template <typename T, int D1, int Q, int NE>
+constexpr int elast_min_blocks() {
+  if (!std::is_same<T, float>::value || D1 > 6) return 1;
+  constexpr int bytes = NE * 3 * ElemSmem<T, D1, Q>::SE * (int)sizeof(T);
+  constexpr int fit = (227 * 1024) / (bytes + 1024);
+  return fit < 4 ? (fit > 0 ? fit : 1) : 4;
+}
+
 template <typename T, int D1, int Q, int NE, typename TX>
-__global__ void __launch_bounds__(Q * Q * NE)
+__global__ void __launch_bounds__(Q * Q * NE, (elast_min_blocks<T, D1, Q, NE>()))
 k_elasticity_apply(const int* __restrict__ skip, int ne, int64_t ndof, const int32_t* __restrict__ e2l,
                    const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye) {
   constexpr int NQ = Q * Q * Q, NT = Q * Q * NE;
