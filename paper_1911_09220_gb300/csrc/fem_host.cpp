@@ -461,11 +461,16 @@ static fem_status space_finish(fem_space* sp, fem_space** out) {
   fem_status st = dev_alloc(&sp->d_e2l, sp->e2l.size());
   if (st == FEM_OK) st = dev_alloc(&sp->d_l2e_off, off.size());
   if (st == FEM_OK) st = dev_alloc(&sp->d_l2e_idx, idx.size());
+  std::vector<int32_t> pos(idx.size());
+  for (size_t j = 0; j < idx.size(); ++j) pos[idx[j]] = (int32_t)j;
+  if (st == FEM_OK) st = dev_alloc(&sp->d_pos, pos.size());
   if (st == FEM_OK) st = dev_alloc(&sp->d_nodes, sp->nodes.size());
   if (st == FEM_OK) {
     cudaError_t e1 = cudaMemcpy(sp->d_e2l, sp->e2l.data(), sizeof(int32_t) * sp->e2l.size(), cudaMemcpyHostToDevice);
     cudaError_t e2 = cudaMemcpy(sp->d_l2e_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice);
     cudaError_t e3 = cudaMemcpy(sp->d_l2e_idx, idx.data(), sizeof(int32_t) * idx.size(), cudaMemcpyHostToDevice);
+    if (e3 == cudaSuccess)
+      e3 = cudaMemcpy(sp->d_pos, pos.data(), sizeof(int32_t) * pos.size(), cudaMemcpyHostToDevice);
     cudaError_t e4 = cudaMemcpy(sp->d_nodes, sp->nodes.data(), sizeof(double) * sp->nodes.size(), cudaMemcpyHostToDevice);
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess)
       st = fem_fail(FEM_ECUDA, "fem_space_create: upload of restriction maps failed");
@@ -483,6 +488,7 @@ extern "C" void fem_space_destroy(fem_space* sp) {
   dev_free(sp->d_e2l);
   dev_free(sp->d_l2e_off);
   dev_free(sp->d_l2e_idx);
+  dev_free(sp->d_pos);
   dev_free(sp->d_nodes);
   dev_free(sp->d_gBn);
   delete sp;

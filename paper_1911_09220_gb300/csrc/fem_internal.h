@@ -77,6 +77,7 @@ struct fem_space {
   int32_t* d_e2l = nullptr;     // [ne][nd]
   int32_t* d_l2e_off = nullptr; // [ndof+1]
   int32_t* d_l2e_idx = nullptr; // [ne*nd], e*nd + k
+  int32_t* d_pos = nullptr;     // [ne*nd]: position of slot e*nd + k in the inverse map (DOF-sorted order)
   double* d_nodes = nullptr;
   double* d_gBn = nullptr;      // order-k geometry basis at this space's GLL nodes [D1][k+1]
   int gBn_k = 0;
@@ -173,13 +174,20 @@ int fem_kernels_supported(int p, int q1d);
 fem_status fem_launch_setup(const fem_form* f, cudaStream_t s);
 fem_status fem_launch_qpoint_coords(const fem_form* f, double* xq, cudaStream_t s);
 fem_status fem_launch_dof_coords(const fem_space* sp, double* out, cudaStream_t s);
+// sorted: the element kernel writes each E-vector value at its slot's
+// position in the inverse map (DOF-sorted order, space->d_pos) instead of
+// e*nd + k, and the scatter then reads each DOF's values contiguously. The
+// two halves must agree; fem_sorted_evec(f) says whether a form supports it
+// (3D scalar forms), and both launchers fall back to the element-major order
+// otherwise.
 fem_status fem_launch_apply_element(const fem_form* f, int dtype, const void* x, void* ye,
-                                    cudaStream_t s, const int* skip = nullptr);
+                                    cudaStream_t s, const int* skip = nullptr, bool sorted = false);
 // scatter: y_i = sum over inverse map of ye; ess rows (if mask) get x_i (constrained).
 // pdot != nullptr: also writes per-block partial sums of x_i*y_i to pdot[nblocks].
 fem_status fem_launch_scatter(const fem_form* f, int dtype, const void* ye, void* y,
                               const uint8_t* mask, const void* xess, double* pdot,
-                              int nblocks, cudaStream_t s, const int* skip = nullptr);
+                              int nblocks, cudaStream_t s, const int* skip = nullptr, bool sorted = false);
+bool fem_sorted_evec(const fem_form* f);
 fem_status fem_launch_zero_ess(const fem_form* f, int dtype, const void* x, void* xz,
                                cudaStream_t s);
 fem_status fem_launch_diag_element(const fem_form* f, double* ye, cudaStream_t s);

@@ -21,7 +21,7 @@ fem_status prepare_smem(K kernel, size_t bytes) {
 
 template <typename T, int P, int Q, typename TX = T>
 fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G, const TX* x, TX* ye,
-                           const int* skip, cudaStream_t s) {
+                           const int* skip, cudaStream_t s, const int32_t* pos) {
   constexpr int D1 = P + 1, NE = ne_for<T>(Q);
   const int ne = (int)f->space->ne;
   const dim3 block(Q, Q, NE);
@@ -32,15 +32,15 @@ fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G
   if (f->kind == FEM_CONVECTION) {
     auto kern = k_convection_apply<T, D1, Q, NE, TX>;
     FEM_TRY(prepare_smem(kern, bytes));
-    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, x, ye);
+    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, pos, D, x, ye);
   } else if (f->kind == FEM_DIFFUSION) {
     auto kern = k_diffusion_apply<T, D1, Q, NE, TX>;
     FEM_TRY(prepare_smem(kern, bytes));
-    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, x, ye);
+    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, pos, D, x, ye);
   } else {
     auto kern = k_mass_apply<T, D1, Q, NE, TX>;
     FEM_TRY(prepare_smem(kern, bytes));
-    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, D, x, ye);
+    kern<<<grid, block, bytes, s>>>(skip, ne, f->space->d_e2l, pos, D, x, ye);
   }
   FEM_LAUNCHED();
   return FEM_OK;
@@ -54,11 +54,14 @@ fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G
 // every load stays coalesced across the warp. VD = 3: vector entries
 // i in [0, 3 ndof), component c = i / ndof of DOF i - c ndof, whose slots
 // are read from the E-vector component ye + c * nend.
+// sorted (VD = 1 only): ye is the DOF-sorted E-vector, DOF i's values at
+// ye[off[i] .. off[i+1]) in the inverse map's order (no idx reads; the same
+// sums in the same order).
 template <typename T, int VD = 1>
 __global__ void k_scatter(const int* __restrict__ skip, int64_t ndof, const int32_t* __restrict__ off,
                           const int32_t* __restrict__ idx, const T* __restrict__ ye, T* __restrict__ y,
                           const uint8_t* __restrict__ mask, const T* __restrict__ xin,
-                          double* __restrict__ pdot, int64_t nend = 0) {
+                          double* __restrict__ pdot, int64_t nend = 0, bool sorted = false) {
   constexpr int kU = 4;
   __shared__ double red[32];
   if (skip && *skip) return;
@@ -87,13 +90,21 @@ __global__ void k_scatter(const int* __restrict__ skip, int64_t ndof, const int3
     T sum[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) sum[u] = 0;
-    for (int j = 0; j < len; ++j) {
-      int32_t sl[kU];
+    if (VD == 1 && sorted) {
+      for (int j = 0; j < len; ++j) {
 #pragma unroll
-      for (int u = 0; u < kU; ++u) sl[u] = a[u] + j < b[u] ? __ldg(idx + a[u] + j) : -1;
+        for (int u = 0; u < kU; ++u)
+          if (a[u] + j < b[u]) sum[u] += __ldg(ye + a[u] + j);
+      }
+    } else {
+      for (int j = 0; j < len; ++j) {
+        int32_t sl[kU];
 #pragma unroll
-      for (int u = 0; u < kU; ++u)
-        if (sl[u] >= 0) sum[u] += __ldg(yc[u] + sl[u]);
+        for (int u = 0; u < kU; ++u) sl[u] = a[u] + j < b[u] ? __ldg(idx + a[u] + j) : -1;
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+          if (sl[u] >= 0) sum[u] += __ldg(yc[u] + sl[u]);
+      }
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
@@ -176,22 +187,27 @@ fem_status fem_form_ensure_df64(const fem_form* fc, cudaStream_t s) {
   return FEM_OK;
 }
 
+bool fem_sorted_evec(const fem_form* f) {
+  return f->space->mesh->dim == 3 && f->kind != FEM_ELASTICITY && f->space->d_pos != nullptr;
+}
+
 fem_status fem_launch_apply_element(const fem_form* f, int dtype, const void* x, void* ye, cudaStream_t s,
-                                    const int* skip) {
+                                    const int* skip, bool sorted) {
   if (f->space->mesh->dim == 2) return fem_launch_apply_element_2d(f, dtype, x, ye, s, skip);
   if (f->kind == FEM_ELASTICITY) return fem_launch_apply_elasticity(f, dtype, x, ye, s, skip);
   const int p = f->space->p, q = f->q1d;
+  const int32_t* pos = sorted && fem_sorted_evec(f) ? f->space->d_pos : nullptr;
   if (dtype == FEM_F64) {
 #define X(P, Q)                                                                                            \
   if (p == P && q == Q)                                                                                    \
-    return launch_apply_pq<double, P, Q>(f, f->d_D, f->d_B, f->d_G, (const double*)x, (double*)ye, skip, s);
+    return launch_apply_pq<double, P, Q>(f, f->d_D, f->d_B, f->d_G, (const double*)x, (double*)ye, skip, s, pos);
     FEM_FOR_EACH_PQ(X)
 #undef X
   } else if (dtype == FEM_F32) {
     FEM_TRY(fem_form_ensure_f32(f, s));
 #define X(P, Q)                                                                                            \
   if (p == P && q == Q)                                                                                    \
-    return launch_apply_pq<float, P, Q>(f, f->d_D32, f->d_B32, f->d_G32, (const float*)x, (float*)ye, skip, s);
+    return launch_apply_pq<float, P, Q>(f, f->d_D32, f->d_B32, f->d_G32, (const float*)x, (float*)ye, skip, s, pos);
     FEM_FOR_EACH_PQ(X)
 #undef X
   } else if (dtype == FEM_DF64) {
@@ -201,7 +217,7 @@ fem_status fem_launch_apply_element(const fem_form* f, int dtype, const void* x,
     const df64* G = reinterpret_cast<const df64*>(f->d_Gdf);
 #define X(P, Q)                                                                                            \
   if (p == P && q == Q)                                                                                    \
-    return launch_apply_pq<df64, P, Q, double>(f, D, B, G, (const double*)x, (double*)ye, skip, s);
+    return launch_apply_pq<df64, P, Q, double>(f, D, B, G, (const double*)x, (double*)ye, skip, s, pos);
     FEM_FOR_EACH_PQ(X)
 #undef X
   } else {
@@ -211,8 +227,10 @@ fem_status fem_launch_apply_element(const fem_form* f, int dtype, const void* x,
 }
 
 fem_status fem_launch_scatter(const fem_form* f, int dtype, const void* ye, void* y, const uint8_t* mask,
-                              const void* xin, double* pdot, int nblocks, cudaStream_t s, const int* skip) {
+                              const void* xin, double* pdot, int nblocks, cudaStream_t s, const int* skip,
+                              bool sorted) {
   const fem_space* sp = f->space;
+  sorted = sorted && fem_sorted_evec(f);
   const int grid = nblocks > 0 ? nblocks : fem_scatter_blocks(fem_form_len(f));
   const int64_t nend = sp->ne * (int64_t)sp->nd;
   if (f->vdim == 3) {
@@ -224,10 +242,10 @@ fem_status fem_launch_scatter(const fem_form* f, int dtype, const void* ye, void
                                                (float*)y, mask, (const float*)xin, pdot, nend);
   } else if (dtype == FEM_F64) {
     k_scatter<double><<<grid, 256, 0, s>>>(skip, sp->ndof, sp->d_l2e_off, sp->d_l2e_idx, (const double*)ye,
-                                           (double*)y, mask, (const double*)xin, pdot);
+                                           (double*)y, mask, (const double*)xin, pdot, 0, sorted);
   } else {
     k_scatter<float><<<grid, 256, 0, s>>>(skip, sp->ndof, sp->d_l2e_off, sp->d_l2e_idx, (const float*)ye,
-                                          (float*)y, mask, (const float*)xin, pdot);
+                                          (float*)y, mask, (const float*)xin, pdot, 0, sorted);
   }
   FEM_LAUNCHED();
   return FEM_OK;
@@ -290,9 +308,9 @@ extern "C" fem_status fem_apply(const fem_form* fc, int dtype, const void* x, vo
     FEM_TRY(ensure_work(f, vt, (size_t)fem_form_len(f)));
     void* xz = vt == FEM_F64 ? (void*)f->d_work64 : (void*)f->d_work32;
     FEM_TRY(fem_launch_zero_ess(f, vt, x, xz, s));
-    FEM_TRY(fem_launch_apply_element(f, dtype, xz, ye, s));
-    return fem_launch_scatter(f, vt, ye, y, f->d_ess_mask, x, nullptr, 0, s);
+    FEM_TRY(fem_launch_apply_element(f, dtype, xz, ye, s, nullptr, true));
+    return fem_launch_scatter(f, vt, ye, y, f->d_ess_mask, x, nullptr, 0, s, nullptr, true);
   }
-  FEM_TRY(fem_launch_apply_element(f, dtype, x, ye, s));
-  return fem_launch_scatter(f, vt, ye, y, nullptr, nullptr, nullptr, 0, s);
+  FEM_TRY(fem_launch_apply_element(f, dtype, x, ye, s, nullptr, true));
+  return fem_launch_scatter(f, vt, ye, y, nullptr, nullptr, nullptr, 0, s, nullptr, true);
 }

@@ -45,7 +45,7 @@ struct BlockSmem {
 // per SM while the dependent map -> x gather stayed exposed.)
 template <typename T, int D1, int Q, int NE, typename TX>
 __global__ void __launch_bounds__(Q * Q * NE)
-k_diffusion_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
+k_diffusion_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l, const int32_t* __restrict__ pos,
                   const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye) {
   constexpr int NQ = Q * Q * Q;
   if (skip && *skip) return;  // a captured solver iteration after convergence
@@ -55,12 +55,12 @@ k_diffusion_apply(const int* __restrict__ skip, int ne, const int32_t* __restric
   const int e0 = blockIdx.x * NE;
   const int nel = min(NE, ne - e0);
   if (tid == 0) l2_prefetch_range(Dq + (size_t)e0 * 6 * NQ, sizeof(T) * (size_t)nel * 6 * NQ);
-  diffusion_block<T, D1, Q, TX>(tid, e0, nel, e2l, Dq, sm, x, ye);
+  diffusion_block<T, D1, Q, TX>(tid, e0, nel, e2l, Dq, sm, x, ye, pos);
 }
 
 template <typename T, int D1, int Q, int NE, typename TX>
 __global__ void __launch_bounds__(Q * Q * NE)
-k_mass_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
+k_mass_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l, const int32_t* __restrict__ pos,
              const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye) {
   constexpr int NQ = Q * Q * Q;
   if (skip && *skip) return;
@@ -70,12 +70,12 @@ k_mass_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e
   const int e0 = blockIdx.x * NE;
   const int nel = min(NE, ne - e0);
   if (tid == 0) l2_prefetch_range(Dq + (size_t)e0 * NQ, sizeof(T) * (size_t)nel * NQ);
-  mass_block<T, D1, Q, TX>(tid, e0, nel, e2l, Dq, sm, x, ye);
+  mass_block<T, D1, Q, TX>(tid, e0, nel, e2l, Dq, sm, x, ye, pos);
 }
 
 template <typename T, int D1, int Q, int NE, typename TX>
 __global__ void __launch_bounds__(Q * Q * NE)
-k_convection_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l,
+k_convection_apply(const int* __restrict__ skip, int ne, const int32_t* __restrict__ e2l, const int32_t* __restrict__ pos,
                    const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye) {
   constexpr int NQ = Q * Q * Q;
   if (skip && *skip) return;
@@ -85,5 +85,5 @@ k_convection_apply(const int* __restrict__ skip, int ne, const int32_t* __restri
   const int e0 = blockIdx.x * NE;
   const int nel = min(NE, ne - e0);
   if (tid == 0) l2_prefetch_range(Dq + (size_t)e0 * 3 * NQ, sizeof(T) * (size_t)nel * 3 * NQ);
-  convection_block<T, D1, Q, TX>(tid, e0, nel, e2l, Dq, sm, x, ye);
+  convection_block<T, D1, Q, TX>(tid, e0, nel, e2l, Dq, sm, x, ye, pos);
 }

@@ -418,9 +418,10 @@ struct Lines {
       ob[dy * RU + t] = fe_norm(u1[dy] + u2[dy]);
     }
   }
-  // S5: line t = (dz, dy) along qx -> out[t * D1 + dx]
+  // S5: line t = (dz, dy) along qx -> out[t * D1 + dx], or out[pos[t * D1 +
+  // dx]] when pos (the element's DOF-sorted slot positions) is given
   template <typename TX>
-  __device__ static void d5(int t, T* s, TX* __restrict__ out) {
+  __device__ static void d5(int t, T* s, TX* __restrict__ out, const int32_t* __restrict__ pos = nullptr) {
     const int dz = t / D1, dy = t % D1;
     T ua[Q], ub[Q], y1[D1], y2[D1];
     const T *sa = UA(s) + dy * RU + dz * Q, *sb = UB(s) + dy * RU + dz * Q;
@@ -431,8 +432,13 @@ struct Lines {
     }
     eo_line<T, D1, Q, -1, GT>(ua, y1);
     eo_line<T, D1, Q, 1, BT>(ub, y2);
+    if (pos) {
 #pragma unroll
-    for (int dx = 0; dx < D1; ++dx) fe_store(&out[t * D1 + dx], y1[dx] + y2[dx]);
+      for (int dx = 0; dx < D1; ++dx) fe_store(&out[__ldg(pos + t * D1 + dx)], y1[dx] + y2[dx]);
+    } else {
+#pragma unroll
+      for (int dx = 0; dx < D1; ++dx) fe_store(&out[t * D1 + dx], y1[dx] + y2[dx]);
+    }
   }
 
   // ---- convection: the diffusion forward stages (d1, d2), then one value
@@ -577,15 +583,20 @@ struct Lines {
     for (int dy = 0; dy < D1; ++dy) oa[dy * RU + t] = ua[dy];
   }
   template <typename TX>
-  __device__ static void m5(int t, T* s, TX* __restrict__ out) {
+  __device__ static void m5(int t, T* s, TX* __restrict__ out, const int32_t* __restrict__ pos = nullptr) {
     const int dz = t / D1, dy = t % D1;
     T ua[Q], y[D1];
     const T* sa = UA(s) + dy * RU + dz * Q;
 #pragma unroll
     for (int q = 0; q < Q; ++q) ua[q] = sa[q];
     eo_line<T, D1, Q, 1, BT>(ua, y);
+    if (pos) {
 #pragma unroll
-    for (int dx = 0; dx < D1; ++dx) fe_store(&out[t * D1 + dx], y[dx]);
+      for (int dx = 0; dx < D1; ++dx) fe_store(&out[__ldg(pos + t * D1 + dx)], y[dx]);
+    } else {
+#pragma unroll
+      for (int dx = 0; dx < D1; ++dx) fe_store(&out[t * D1 + dx], y[dx]);
+    }
   }
 };
 
@@ -600,12 +611,13 @@ struct Lines {
 // elements onto the lowest thread ids, so warps are full and the arithmetic
 // pipe issues no instructions for idle lanes. Element e's DOF list is
 // e2l + e*D1^3, its D block Dq + e*NC*Q^3 (NC = 6 diffusion, 1 mass), its
-// E-vector slice ye + e*D1^3; its slab sm + el*SE. Every thread of the block
-// must call the driver (it contains __syncthreads).
+// E-vector slice ye + e*D1^3 (or, with pos, the positions pos[e*D1^3 + k]
+// of the DOF-sorted E-vector ye); its slab sm + el*SE. Every thread of the
+// block must call the driver (it contains __syncthreads).
 template <typename T, int D1, int Q, typename TX = T>
 __device__ __forceinline__ void diffusion_block(int tid, int e0, int nel, const int32_t* __restrict__ e2l,
                                                 const T* __restrict__ Dq, T* sm, const TX* __restrict__ x,
-                                                TX* __restrict__ ye) {
+                                                TX* __restrict__ ye, const int32_t* __restrict__ pos = nullptr) {
   using Ln = Lines<T, D1, Q>;
   constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
   constexpr int N1 = D1 * D1, N2 = D1 * Q;
@@ -630,9 +642,12 @@ __device__ __forceinline__ void diffusion_block(int tid, int e0, int nel, const 
   if (tid < nel * N2) Ln::d4(tid % N2, sm + (tid / N2) * SE);
   __syncthreads();
   if constexpr (use_tc<T, D1>()) {
-    tc_s5<D1, Q, TX>(nel * N1, sm, tid, blockDim.x * blockDim.y * blockDim.z, ye + (size_t)e0 * ND);
-  } else {
-    if (tid < nel * N1) Ln::template d5<TX>(tid % N1, sm + (tid / N1) * SE, ye + (size_t)(e0 + tid / N1) * ND);
+    tc_s5<D1, Q, TX>(nel * N1, sm, tid, blockDim.x * blockDim.y * blockDim.z, ye + (pos ? 0 : (size_t)e0 * ND),
+                     pos ? pos + (size_t)e0 * ND : nullptr);
+  } else if (tid < nel * N1) {
+    const size_t eo = (size_t)(e0 + tid / N1) * ND;
+    if (pos) Ln::template d5<TX>(tid % N1, sm + (tid / N1) * SE, ye, pos + eo);
+    else Ln::template d5<TX>(tid % N1, sm + (tid / N1) * SE, ye + eo);
   }
 }
 
@@ -641,7 +656,7 @@ __device__ __forceinline__ void diffusion_block(int tid, int e0, int nel, const 
 template <typename T, int D1, int Q, typename TX = T>
 __device__ __forceinline__ void convection_block(int tid, int e0, int nel, const int32_t* __restrict__ e2l,
                                                  const T* __restrict__ Dq, T* sm, const TX* __restrict__ x,
-                                                 TX* __restrict__ ye) {
+                                                 TX* __restrict__ ye, const int32_t* __restrict__ pos = nullptr) {
   using Ln = Lines<T, D1, Q>;
   constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
   constexpr int N1 = D1 * D1, N2 = D1 * Q;
@@ -661,13 +676,17 @@ __device__ __forceinline__ void convection_block(int tid, int e0, int nel, const
   __syncthreads();
   if (tid < nel * N2) Ln::m4(tid % N2, sm + (tid / N2) * SE);
   __syncthreads();
-  if (tid < nel * N1) Ln::template m5<TX>(tid % N1, sm + (tid / N1) * SE, ye + (size_t)(e0 + tid / N1) * ND);
+  if (tid < nel * N1) {
+    const size_t eo = (size_t)(e0 + tid / N1) * ND;
+    if (pos) Ln::template m5<TX>(tid % N1, sm + (tid / N1) * SE, ye, pos + eo);
+    else Ln::template m5<TX>(tid % N1, sm + (tid / N1) * SE, ye + eo);
+  }
 }
 
 template <typename T, int D1, int Q, typename TX = T>
 __device__ __forceinline__ void mass_block(int tid, int e0, int nel, const int32_t* __restrict__ e2l,
                                            const T* __restrict__ Dq, T* sm, const TX* __restrict__ x,
-                                           TX* __restrict__ ye) {
+                                           TX* __restrict__ ye, const int32_t* __restrict__ pos = nullptr) {
   using Ln = Lines<T, D1, Q>;
   constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
   constexpr int N1 = D1 * D1, N2 = D1 * Q;
@@ -687,7 +706,11 @@ __device__ __forceinline__ void mass_block(int tid, int e0, int nel, const int32
   __syncthreads();
   if (tid < nel * N2) Ln::m4(tid % N2, sm + (tid / N2) * SE);
   __syncthreads();
-  if (tid < nel * N1) Ln::template m5<TX>(tid % N1, sm + (tid / N1) * SE, ye + (size_t)(e0 + tid / N1) * ND);
+  if (tid < nel * N1) {
+    const size_t eo = (size_t)(e0 + tid / N1) * ND;
+    if (pos) Ln::template m5<TX>(tid % N1, sm + (tid / N1) * SE, ye, pos + eo);
+    else Ln::template m5<TX>(tid % N1, sm + (tid / N1) * SE, ye + eo);
+  }
 }
 
 // Linear elasticity on the three components of a vector H1 field

@@ -575,8 +575,8 @@ template <typename T>
 fem_status level_apply(const MgLevel& L, const T* x, T* y, const int* skip, cudaStream_t s, double* pdot = nullptr,
                        int nb = 0) {
   const int dt = std::is_same<T, float>::value ? FEM_F32 : FEM_F64;
-  FEM_TRY(fem_launch_apply_element(L.f, dt, x, L.f->d_ye, s, skip));
-  return fem_launch_scatter(L.f, dt, L.f->d_ye, y, L.f->d_ess_mask, x, pdot, nb, s, skip);
+  FEM_TRY(fem_launch_apply_element(L.f, dt, x, L.f->d_ye, s, skip, true));
+  return fem_launch_scatter(L.f, dt, L.f->d_ye, y, L.f->d_ess_mask, x, pdot, nb, s, skip, true);
 }
 
 int vblocks(int64_t n) { return grid_for(n, 256); }
@@ -585,8 +585,8 @@ int vblocks(int64_t n) { return grid_for(n, 256); }
 // essential DOFs): the lambda estimate needs no more than its ~1e-13
 // accuracy, and it runs on the FP32 pipe at about 4x the FP64 apply's rate.
 fem_status level_apply_df(const MgLevel& L, const double* x, double* y, const int* skip, cudaStream_t s) {
-  FEM_TRY(fem_launch_apply_element(L.f, FEM_DF64, x, L.f->d_ye, s, skip));
-  return fem_launch_scatter(L.f, FEM_F64, L.f->d_ye, y, L.f->d_ess_mask, x, nullptr, 0, s, skip);
+  FEM_TRY(fem_launch_apply_element(L.f, FEM_DF64, x, L.f->d_ye, s, skip, true));
+  return fem_launch_scatter(L.f, FEM_F64, L.f->d_ye, y, L.f->d_ess_mask, x, nullptr, 0, s, skip, true);
 }
 
 // Dispatch of the interpolation kernel over the compiled (D1f, D1c) pairs.
@@ -1053,13 +1053,13 @@ fem_status fcg_iteration(fem_mg* m, int dtype, double* x, double* r, double* rol
     float *p32 = m->w32, *q32 = m->w32 + n;
     k_p_to_f32<<<vblocks(n), 256, 0, s>>>(n, p, p32, skip);
     FEM_LAUNCHED();
-    FEM_TRY(fem_launch_apply_element(L.f, FEM_F32, p32, L.f->d_ye, s, skip));
-    FEM_TRY(fem_launch_scatter(L.f, FEM_F32, L.f->d_ye, q32, L.f->d_ess_mask, p32, m->part, nb, s, skip));
+    FEM_TRY(fem_launch_apply_element(L.f, FEM_F32, p32, L.f->d_ye, s, skip, true));
+    FEM_TRY(fem_launch_scatter(L.f, FEM_F32, L.f->d_ye, q32, L.f->d_ess_mask, p32, m->part, nb, s, skip, true));
     k_q_to_f64<<<vblocks(n), 256, 0, s>>>(n, q32, q, skip);
     FEM_LAUNCHED();
   } else {
-    FEM_TRY(fem_launch_apply_element(L.f, dtype, p, L.f->d_ye, s, skip));
-    FEM_TRY(fem_launch_scatter(L.f, FEM_F64, L.f->d_ye, q, L.f->d_ess_mask, p, m->part, nb, s, skip));
+    FEM_TRY(fem_launch_apply_element(L.f, dtype, p, L.f->d_ye, s, skip, true));
+    FEM_TRY(fem_launch_scatter(L.f, FEM_F64, L.f->d_ye, q, L.f->d_ess_mask, p, m->part, nb, s, skip, true));
   }
   k_fg_alpha<<<1, kRed, 0, s>>>(m->sc, m->part, nb);
   k_fg_update<<<nb, 256, 0, s>>>(n, m->sc, x, r, rold, p, q, m->part);
@@ -1078,8 +1078,8 @@ fem_status fine_residual(fem_mg* m, const double* b, const double* x, double* r,
                          cudaStream_t s) {
   const MgLevel& L = m->lv[0];
   FEM_TRY(fem_launch_zero_ess(L.f, FEM_F64, x, t, s));
-  FEM_TRY(fem_launch_apply_element(L.f, FEM_F64, t, L.f->d_ye, s));
-  FEM_TRY(fem_launch_scatter(L.f, FEM_F64, L.f->d_ye, y, L.f->d_ess_mask, x, nullptr, 0, s));
+  FEM_TRY(fem_launch_apply_element(L.f, FEM_F64, t, L.f->d_ye, s, nullptr, true));
+  FEM_TRY(fem_launch_scatter(L.f, FEM_F64, L.f->d_ye, y, L.f->d_ess_mask, x, nullptr, 0, s, nullptr, true));
   k_resid<<<m->nb, 256, 0, s>>>(L.n, b, y, r, m->part);
   k_sum1<<<1, kRed, 0, s>>>(m->part, m->nb, m->part + 3 * m->nb);
   FEM_LAUNCHED();

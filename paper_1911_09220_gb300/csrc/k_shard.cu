@@ -249,8 +249,8 @@ fem_status apply_raw(const fem_shard* sh, const fem_form* f, const double* x, do
     FEM_LAUNCHED();
     xin = xz;
   }
-  FEM_TRY(fem_launch_apply_element(f, FEM_F64, xin, f->d_ye, s));
-  FEM_TRY(fem_launch_scatter(f, FEM_F64, f->d_ye, y, nullptr, nullptr, nullptr, 0, s));
+  FEM_TRY(fem_launch_apply_element(f, FEM_F64, xin, f->d_ye, s, nullptr, true));
+  FEM_TRY(fem_launch_scatter(f, FEM_F64, f->d_ye, y, nullptr, nullptr, nullptr, 0, s, nullptr, true));
   FEM_TRY(halo_sum(sh, f->vdim, y, comm, s));
   if (constrained) {
     k_sh_ess_rows<<<grid_for(n, kT), kT, 0, s>>>(n, f->d_ess_mask, x, 0.0, y);

@@ -429,8 +429,8 @@ fem_status cg_iteration(const fem_form* f, const Work& w, int dtype, T* x, T* r,
                         cudaStream_t s) {
   const int* skip = &w.sc->done;
   const int vt = std::is_same<T, float>::value ? FEM_F32 : FEM_F64;
-  FEM_TRY(fem_launch_apply_element(f, dtype, p, f->d_ye, s, skip));
-  FEM_TRY(fem_launch_scatter(f, vt, f->d_ye, q, f->d_ess_mask, p, w.part, w.nb, s, skip));
+  FEM_TRY(fem_launch_apply_element(f, dtype, p, f->d_ye, s, skip, true));
+  FEM_TRY(fem_launch_scatter(f, vt, f->d_ye, q, f->d_ess_mask, p, w.part, w.nb, s, skip, true));
   k_cg_update<T><<<w.nb, kRedThreads, 0, s>>>(w.n, w.sc, x, r, z, p, q, diag, w.part, w.part + w.nb, w.nb);
   k_cg_direction<T><<<w.nb, kRedThreads, 0, s>>>(w.n, w.sc, z, p, w.part + w.nb, w.nb);
   FEM_LAUNCHED();
@@ -497,8 +497,8 @@ fem_status cg_loop(fem_form* f, const Work& w, int dtype, T* x, T* r, T* z, T* p
 fem_status true_residual(fem_form* f, const Work& w, const double* b, const double* x, double* r, double* out,
                          cudaStream_t s) {
   FEM_TRY(fem_launch_zero_ess(f, FEM_F64, x, w.t, s));
-  FEM_TRY(fem_launch_apply_element(f, FEM_F64, w.t, f->d_ye, s));
-  FEM_TRY(fem_launch_scatter(f, FEM_F64, f->d_ye, w.q, f->d_ess_mask, x, nullptr, 0, s));
+  FEM_TRY(fem_launch_apply_element(f, FEM_F64, w.t, f->d_ye, s, nullptr, true));
+  FEM_TRY(fem_launch_scatter(f, FEM_F64, f->d_ye, w.q, f->d_ess_mask, x, nullptr, 0, s, nullptr, true));
   k_residual<double><<<w.nb, 256, 0, s>>>(w.n, b, w.q, r, w.part);
   k_sum_to<<<1, kRedThreads, 0, s>>>(w.part, w.nb, out);
   FEM_LAUNCHED();

@@ -131,9 +131,10 @@ __device__ __forceinline__ void tc_s1(int nlines, float* sm, int tid, int nthrea
 }
 
 // S5 over nlines = nel * D1^2 lines (line L: element L / D1^2, t = L % D1^2 =
-// (dz, dy)); output out[el * D1^3 + t * D1 + dx].
+// (dz, dy)); output out[el * D1^3 + t * D1 + dx] (with pos: at out[pos[...]]).
 template <int D1, int Q, typename TX>
-__device__ __forceinline__ void tc_s5(int nlines, float* sm, int tid, int nthreads, TX* __restrict__ out) {
+__device__ __forceinline__ void tc_s5(int nlines, float* sm, int tid, int nthreads, TX* __restrict__ out,
+                                      const int32_t* __restrict__ pos = nullptr) {
   using L = ElemSmem<float, D1, Q>;
   constexpr int N1 = D1 * D1, ND = D1 * D1 * D1, SE = L::SE, RU = L::RU, RT = L::RT;
   constexpr int KS = (2 * Q + 7) / 8, NT = (D1 + 7) / 8, OFF = tab_off(D1, Q);
@@ -185,8 +186,10 @@ __device__ __forceinline__ void tc_s5(int nlines, float* sm, int tid, int nthrea
       for (int h = 0; h < 2; ++h) {
         const int dx = nt * 8 + 2 * c + h;
         if (dx >= D1) continue;
-        if (v0) fe_store(&out[(size_t)(L0 / N1) * ND + (L0 % N1) * D1 + dx], acc[nt][h]);
-        if (v1) fe_store(&out[(size_t)(L1 / N1) * ND + (L1 % N1) * D1 + dx], acc[nt][2 + h]);
+        const size_t i0 = (size_t)(L0 / N1) * ND + (L0 % N1) * D1 + dx;
+        const size_t i1 = (size_t)(L1 / N1) * ND + (L1 % N1) * D1 + dx;
+        if (v0) fe_store(&out[pos ? (size_t)__ldg(pos + i0) : i0], acc[nt][h]);
+        if (v1) fe_store(&out[pos ? (size_t)__ldg(pos + i1) : i1], acc[nt][2 + h]);
       }
     }
   }
