@@ -177,9 +177,10 @@ fem_status fem_launch_dof_coords(const fem_space* sp, double* out, cudaStream_t 
 // sorted: the element kernel writes each E-vector value at its slot's
 // position in the inverse map (DOF-sorted order, space->d_pos) instead of
 // e*nd + k, and the scatter then reads each DOF's values contiguously. The
-// two halves must agree; fem_sorted_evec(f) says whether a form supports it
-// (3D scalar forms), and both launchers fall back to the element-major order
-// otherwise.
+// two halves must agree; fem_sorted_evec(f, dtype) says whether a form uses
+// it (3D forms whose E-vector exceeds half the L2; a vector form sorts each
+// component's block), and both launchers fall back to the element-major
+// order otherwise. dtype: the element dtype (FEM_DF64 E-vectors are float64).
 fem_status fem_launch_apply_element(const fem_form* f, int dtype, const void* x, void* ye,
                                     cudaStream_t s, const int* skip = nullptr, bool sorted = false);
 // scatter: y_i = sum over inverse map of ye; ess rows (if mask) get x_i (constrained).
@@ -187,14 +188,14 @@ fem_status fem_launch_apply_element(const fem_form* f, int dtype, const void* x,
 fem_status fem_launch_scatter(const fem_form* f, int dtype, const void* ye, void* y,
                               const uint8_t* mask, const void* xess, double* pdot,
                               int nblocks, cudaStream_t s, const int* skip = nullptr, bool sorted = false);
-bool fem_sorted_evec(const fem_form* f);
+bool fem_sorted_evec(const fem_form* f, int dtype);
 fem_status fem_launch_zero_ess(const fem_form* f, int dtype, const void* x, void* xz,
                                cudaStream_t s);
 fem_status fem_launch_diag_element(const fem_form* f, double* ye, cudaStream_t s);
 // Elasticity element kernel (k_elasticity.cu) and its diagonal helper: the
 // 6-component matrix of component c at every point, [ne][q1d^3][6].
 fem_status fem_launch_apply_elasticity(const fem_form* f, int dtype, const void* x, void* ye, cudaStream_t s,
-                                       const int* skip);
+                                       const int* skip, bool sorted = false);
 fem_status fem_launch_elasticity_diag_D(const fem_form* f, int c, double* Dc, cudaStream_t s);
 fem_status fem_launch_rhs_element(const fem_form* f, const double* fq, double* ye,
                                   cudaStream_t s);

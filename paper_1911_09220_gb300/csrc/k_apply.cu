@@ -54,9 +54,9 @@ fem_status launch_apply_pq(const fem_form* f, const T* D, const T* B, const T* G
 // every load stays coalesced across the warp. VD = 3: vector entries
 // i in [0, 3 ndof), component c = i / ndof of DOF i - c ndof, whose slots
 // are read from the E-vector component ye + c * nend.
-// sorted (VD = 1 only): ye is the DOF-sorted E-vector, DOF i's values at
-// ye[off[i] .. off[i+1]) in the inverse map's order (no idx reads; the same
-// sums in the same order).
+// sorted: ye is the DOF-sorted E-vector, DOF i's values at ye[off[i] ..
+// off[i+1]) (component c's block at ye + c * nend for VD = 3) in the
+// inverse map's order: no idx reads, the same sums in the same order.
 template <typename T, int VD = 1>
 __global__ void k_scatter(const int* __restrict__ skip, int64_t ndof, const int32_t* __restrict__ off,
                           const int32_t* __restrict__ idx, const T* __restrict__ ye, T* __restrict__ y,
@@ -90,11 +90,11 @@ __global__ void k_scatter(const int* __restrict__ skip, int64_t ndof, const int3
     T sum[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) sum[u] = 0;
-    if (VD == 1 && sorted) {
+    if (sorted) {
       for (int j = 0; j < len; ++j) {
 #pragma unroll
         for (int u = 0; u < kU; ++u)
-          if (a[u] + j < b[u]) sum[u] += __ldg(ye + a[u] + j);
+          if (a[u] + j < b[u]) sum[u] += __ldg(yc[u] + a[u] + j);
       }
     } else {
       for (int j = 0; j < len; ++j) {
@@ -187,16 +187,23 @@ fem_status fem_form_ensure_df64(const fem_form* fc, cudaStream_t s) {
   return FEM_OK;
 }
 
-bool fem_sorted_evec(const fem_form* f) {
-  return f->space->mesh->dim == 3 && f->kind != FEM_ELASTICITY && f->space->d_pos != nullptr;
+// The sorted order pays where the E-vector does not stay in L2 between the
+// element kernel and the scatter (measured: FP32 diffusion at p = 4 with a
+// 131 MB E-vector, scatter 0.110 -> 0.048 ms; FP32 elasticity with 18-25 MB
+// E-vectors 3-4 % slower sorted, the pos reads and scattered stores costing
+// more than the gathers that hit L2): half the L2 size is the threshold.
+bool fem_sorted_evec(const fem_form* f, int dtype) {
+  constexpr double kMinBytes = 64.0 * 1024 * 1024;
+  const double bytes = (double)f->vdim * f->space->ne * f->space->nd * (dtype == FEM_F32 ? 4 : 8);
+  return f->space->mesh->dim == 3 && f->space->d_pos != nullptr && bytes > kMinBytes;
 }
 
 fem_status fem_launch_apply_element(const fem_form* f, int dtype, const void* x, void* ye, cudaStream_t s,
                                     const int* skip, bool sorted) {
   if (f->space->mesh->dim == 2) return fem_launch_apply_element_2d(f, dtype, x, ye, s, skip);
-  if (f->kind == FEM_ELASTICITY) return fem_launch_apply_elasticity(f, dtype, x, ye, s, skip);
+  if (f->kind == FEM_ELASTICITY) return fem_launch_apply_elasticity(f, dtype, x, ye, s, skip, sorted);
   const int p = f->space->p, q = f->q1d;
-  const int32_t* pos = sorted && fem_sorted_evec(f) ? f->space->d_pos : nullptr;
+  const int32_t* pos = sorted && fem_sorted_evec(f, dtype) ? f->space->d_pos : nullptr;
   if (dtype == FEM_F64) {
 #define X(P, Q)                                                                                            \
   if (p == P && q == Q)                                                                                    \
@@ -230,16 +237,16 @@ fem_status fem_launch_scatter(const fem_form* f, int dtype, const void* ye, void
                               const void* xin, double* pdot, int nblocks, cudaStream_t s, const int* skip,
                               bool sorted) {
   const fem_space* sp = f->space;
-  sorted = sorted && fem_sorted_evec(f);
+  sorted = sorted && fem_sorted_evec(f, dtype);
   const int grid = nblocks > 0 ? nblocks : fem_scatter_blocks(fem_form_len(f));
   const int64_t nend = sp->ne * (int64_t)sp->nd;
   if (f->vdim == 3) {
     if (dtype == FEM_F64)
       k_scatter<double, 3><<<grid, 256, 0, s>>>(skip, sp->ndof, sp->d_l2e_off, sp->d_l2e_idx, (const double*)ye,
-                                                (double*)y, mask, (const double*)xin, pdot, nend);
+                                                (double*)y, mask, (const double*)xin, pdot, nend, sorted);
     else
       k_scatter<float, 3><<<grid, 256, 0, s>>>(skip, sp->ndof, sp->d_l2e_off, sp->d_l2e_idx, (const float*)ye,
-                                               (float*)y, mask, (const float*)xin, pdot, nend);
+                                               (float*)y, mask, (const float*)xin, pdot, nend, sorted);
   } else if (dtype == FEM_F64) {
     k_scatter<double><<<grid, 256, 0, s>>>(skip, sp->ndof, sp->d_l2e_off, sp->d_l2e_idx, (const double*)ye,
                                            (double*)y, mask, (const double*)xin, pdot, 0, sorted);

@@ -10,7 +10,9 @@
 // blocks) stride over the item lists, which are sorted by decreasing cost. An
 // element item applies its tile to all nrhs right-hand sides in turn, so each
 // D block streams from HBM once and is re-read from L1 / L2 for the other
-// right-hand sides. All launches of an apply (or of `check_every` CG
+// right-hand sides. The E-vector is DOF-sorted (each element value at its
+// slot's position in the inverse map), so the scatter reads each DOF's
+// values contiguously. All launches of an apply (or of `check_every` CG
 // iterations) are captured into one CUDA graph and replayed.
 //
 // System s = (problem i, rhs r) = i * nrhs + r. Batched vectors are
@@ -40,6 +42,7 @@ struct BProb {
   const int32_t* e2l;
   const int32_t* off;
   const int32_t* idx;
+  const int32_t* pos;   // DOF-sorted E-vector positions of the slots
   const double* D64;
   const float* D32;
   const double* B64;
@@ -86,9 +89,9 @@ __device__ __noinline__ void run_tile(const BProb& P, int e0, int tile, int nrhs
     const T* x = X + P.xoff + (int64_t)r * P.ndof;
     T* ye = YE + P.yeoff + (int64_t)r * P.ne * ND;
     if (P.kind == FEM_DIFFUSION)
-      diffusion_block<T, D1, Q>(tid, e0, nel, P.e2l, D, sm, x, ye);
+      diffusion_block<T, D1, Q>(tid, e0, nel, P.e2l, D, sm, x, ye, P.pos);
     else
-      mass_block<T, D1, Q>(tid, e0, nel, P.e2l, D, sm, x, ye);
+      mass_block<T, D1, Q>(tid, e0, nel, P.e2l, D, sm, x, ye, P.pos);
   }
 }
 
@@ -120,11 +123,12 @@ k_batch_element(const BProb* __restrict__ probs, const BItem* __restrict__ items
   }
 }
 
-// y = G^T ye (inverse map), optional constraint (y_ess = xin_ess) and partial
-// dot products xin . y per (system, chunk). Each DOF's inverse-map entries
-// are read once for a group of up to kRG right-hand sides (their E-vector
-// slots are the same, kRG * ne * nd apart); the sums run in the same order
-// as a one-right-hand-side scatter.
+// y = G^T ye, optional constraint (y_ess = xin_ess) and partial dot products
+// xin . y per (system, chunk). The element kernel writes the E-vector in
+// DOF-sorted order (each slot at its position in the inverse map), so DOF
+// i's values are ye[off[i] .. off[i+1]) for every right-hand side (ne * nd
+// apart); a group of up to kRG right-hand sides shares the offsets. The sums
+// run in the inverse map's order.
 constexpr int kRG = 8;
 
 template <typename T>
@@ -154,10 +158,9 @@ k_batch_scatter(const BProb* __restrict__ probs, const VItem* __restrict__ items
 #pragma unroll
         for (int g = 0; g < kRG; ++g) sum[g] = 0;
         for (int32_t k = a; k < b; ++k) {
-          const int32_t sl = P.idx[k];
 #pragma unroll
           for (int g = 0; g < kRG; ++g)
-            if (live[g]) sum[g] += ye[g * es + sl];
+            if (live[g]) sum[g] += ye[g * es + k];
         }
         const bool ess = constrained && P.mask && P.mask[i];
 #pragma unroll
@@ -705,7 +708,7 @@ extern "C" fem_status fem_batch_create(const fem_form* const* forms, int nprob, 
     P.xoff = (int64_t)nrhs * ndof_sum;
     P.yeoff = (int64_t)nrhs * ye_sum;
     P.poff = (int64_t)nrhs * chunk_sum;
-    P.e2l = sp->d_e2l; P.off = sp->d_l2e_off; P.idx = sp->d_l2e_idx;
+    P.e2l = sp->d_e2l; P.off = sp->d_l2e_off; P.idx = sp->d_l2e_idx; P.pos = sp->d_pos;
     P.D64 = f->d_D; P.D32 = f->d_D32;
     P.B64 = f->d_B; P.G64 = f->d_G; P.B32 = f->d_B32; P.G32 = f->d_G32;
     P.mask = f->d_ess_mask;

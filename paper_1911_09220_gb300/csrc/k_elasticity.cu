@@ -43,7 +43,8 @@ constexpr int elast_min_blocks() {
 template <typename T, int D1, int Q, int NE, typename TX>
 __global__ void __launch_bounds__(Q * Q * NE, (elast_min_blocks<T, D1, Q, NE>()))
 k_elasticity_apply(const int* __restrict__ skip, int ne, int64_t ndof, const int32_t* __restrict__ e2l,
-                   const T* __restrict__ Dq, const TX* __restrict__ x, TX* __restrict__ ye) {
+                   const int32_t* __restrict__ pos, const T* __restrict__ Dq, const TX* __restrict__ x,
+                   TX* __restrict__ ye) {
   constexpr int NQ = Q * Q * Q, NT = Q * Q * NE;
   if (skip && *skip) return;  // a captured solver iteration after convergence
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -52,18 +53,20 @@ k_elasticity_apply(const int* __restrict__ skip, int ne, int64_t ndof, const int
   const int e0 = blockIdx.x * NE;
   const int nel = min(NE, ne - e0);
   if (tid == 0) l2_prefetch_range(Dq + (size_t)e0 * 12 * NQ, sizeof(T) * (size_t)nel * 12 * NQ);
-  elasticity_block<T, D1, Q, NT, TX>(tid, e0, nel, ne, ndof, e2l, Dq, sm, x, ye);
+  elasticity_block<T, D1, Q, NT, TX>(tid, e0, nel, ne, ndof, e2l, Dq, sm, x, ye, pos);
 }
 
 template <typename T, int P, int Q, typename TX = T>
-fem_status launch(const fem_form* f, const T* D, const TX* x, TX* ye, const int* skip, cudaStream_t s) {
+fem_status launch(const fem_form* f, const T* D, const TX* x, TX* ye, const int* skip, cudaStream_t s,
+                  const int32_t* pos) {
   constexpr int D1 = P + 1, NE = ne_elast<T, D1, Q>();
   const int ne = (int)f->space->ne;
   const size_t bytes = sizeof(T) * (size_t)NE * 3 * ElemSmem<T, D1, Q>::SE;
   auto kern = k_elasticity_apply<T, D1, Q, NE, TX>;
   if (bytes > 48 * 1024)
     FEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  kern<<<(ne + NE - 1) / NE, dim3(Q, Q, NE), bytes, s>>>(skip, ne, f->space->ndof, f->space->d_e2l, D, x, ye);
+  kern<<<(ne + NE - 1) / NE, dim3(Q, Q, NE), bytes, s>>>(skip, ne, f->space->ndof, f->space->d_e2l, pos, D, x,
+                                                         ye);
   FEM_LAUNCHED();
   return FEM_OK;
 }
@@ -73,24 +76,25 @@ fem_status launch(const fem_form* f, const T* D, const TX* x, TX* ye, const int*
 fem_status fem_elast_tables_init() { return fem_tables_ensure(); }
 
 fem_status fem_launch_apply_elasticity(const fem_form* f, int dtype, const void* x, void* ye, cudaStream_t s,
-                                       const int* skip) {
+                                       const int* skip, bool sorted) {
   const int p = f->space->p, q = f->q1d;
+  const int32_t* pos = sorted && fem_sorted_evec(f, dtype) ? f->space->d_pos : nullptr;
   if (dtype == FEM_F64) {
 #define X(P, Q) \
-  if (p == P && q == Q) return launch<double, P, Q>(f, f->d_D, (const double*)x, (double*)ye, skip, s);
+  if (p == P && q == Q) return launch<double, P, Q>(f, f->d_D, (const double*)x, (double*)ye, skip, s, pos);
     FEM_FOR_EACH_PQ(X)
 #undef X
   } else if (dtype == FEM_F32) {
     FEM_TRY(fem_form_ensure_f32(f, s));
 #define X(P, Q) \
-  if (p == P && q == Q) return launch<float, P, Q>(f, f->d_D32, (const float*)x, (float*)ye, skip, s);
+  if (p == P && q == Q) return launch<float, P, Q>(f, f->d_D32, (const float*)x, (float*)ye, skip, s, pos);
     FEM_FOR_EACH_PQ(X)
 #undef X
   } else if (dtype == FEM_DF64) {
     FEM_TRY(fem_form_ensure_df64(f, s));
     const df64* D = reinterpret_cast<const df64*>(f->d_Ddf);
 #define X(P, Q) \
-  if (p == P && q == Q) return launch<df64, P, Q, double>(f, D, (const double*)x, (double*)ye, skip, s);
+  if (p == P && q == Q) return launch<df64, P, Q, double>(f, D, (const double*)x, (double*)ye, skip, s, pos);
     FEM_FOR_EACH_PQ(X)
 #undef X
   } else {

@@ -722,7 +722,8 @@ __device__ __forceinline__ void mass_block(int tid, int e0, int nel, const int32
 template <typename T, int D1, int Q, int NT, typename TX = T>
 __device__ __forceinline__ void elasticity_block(int tid, int e0, int nel, int ne, int64_t ndof,
                                                  const int32_t* __restrict__ e2l, const T* __restrict__ Dq, T* sm,
-                                                 const TX* __restrict__ x, TX* __restrict__ ye) {
+                                                 const TX* __restrict__ x, TX* __restrict__ ye,
+                                                 const int32_t* __restrict__ pos = nullptr) {
   using Ln = Lines<T, D1, Q>;
   constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
   constexpr int N1 = D1 * D1, N2 = D1 * Q, XP = Ln::XP;
@@ -754,7 +755,10 @@ __device__ __forceinline__ void elasticity_block(int tid, int e0, int nel, int n
   __syncthreads();
   for (int i = tid; i < 3 * nel * N1; i += NT) {
     const int sl = i / N1, l = sl / 3, c = sl % 3;
-    Ln::template d5<TX>(i % N1, sm + sl * SE, ye + ((size_t)c * ne + e0 + l) * ND);
+    if (pos)  // component c's DOF-sorted E-vector at ye + c ne ND
+      Ln::template d5<TX>(i % N1, sm + sl * SE, ye + (size_t)c * ne * ND, pos + (size_t)(e0 + l) * ND);
+    else
+      Ln::template d5<TX>(i % N1, sm + sl * SE, ye + ((size_t)c * ne + e0 + l) * ND);
   }
 }
 
