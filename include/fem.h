@@ -111,8 +111,8 @@ fem_status fem_mesh_create(const double* coords_host, int64_t nv,
  * coords_host [nv][2] float64; quad_host [ne][4] int32, local vertex order
  * 0:(0,0) 1:(1,0) 2:(1,1) 3:(0,1) (counter-clockwise on [0,1]^2, bilinear
  * map). Everything built on it takes the 2D shapes stated below ((p+1)^2
- * local DOFs, q1d^2 points, [..][2] coordinates). Not accepted by
- * fem_batch_create (FEM_EUNSUPPORTED). Same ownership and errors as
+ * local DOFs, q1d^2 points, [..][2] coordinates); batches may mix
+ * quadrilateral and hexahedral problems. Same ownership and errors as
  * fem_mesh_create. */
 fem_status fem_mesh2d_create(const double* coords_host, int64_t nv,
                              const int32_t* quad_host, int64_t ne, fem_mesh** out);
@@ -345,7 +345,9 @@ fem_status fem_compliance(const fem_form* form, const double* b, const double* u
  * work items, each applying its tile to all nrhs right-hand sides (D streams
  * from HBM once per nrhs); the scatter is one persistent kernel over
  * (problem, DOF chunk) items. Applies and CG iterations run as CUDA graphs.
- * Orders p = 1..6 (FEM_EUNSUPPORTED otherwise). */
+ * Problems on hexahedral and quadrilateral meshes may be mixed (a 2D tile
+ * puts one element on each row of q1d threads). Orders p = 1..6
+ * (FEM_EUNSUPPORTED otherwise). */
 fem_status fem_batch_create(const fem_form* const* forms, int nprob, int nrhs, void* stream,
                             fem_batch** out);
 void fem_batch_destroy(fem_batch* batch);
@@ -366,12 +368,14 @@ fem_status fem_batch_apply(fem_batch* batch, int dtype, const void* X, void* Y, 
  * may be NULL). Synchronises stream. Errors: FEM_ENOCONV, FEM_EBREAKDOWN. */
 fem_status fem_batch_solve(fem_batch* batch, const double* B, double* X, const fem_solve_opts* opts,
                            int* iters_host, double* relres_host, void* stream);
-/* Autotuner: for every (p, q) in the batch, times the batched apply with
- * candidate element tiles (elements per work item) and keeps the fastest;
+/* Autotuner: for every (p, q) of the batch's hexahedral problems, times the
+ * batched apply with candidate element tiles (elements per work item) and
+ * keeps the fastest (quadrilateral problems keep floor(256 / q1d));
  * results are read from / written to the line-per-entry JSON cache at
  * cache_path (NULL: no cache), keyed by device name, dtype and (p, q). */
 fem_status fem_batch_tune(fem_batch* batch, int dtype, const char* cache_path, void* stream);
-/* Current element tiles: tiles_host [18], entry 2p + (q - p - 1). */
+/* Current element tiles of the hexahedral problems: tiles_host [18], entry
+ * 2p + (q - p - 1). */
 fem_status fem_batch_tiles(const fem_batch* batch, int* tiles_host);
 
 /* ---- p-multigrid preconditioner (Sec. 5.2 names matrix-free p-multigrid

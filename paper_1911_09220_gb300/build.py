@@ -57,6 +57,9 @@ def _defines():
     mb = os.environ.get("FEM_BATCH_MIN_BLOCKS")
     if mb:
         out.append(f"-DFEM_BATCH_MIN_BLOCKS={int(mb)}")
+    mb64 = os.environ.get("FEM_BATCH_MIN_BLOCKS64")
+    if mb64:
+        out.append(f"-DFEM_BATCH_MIN_BLOCKS64={int(mb64)}")
     if os.environ.get("FEM_F32_TC") in ("1", "2"):
         out.append(f"-DFEM_F32_TC={os.environ['FEM_F32_TC']}")
     return out

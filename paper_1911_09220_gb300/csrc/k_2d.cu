@@ -20,6 +20,7 @@
 #include "fem_internal.h"
 #include "k_common.cuh"
 #include "k_element.cuh"
+#include "k_element2d.cuh"
 
 namespace {
 
@@ -131,133 +132,17 @@ __global__ void k_dof_coords_2d(int64_t ndof, int D1, const double* __restrict__
 }
 
 // ------------------------------------------------------------ element ------
-template <int D1, int Q>
-struct Smem2 {
-  static constexpr int XP = D1 | 1;  // padded x rows of X
-  static constexpr int YP = D1 | 1;  // padded y rows of BX, GX
-  static constexpr int QP = Q | 1;   // padded qx rows of T0, T1
-  static constexpr int SE = D1 * XP + 2 * Q * YP + 2 * D1 * QP;  // per element, in T
-};
-
-// Elements per block: rows of Q threads, about 128 threads per block.
-__host__ __device__ constexpr int ne2(int Q) { return Q <= 3 ? 42 : Q <= 4 ? 32 : Q <= 6 ? 21 : Q <= 8 ? 16 : 12; }
-
 template <typename T, int D1, int Q, int NE, typename TX, bool DIFF>
 __global__ void __launch_bounds__(Q * NE) k_apply_2d(const int* __restrict__ skip, int ne,
                                                      const int32_t* __restrict__ e2l, const T* __restrict__ Dq,
                                                      const TX* __restrict__ x, TX* __restrict__ ye) {
   if (skip && *skip) return;
-  using L = Smem2<D1, Q>;
-  constexpr int XP = L::XP, YP = L::YP, QP = L::QP, ND = D1 * D1, NQ = Q * Q;
-  constexpr int BF = eo_off(D1, Q, 0), GF = eo_off(D1, Q, 1), BT = eo_off(D1, Q, 2), GT = eo_off(D1, Q, 3);
-  // slab offsets: X [y][XP], BX, GX [qx][YP], T0, T1 [dy][QP]
-  constexpr int OBX = D1 * XP, OGX = OBX + Q * YP, OT0 = OGX + Q * YP, OT1 = OT0 + D1 * QP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  const int t = threadIdx.x, el = threadIdx.y, tid = t + Q * el;
-  const int64_t e0 = (int64_t)blockIdx.x * NE, e = e0 + el;
+  const int t = threadIdx.x, el = threadIdx.y;
+  const int64_t e0 = (int64_t)blockIdx.x * NE;
   const int nel = (int)min((int64_t)NE, ne - e0);
-  const bool valid = e < ne;
-  if (valid) {
-    T* sX = sm + el * L::SE;
-    const int32_t* map = e2l + e * ND;
-    for (int k = t; k < ND; k += Q) sX[(k / D1) * XP + k % D1] = fe_from<T>(__ldg(x + __ldg(map + k)));
-  }
-  __syncthreads();
-  // S1 and S3 have D1 lines per element: the lines of all nel elements are
-  // packed onto the lowest thread ids (full warps); S2 has Q lines per
-  // element and keeps one row of Q threads per element.
-  if (tid < nel * D1) {  // S1: line y along x
-    T* s = sm + (tid / D1) * L::SE;
-    const int t = tid % D1;
-    T *sX = s, *sBX = s + OBX, *sGX = s + OGX;
-    T xr[D1], bx[Q], gx[Q];
-#pragma unroll
-    for (int d = 0; d < D1; ++d) xr[d] = sX[t * XP + d];
-    if constexpr (DIFF) {
-      T ev[(D1 + 1) / 2], od[D1 / 2 > 0 ? D1 / 2 : 1];
-      eo_split<T, D1>(xr, ev, od);
-      eo_apply<T, Q, D1, 1, BF>(ev, od, bx);
-      eo_apply<T, Q, D1, -1, GF>(ev, od, gx);
-#pragma unroll
-      for (int qx = 0; qx < Q; ++qx) {
-        sBX[qx * YP + t] = bx[qx];
-        sGX[qx * YP + t] = gx[qx];
-      }
-    } else {
-      eo_line<T, Q, D1, 1, BF>(xr, bx);
-#pragma unroll
-      for (int qx = 0; qx < Q; ++qx) sBX[qx * YP + t] = bx[qx];
-    }
-  }
-  __syncthreads();
-  {  // S2: line qx along y, D at every point, back along y (t < Q always)
-    const int qx = t;
-    T* s = sm + el * L::SE;
-    T *sBX = s + OBX, *sGX = s + OGX, *sT0 = s + OT0, *sT1 = s + OT1;
-    T br[D1], t0[D1];
-#pragma unroll
-    for (int d = 0; d < D1; ++d) br[d] = sBX[qx * YP + d];
-    if constexpr (DIFF) {
-      T gr[D1], g0[Q], g1[Q], t1[D1];
-#pragma unroll
-      for (int d = 0; d < D1; ++d) gr[d] = sGX[qx * YP + d];
-      eo_line<T, Q, D1, 1, BF>(gr, g0);   // d/dx
-      eo_line<T, Q, D1, -1, GF>(br, g1);  // d/dy
-      const T* Dp = Dq + ((size_t)e * NQ + qx) * 3;
-#pragma unroll
-      for (int qy = 0; qy < Q; ++qy) {
-        T d00 = 0, d01 = 0, d11 = 0;
-        if (valid) {
-          d00 = fe_ldg(Dp + qy * Q * 3);
-          d01 = fe_ldg(Dp + qy * Q * 3 + 1);
-          d11 = fe_ldg(Dp + qy * Q * 3 + 2);
-        }
-        const T a0 = g0[qy], a1 = g1[qy];
-        g0[qy] = fe_norm(d00 * a0 + d01 * a1);
-        g1[qy] = fe_norm(d01 * a0 + d11 * a1);
-      }
-      eo_line<T, D1, Q, 1, BT>(g0, t0);
-      eo_line<T, D1, Q, -1, GT>(g1, t1);
-#pragma unroll
-      for (int dy = 0; dy < D1; ++dy) {
-        sT0[dy * QP + qx] = t0[dy];
-        sT1[dy * QP + qx] = t1[dy];
-      }
-    } else {
-      T u[Q];
-      eo_line<T, Q, D1, 1, BF>(br, u);
-      const T* Dp = Dq + (size_t)e * NQ + qx;
-#pragma unroll
-      for (int qy = 0; qy < Q; ++qy) u[qy] = valid ? fe_norm(fe_ldg(Dp + qy * Q) * u[qy]) : T(0);
-      eo_line<T, D1, Q, 1, BT>(u, t0);
-#pragma unroll
-      for (int dy = 0; dy < D1; ++dy) sT0[dy * QP + qx] = t0[dy];
-    }
-  }
-  __syncthreads();
-  if (tid < nel * D1) {  // S3: line dy along qx
-    const int el3 = tid / D1, t = tid % D1;
-    T* s = sm + el3 * L::SE;
-    const T *sT0 = s + OT0, *sT1 = s + OT1;
-    T a0[Q], y1[D1];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) a0[q] = sT0[t * QP + q];
-    TX* out = ye + (e0 + el3) * ND + t * D1;
-    if constexpr (DIFF) {
-      T a1[Q], y2[D1];
-#pragma unroll
-      for (int q = 0; q < Q; ++q) a1[q] = sT1[t * QP + q];
-      eo_line<T, D1, Q, -1, GT>(a0, y1);
-      eo_line<T, D1, Q, 1, BT>(a1, y2);
-#pragma unroll
-      for (int dx = 0; dx < D1; ++dx) fe_store(out + dx, y1[dx] + y2[dx]);
-    } else {
-      eo_line<T, D1, Q, 1, BT>(a0, y1);
-#pragma unroll
-      for (int dx = 0; dx < D1; ++dx) fe_store(out + dx, y1[dx]);
-    }
-  }
+  quad_block<T, D1, Q, TX, DIFF>(t, el, e0, nel, e2l, Dq, sm, x, ye);
 }
 
 // Element diagonal, one thread per (element, local DOF i = ix + D1 iy):

@@ -29,15 +29,18 @@
 #include "fem_internal.h"
 #include "k_common.cuh"
 #include "k_element.cuh"
+#include "k_element2d.cuh"
 
 namespace {
 
 constexpr int kBT = 256;     // threads of the persistent element / vector blocks
 constexpr int kCH = 2048;    // DOFs per vector work item
 constexpr int kMaxP = 8;
+constexpr int kTiles3 = (kMaxP + 1) * 2;  // tiles[0, kTiles3): hexahedra; then quadrilaterals
 
 struct BProb {
   int p, q, kind, ne, nd, nq, nchunks, sys0;
+  int dim;              // 3: hexahedra, 2: quadrilaterals
   int64_t ndof, xoff, yeoff, poff;
   const int32_t* e2l;
   const int32_t* off;
@@ -76,6 +79,28 @@ __device__ __forceinline__ const float* diag_of<float>(const BProb& P) { return 
 // Shared-memory slabs a block needs for order p (q = p + 2 or p + 1): one per
 // (partial) thread plane of the 256-thread block.
 __host__ __device__ constexpr int planes_for(int Q) { return (kBT + Q * Q - 1) / (Q * Q); }
+// 2D: one element per row of Q threads.
+__host__ __device__ constexpr int rows_for(int Q) { return (kBT + Q - 1) / Q; }
+
+// A 2D tile: rows of Q threads, element el of the tile on row el (tile <=
+// floor(256 / Q)), all nrhs right-hand sides in turn; DOF-sorted output.
+template <typename T, int D1, int Q>
+__device__ __noinline__ void run_tile_2d(const BProb& P, int e0, int tile, int nrhs, const int* __restrict__ done,
+                                         const T* __restrict__ X, T* __restrict__ YE, T* sm) {
+  constexpr int ND = D1 * D1;
+  const int tid = threadIdx.x, el = tid / Q, t = tid % Q;
+  const int nel = min(tile, P.ne - e0);
+  const T* D = D_of<T>(P);
+  for (int r = 0; r < nrhs; ++r) {
+    if (done && done[P.sys0 + r]) continue;  // uniform over the block
+    const T* x = X + P.xoff + (int64_t)r * P.ndof;
+    T* ye = YE + P.yeoff + (int64_t)r * P.ne * ND;
+    if (P.kind == FEM_DIFFUSION)
+      quad_block<T, D1, Q, T, true>(t, el, e0, nel, P.e2l, D, sm, x, ye, P.pos);
+    else
+      quad_block<T, D1, Q, T, false>(t, el, e0, nel, P.e2l, D, sm, x, ye, P.pos);
+  }
+}
 
 template <typename T, int D1, int Q>
 __device__ __noinline__ void run_tile(const BProb& P, int e0, int tile, int nrhs, const int* __restrict__ done,
@@ -95,13 +120,22 @@ __device__ __noinline__ void run_tile(const BProb& P, int e0, int tile, int nrhs
   }
 }
 
-// Resident blocks per SM the FP32 element kernel is compiled for (its
-// register budget: 65536 / (kBT * blocks)); build option FEM_BATCH_MIN_BLOCKS.
+// Resident blocks per SM the element kernels are compiled for (register
+// budget 65536 / (kBT * blocks); the largest variant sets a persistent
+// kernel's register count): FP32 4 blocks (64 registers; 16.1 -> 14.6 ms for
+// 256 problems x 8 right-hand sides), FP64 2 blocks (128 registers instead
+// of 190; 251.2 -> 239.9 ms). Build options FEM_BATCH_MIN_BLOCKS and
+// FEM_BATCH_MIN_BLOCKS64.
 #ifndef FEM_BATCH_MIN_BLOCKS
 #define FEM_BATCH_MIN_BLOCKS 4
 #endif
+#ifndef FEM_BATCH_MIN_BLOCKS64
+#define FEM_BATCH_MIN_BLOCKS64 2
+#endif
 template <typename T>
-constexpr int batch_min_blocks() { return std::is_same<T, float>::value ? FEM_BATCH_MIN_BLOCKS : 1; }
+constexpr int batch_min_blocks() {
+  return std::is_same<T, float>::value ? FEM_BATCH_MIN_BLOCKS : FEM_BATCH_MIN_BLOCKS64;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kBT, batch_min_blocks<T>())
@@ -115,11 +149,18 @@ k_batch_element(const BProb* __restrict__ probs, const BItem* __restrict__ items
     const BProb& P = probs[item.prob];
     const int p = P.p, q = P.q;
     __syncthreads();  // the previous item is done with the slabs
-    const int tile = tiles[p * 2 + (q - p - 1)];
+    const int tile = tiles[(P.dim == 2 ? kTiles3 : 0) + p * 2 + (q - p - 1)];
+    if (P.dim == 2) {
+#define CASE(PP, QQ) \
+  if (p == PP && q == QQ) run_tile_2d<T, PP + 1, QQ>(P, item.e0, tile, nrhs, done, X, YE, sm);
+      FEM_FOR_EACH_PQ_BATCH(CASE)
+#undef CASE
+    } else {
 #define CASE(PP, QQ) \
   if (p == PP && q == QQ) run_tile<T, PP + 1, QQ>(P, item.e0, tile, nrhs, done, X, YE, sm);
-    FEM_FOR_EACH_PQ_BATCH(CASE)
+      FEM_FOR_EACH_PQ_BATCH(CASE)
 #undef CASE
+    }
   }
 }
 
@@ -460,7 +501,14 @@ __global__ void k_cast_vec(int64_t n, const double* __restrict__ a, float* __res
 }
 
 template <typename T>
-size_t slab_bytes(int p, int q) {
+size_t slab_bytes(int p, int q, int dim) {
+  if (dim == 2) {
+#define X(P, Q) \
+  if (p == P && q == Q) return sizeof(T) * (size_t)rows_for(Q) * (size_t)Smem2<P + 1, Q>::SE;
+    FEM_FOR_EACH_PQ_BATCH(X)
+#undef X
+    return 0;
+  }
 #define X(P, Q) \
   if (p == P && q == Q) return sizeof(T) * (size_t)planes_for(Q) * (size_t)ElemSmem<T, P + 1, Q>::SE;
   FEM_FOR_EACH_PQ_BATCH(X)
@@ -484,8 +532,9 @@ struct fem_batch {
   int nitems = 0;
   VItem* d_vitems = nullptr;
   int nvitems = 0;
-  int* d_tiles = nullptr;       // [kMaxP + 1][2]: elements per item for (p, q = p+1 / p+2)
+  int* d_tiles = nullptr;       // hexahedra [kMaxP + 1][2], then quadrilaterals: elements per item for (p, q = p+1 / p+2)
   int h_tiles[(kMaxP + 1) * 2];
+  int h_tiles2[(kMaxP + 1) * 2];  // quadrilaterals: floor(256 / q) (rows of q threads)
   double* d_ye = nullptr;       // E-vector scratch for all systems (float uses the front half)
   double* d_diag = nullptr;
   float* d_diag32 = nullptr;
@@ -509,8 +558,8 @@ namespace {
 fem_status setup_grids(fem_batch* b) {
   size_t s64 = 0, s32 = 0;
   for (const BProb& P : b->hprobs) {
-    s64 = std::max(s64, slab_bytes<double>(P.p, P.q));
-    s32 = std::max(s32, slab_bytes<float>(P.p, P.q));
+    s64 = std::max(s64, slab_bytes<double>(P.p, P.q, P.dim));
+    s32 = std::max(s32, slab_bytes<float>(P.p, P.q, P.dim));
   }
   b->smem64 = s64;
   b->smem32 = s32;
@@ -532,8 +581,8 @@ fem_status build_items(fem_batch* b) {
   std::vector<std::pair<double, BItem>> el;
   for (int i = 0; i < b->nprob; ++i) {
     const BProb& P = b->hprobs[i];
-    const int tile = b->h_tiles[P.p * 2 + (P.q - P.p - 1)];
-    const double cost = (double)tile * std::pow((double)P.q, 4.0) * (P.kind == FEM_DIFFUSION ? 3.0 : 1.0);
+    const int tile = (P.dim == 2 ? b->h_tiles2 : b->h_tiles)[P.p * 2 + (P.q - P.p - 1)];
+    const double cost = (double)tile * std::pow((double)P.q, P.dim + 1.0) * (P.kind == FEM_DIFFUSION ? 3.0 : 1.0);
     for (int e0 = 0; e0 < P.ne; e0 += tile) el.push_back({cost, BItem{i, e0}});
   }
   std::stable_sort(el.begin(), el.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
@@ -549,6 +598,7 @@ fem_status build_items(fem_batch* b) {
 fem_status upload_probs(fem_batch* b) {
   FEM_CUDA(cudaMemcpy(b->d_probs, b->hprobs.data(), sizeof(BProb) * b->hprobs.size(), cudaMemcpyHostToDevice));
   FEM_CUDA(cudaMemcpy(b->d_tiles, b->h_tiles, sizeof(b->h_tiles), cudaMemcpyHostToDevice));
+  FEM_CUDA(cudaMemcpy(b->d_tiles + kTiles3, b->h_tiles2, sizeof(b->h_tiles2), cudaMemcpyHostToDevice));
   return FEM_OK;
 }
 
@@ -673,6 +723,7 @@ extern "C" fem_status fem_batch_create(const fem_form* const* forms, int nprob, 
     for (int j = 0; j < 2; ++j) {
       const int q = p + 1 + j;
       b->h_tiles[p * 2 + j] = std::max(1, kBT / std::max(1, q * q));
+      b->h_tiles2[p * 2 + j] = std::max(1, kBT / std::max(1, q));
     }
   int64_t ndof_sum = 0, ye_sum = 0, chunk_sum = 0;
   std::vector<VItem> vitems;
@@ -692,16 +743,14 @@ extern "C" fem_status fem_batch_create(const fem_form* const* forms, int nprob, 
       delete b;
       return fem_fail(FEM_EINVAL, "fem_batch_create: form %d is an elasticity form", i);
     }
-    if (sp->mesh->dim != 3) {
-      delete b;
-      return fem_fail(FEM_EUNSUPPORTED, "fem_batch_create: form %d is on a 2D mesh; batches hold hexahedra", i);
-    }
+
     if (sp->p > 6) {
       delete b;
       return fem_fail(FEM_EUNSUPPORTED, "fem_batch_create: form %d has p = %d; batches hold p <= 6", i, sp->p);
     }
     BProb P{};
     P.p = sp->p; P.q = f->q1d; P.kind = f->kind; P.ne = (int)sp->ne; P.nd = sp->nd; P.nq = f->nq;
+    P.dim = sp->mesh->dim;
     P.ndof = sp->ndof;
     P.nchunks = (int)((sp->ndof + kCH - 1) / kCH);
     P.sys0 = i * nrhs;
@@ -724,7 +773,7 @@ extern "C" fem_status fem_batch_create(const fem_form* const* forms, int nprob, 
   b->pstride = (int64_t)nrhs * chunk_sum;
   b->ye_len = (int64_t)nrhs * ye_sum;
   fem_status st = dev_alloc(&b->d_probs, (size_t)nprob);
-  if (st == FEM_OK) st = dev_alloc(&b->d_tiles, (size_t)(kMaxP + 1) * 2);
+  if (st == FEM_OK) st = dev_alloc(&b->d_tiles, (size_t)2 * kTiles3);
   if (st == FEM_OK) st = dev_alloc(&b->d_ye, (size_t)b->ye_len);
   if (st == FEM_OK) st = dev_alloc(&b->d_vitems, vitems.size());
   if (st == FEM_OK) {
@@ -1003,8 +1052,9 @@ extern "C" fem_status fem_batch_tune(fem_batch* b, int dtype, const char* cache_
     }
   }
   std::vector<std::pair<int, int>> pqs;
-  for (const BProb& P : b->hprobs)
-    if (std::find(pqs.begin(), pqs.end(), std::make_pair(P.p, P.q)) == pqs.end()) pqs.push_back({P.p, P.q});
+  for (const BProb& P : b->hprobs)  // hexahedral problems (quadrilaterals keep floor(256 / q))
+    if (P.dim == 3 && std::find(pqs.begin(), pqs.end(), std::make_pair(P.p, P.q)) == pqs.end())
+      pqs.push_back({P.p, P.q});
   auto keyof = [&](int p, int q) { return devname + "|" + dts + "|p" + std::to_string(p) + "q" + std::to_string(q); };
   bool all_cached = true;
   for (auto& pq : pqs) {

@@ -225,9 +225,9 @@ def test_errors():
     bad2[0, 0] = c.shape[0]
     with pytest.raises(F.FemError):
         F.Mesh2D(c, bad2)
-    # batches hold hexahedra only
+    # batches hold p <= 6 on quadrilaterals as on hexahedra
     m2 = F.Mesh2D(c, qd)
-    f2 = F.Form(F.Space(m2, 2), "diffusion", 4)
+    f2 = F.Form(F.Space(m2, 7), "diffusion", 9)
     with pytest.raises(F.FemError) as ei:
         F.Batch([f2], 1)
     assert ei.value.status == 7

@@ -1,6 +1,7 @@
 """Batched PA applies and Jacobi-PCG over many independent problems (mixed
-orders, sizes and kinds, several right-hand sides each) against the oracle
-and against the single-problem path; the tile autotuner and its cache."""
+orders, sizes and kinds, several right-hand sides each, hexahedral and
+quadrilateral meshes in one batch) against the oracle and against the
+single-problem path; the tile autotuner and its cache."""
 
 import json
 import os
@@ -8,8 +9,8 @@ import os
 import numpy as np
 import pytest
 
-from fem_inputs import lognormal, x_uniform, splitmix64
-from oracle import assemble, solve as osolve
+from fem_inputs import lognormal, quad_lattice, x_uniform, splitmix64
+from oracle import assemble, solve as osolve, twod
 
 from gpu_util import cuda, make_mesh, relerr
 
@@ -210,3 +211,81 @@ def test_config_size_batch():
         ref = assemble.sampled_apply(c, h, num["e2l"], p, p + 2, "diffusion", kap, x, rows)
         got = bt.block(Y, i, 5).cpu().numpy()[rows]
         assert np.abs(got - ref).max() <= TOL * np.abs(ref).max(), i
+
+
+def _mixed_dims(nprob=10, nrhs=3, seed=380):
+    """Every other problem on a perturbed quadrilateral mesh, the others on
+    hexahedra; p = 1..6, diffusion and mass."""
+    import paper_1911_09220_gb300 as F
+    draws = splitmix64(seed, 3 * nprob)
+    probs = []
+    for i in range(nprob):
+        p = 1 + int(draws[3 * i] % np.uint64(6))
+        kind = ("diffusion", "mass")[int(draws[3 * i + 1] % np.uint64(2))]
+        if i % 2 == 0:
+            N = 2 + int(draws[3 * i + 2] % np.uint64(5))
+            c, qd = quad_lattice(N, 0.2, seed=seed + i, shuffle=(i % 4 == 0))
+            kappa = lognormal(seed + 100 + i, qd.shape[0])
+            space = F.Space(F.Mesh2D(c, qd), p)
+            prob = twod.Problem2(c, qd, p, p + 2, kappa=kappa, rho=kappa)
+        else:
+            N = 1 + int(draws[3 * i + 2] % np.uint64(3))
+            c, h = make_mesh(N, seed=seed + i, shuffle=True)
+            kappa = lognormal(seed + 100 + i, h.shape[0])
+            space = F.Space(F.Mesh(c, h), p)
+            prob = assemble.Problem(c, h, p, p + 2, kappa=kappa, rho=kappa)
+        form = F.Form(space, kind, p + 2, coef=cuda(kappa))
+        probs.append(dict(space=space, form=form, prob=prob, kind=kind, p=p))
+    return probs, F.Batch([q["form"] for q in probs], nrhs)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batch_mixes_quadrilaterals_and_hexahedra(dtype):
+    import torch
+    probs, bt = _mixed_dims()
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    X = cuda(x_uniform(381, bt.total_len), tdt)
+    Y = torch.full_like(X, np.nan)
+    bt.apply(X, Y)
+    bt.apply(X, Y)   # graph replay
+    for i, q in enumerate(probs):
+        for r in range(bt.nrhs):
+            x = bt.block(X, i, r).contiguous()
+            y1 = torch.empty_like(x)
+            q["form"].apply(x, y1)
+            yb = bt.block(Y, i, r)
+            assert relerr(yb.cpu().double().numpy(), y1.cpu().double().numpy()) <= (TOL if dtype == "f64" else 1e-6)
+            ref = q["prob"].apply(q["kind"], x.cpu().double().numpy())
+            assert relerr(yb.cpu().double().numpy(), ref) <= (TOL if dtype == "f64" else 2e-5), (i, r)
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_batch_mixed_dims_constrained_and_solve(precision):
+    import torch
+    probs, bt = _mixed_dims(nprob=8, nrhs=2, seed=390)
+    raw = cuda(x_uniform(391, bt.total_len))
+    Bc = torch.empty_like(raw)
+    for i, q in enumerate(probs):
+        ess = q["space"].boundary_dofs()
+        q["form"].set_essential(cuda(ess))
+        for r in range(bt.nrhs):
+            q["form"].lift_rhs(bt.block(raw, i, r).contiguous(),
+                               torch.zeros(q["space"].ndof, dtype=torch.float64, device="cuda"), bt.block(Bc, i, r))
+    Y = torch.empty_like(raw)
+    bt.apply(raw, Y, constrained=True)
+    for i, q in enumerate(probs):
+        ess = q["space"].boundary_dofs()
+        Ac = osolve.constrain(q["prob"].matrix(q["kind"]), ess)
+        for r in range(bt.nrhs):
+            assert relerr(bt.block(Y, i, r).cpu().numpy(), Ac @ bt.block(raw, i, r).cpu().numpy()) <= TOL
+    X = torch.zeros_like(Bc)
+    info = bt.solve(Bc, X, rtol=1e-10, precision=precision, check_every=8)
+    assert np.all(info["relres"] <= 1e-10)
+    for i, q in enumerate(probs):
+        ess = q["space"].boundary_dofs()
+        A = q["prob"].matrix(q["kind"])
+        Ac = osolve.constrain(A, ess)
+        for r in range(bt.nrhs):
+            b = osolve.constrain_rhs(A, bt.block(raw, i, r).cpu().numpy(), ess)
+            u = bt.block(X, i, r).cpu().numpy()
+            assert np.linalg.norm(b - Ac @ u) / np.linalg.norm(b) <= 1.01e-10, (i, r)
