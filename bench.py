@@ -116,7 +116,7 @@ class ClockSampler:
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("k_apply_kernels.cuh", "k_common.cuh", "k_element.cuh", "k_tables.cuh", "k_df64.cuh"):
+    for f in ("k_apply_kernels.cuh", "k_common.cuh", "k_element.cuh", "k_tables.cuh", "k_df64.cuh", "k_tc.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1911_09220_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
