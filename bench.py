@@ -5,8 +5,8 @@ Workload (one GPU): unit-cube hexahedral mesh N^3 (N = 68), vertices
 perturbed by U[-0.15h, 0.15h] (tangentially on the boundary), order p = 4,
 q = 6 Gauss points per direction, per-element lognormal kappa, 20,346,417
 DOFs, x ~ U[-1, 1]. One step = one operator application y = A x (element
-kernel + inverse-map scatter). Inputs (D = 3.26 GB) are far larger than L2,
-so no flush is needed between steps.
+kernel + inverse-map scatter, through fem_apply). Inputs (D = 3.26 GB) are
+far larger than L2, so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -1101,16 +1101,27 @@ def main():
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
+        form.apply(x, y)
         form.apply_element(x, ye)
         form.scatter(ye, y)
     torch.cuda.synchronize()
 
+    # Timed region: K steps of the public apply (fem_apply: element kernel and
+    # scatter, the E-vector in DOF-sorted order at this size), then the same
+    # K applies through the public halves (element-major E-vector), whose
+    # per-kernel CUDA events give the element kernel's duration for the
+    # roofline (the same arithmetic; only its output addresses differ).
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    e_start, e_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for k in range(args.steps):
+        form.apply(x, y)
+    e_stop.record(stream)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for k in range(args.steps):
@@ -1123,7 +1134,7 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    t_total_ms = ev[0][0].elapsed_time(ev[-1][2])
+    t_total_ms = e_start.elapsed_time(e_stop)
     t_elem = [a.elapsed_time(b) for a, b, _ in ev]
     t_scat = [b.elapsed_time(c_) for _, b, c_ in ev]
     ms_step = reduce_max(t_total_ms / args.steps, dev)
@@ -1186,10 +1197,11 @@ def main():
             "peak_measured": probe["fp64_tflops"], "frac_of_measured": achieved / probe["fp64_tflops"],
             "peak_measured_source": probe["kernel"],
             "alg_flops_per_launch": flops, "alg_bytes_per_launch": bytes_alg,
-            "hbm_achieved_gbs": bytes_alg / (t_el + statistics.mean(t_scat) * 1e-3) / 1e9,
+            "hbm_achieved_gbs": bytes_alg / (ms_step * 1e-3) / 1e9,
             "hbm_peak_gbs_measured": peaks().get("hbm_gbs"),
-            "element_kernel_ms": statistics.mean(t_elem), "scatter_kernel_ms": statistics.mean(t_scat),
-            "element_share": statistics.mean(t_elem) / (statistics.mean(t_elem) + statistics.mean(t_scat))}
+            "element_kernel_ms": statistics.mean(t_elem), "scatter_kernel_ms_element_major": statistics.mean(t_scat),
+            "apply_ms": ms_step,
+            "element_share": statistics.mean(t_elem) / ms_step}
 
     # FP32 apply of the same operator (the inner operator of the mixed solver)
     x32 = x.float()
@@ -1303,7 +1315,7 @@ def main():
                                    f"lognormal kappa, {n} DOFs per GPU", "p": p, "q1d": q, "N": N, "ndof": n,
                        "elements": E, "parallelism": f"replicas x{world} (independent problems)",
                        "l2": "inputs larger than L2 (D alone 3.26 GB); no flush"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 4 * args.steps,
             "fp32_apply": fp32, "mass_apply_f64": mass, "df64_apply": df64, "fma_probe": probe,
             "clocks": clk, "solve": solve,
             "setup_s": {"space_host": t_space, "form_setup": t_setup},
