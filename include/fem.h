@@ -407,6 +407,11 @@ typedef struct {
   int power_its;        /* power iterations per smoothed level (20) */
   int coarse_its;       /* Jacobi-PCG iterations on the coarsest level (30) */
   int precision;        /* FEM_F64 or FEM_F32: arithmetic of the V-cycle */
+  int coarse_assembled; /* 1: an order-1 coarsest level of a scalar form is
+                           assembled once into a sparse matrix (CSR, entries
+                           summed in ascending element order) that its CG
+                           multiplies by; 0: matrix-free like every other
+                           level (1) */
 } fem_mg_opts;
 void fem_mg_opts_default(fem_mg_opts* opts);
 /* Builds the hierarchy for `fine` (fem_form_set_essential must have been

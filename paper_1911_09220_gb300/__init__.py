@@ -447,13 +447,14 @@ class Multigrid:
     forms get a vector hierarchy (vectors of length 3 ndof on every level)."""
 
     def __init__(self, form, cheb_order=2, cheb_lo=0.25, cheb_hi=1.1, power_its=20, coarse_its=30,
-                 precision="f64", stream=None):
+                 precision="f64", stream=None, coarse_assembled=True):
         L = B.lib()
         self.form = form
         o = B.MgOpts()
         L.fem_mg_opts_default(C.byref(o))
         o.cheb_order, o.cheb_lo, o.cheb_hi = int(cheb_order), float(cheb_lo), float(cheb_hi)
         o.power_its, o.coarse_its = int(power_its), int(coarse_its)
+        o.coarse_assembled = int(bool(coarse_assembled))
         o.precision = {"f64": FEM_F64, "f32": FEM_F32}[precision]
         h = C.c_void_p()
         B.check(L.fem_mg_create(form._h, C.byref(o), _stream(stream), C.byref(h)))

@@ -36,7 +36,7 @@ class SolveOpts(C.Structure):
 
 class MgOpts(C.Structure):
     _fields_ = [("cheb_order", C.c_int), ("cheb_lo", C.c_double), ("cheb_hi", C.c_double), ("power_its", C.c_int),
-                ("coarse_its", C.c_int), ("precision", C.c_int)]
+                ("coarse_its", C.c_int), ("precision", C.c_int), ("coarse_assembled", C.c_int)]
 
 
 class SolveInfo(C.Structure):

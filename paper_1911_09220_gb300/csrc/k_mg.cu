@@ -37,6 +37,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -527,6 +528,95 @@ __global__ void k_sum1(const double* __restrict__ part, int nb, double* __restri
   if (threadIdx.x == 0) *out = s;
 }
 
+// ------------------------------------------ assembled order-1 coarsest level
+// Element matrices of an order-1 form (D1 = 2, local node a = ax + 2 ay + 4
+// az): Ke[e][a][b] = sum_q grad phi_a(q) . D_q grad phi_b(q) (diffusion,
+// D point-major [q][6]) or sum_q D_q phi_a(q) phi_b(q) (mass), with the
+// form's 1D tables B, G [Q][2] at its Q Gauss points.
+__global__ void k_p1_element_matrices(int64_t ne, int Q, int kind, const double* __restrict__ D,
+                                      const double* __restrict__ B, const double* __restrict__ G,
+                                      double* __restrict__ Ke) {
+  const int nq = Q * Q * Q;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ne * 64;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / 64;
+    const int a = (int)((t / 8) % 8), b = (int)(t % 8);
+    const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2, bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
+    double v = 0.0;
+    for (int qz = 0; qz < Q; ++qz)
+      for (int qy = 0; qy < Q; ++qy)
+        for (int qx = 0; qx < Q; ++qx) {
+          const int q = qx + Q * (qy + Q * qz);
+          const double Bax = B[qx * 2 + ax], Bay = B[qy * 2 + ay], Baz = B[qz * 2 + az];
+          const double Bbx = B[qx * 2 + bx], Bby = B[qy * 2 + by], Bbz = B[qz * 2 + bz];
+          if (kind == FEM_DIFFUSION) {
+            const double ga0 = G[qx * 2 + ax] * Bay * Baz, ga1 = Bax * G[qy * 2 + ay] * Baz,
+                         ga2 = Bax * Bay * G[qz * 2 + az];
+            const double gb0 = G[qx * 2 + bx] * Bby * Bbz, gb1 = Bbx * G[qy * 2 + by] * Bbz,
+                         gb2 = Bbx * Bby * G[qz * 2 + bz];
+            const double* d = D + (e * nq + q) * 6;
+            v += ga0 * (d[0] * gb0 + d[1] * gb1 + d[2] * gb2) + ga1 * (d[1] * gb0 + d[3] * gb1 + d[4] * gb2) +
+                 ga2 * (d[2] * gb0 + d[4] * gb1 + d[5] * gb2);
+          } else {
+            v += D[e * nq + q] * (Bax * Bay * Baz) * (Bbx * Bby * Bbz);
+          }
+        }
+    Ke[t] = v;
+  }
+}
+
+// CSR values of the constrained operator A_c = (I - E) A (I - E) + E: entry j
+// (row i, column c) sums its element contributions Ke[cidx[k]], k in
+// [coff[j], coff[j+1]), in ascending element order; rows and columns of
+// essential DOFs are zero except the unit diagonal.
+__global__ void k_csr_assemble(int64_t nnz, const int32_t* __restrict__ row_of, const int32_t* __restrict__ cols,
+                               const int32_t* __restrict__ coff, const int32_t* __restrict__ cidx,
+                               const double* __restrict__ Ke, const uint8_t* __restrict__ ess,
+                               double* __restrict__ v64, float* __restrict__ v32) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nnz; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = row_of[j], c = cols[j];
+    double v = 0.0;
+    if (ess[i] || ess[c]) {
+      v = (i == c) ? 1.0 : 0.0;
+    } else {
+      for (int32_t k = coff[j]; k < coff[j + 1]; ++k) v += Ke[cidx[k]];
+    }
+    v64[j] = v;
+    v32[j] = (float)v;
+  }
+}
+
+// y = A x on the assembled level (8 lanes per row, the row's sum reduced by
+// a fixed butterfly) and per-block partials of x . y; skipped when *skip.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_csr_apply(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ cols, const T* __restrict__ vals,
+            const T* __restrict__ x, T* __restrict__ y, double* __restrict__ part, const int* __restrict__ skip) {
+  __shared__ double red[32];
+  if (skip && *skip) return;
+  using A = typename DotAcc<T>::type;
+  A acc = 0;
+  const int lane8 = threadIdx.x & 7;
+  const unsigned mask = 0xffu << (threadIdx.x & 24);
+  const int64_t g0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
+  const int64_t gs = ((int64_t)gridDim.x * blockDim.x) >> 3;
+  for (int64_t i = g0; i < n; i += gs) {
+    T v = 0;
+    for (int32_t k = rowptr[i] + lane8; k < rowptr[i + 1]; k += 8) v += vals[k] * x[cols[k]];
+    v += __shfl_xor_sync(mask, v, 4, 8);
+    v += __shfl_xor_sync(mask, v, 2, 8);
+    v += __shfl_xor_sync(mask, v, 1, 8);
+    if (lane8 == 0) {
+      y[i] = v;
+      if (part) acc += (A)x[i] * (A)v;
+    }
+  }
+  if (part) {
+    const double s = block_sum((double)acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ handle
@@ -544,6 +634,12 @@ struct MgLevel {
   void* vec = nullptr;          // r, z, res, d, q (T each)
   double* I = nullptr;          // to the next coarser level: I [D1][D1c], I^T [D1c][D1]
   double* It = nullptr;
+  // assembled constrained operator (the coarsest level when it has order 1)
+  int64_t nnz = 0;
+  int32_t* rowptr = nullptr;
+  int32_t* cols = nullptr;
+  double* vals64 = nullptr;
+  float* vals32 = nullptr;
 };
 
 struct fem_mg {
@@ -628,7 +724,12 @@ fem_status coarse_solve(fem_mg* m, const MgLevel& C, const int* skip, cudaStream
   k_cc_init<T><<<nb, 256, 0, s>>>(n, lvec<T>(C, 0), D, r, z, p, x, rzp[0], stop, skip);
   FEM_LAUNCHED();
   for (int k = 0; k < m->o.coarse_its; ++k) {
-    FEM_TRY(level_apply<T>(C, p, q, stop, s, pq, nb));
+    if (C.nnz > 0) {
+      const T* vals = std::is_same<T, float>::value ? (const T*)C.vals32 : (const T*)C.vals64;
+      k_csr_apply<T><<<nb, 256, 0, s>>>(n, C.rowptr, C.cols, vals, p, q, pq, stop);
+    } else {
+      FEM_TRY(level_apply<T>(C, p, q, stop, s, pq, nb));
+    }
     k_cc_update<T><<<nb, 256, 0, s>>>(n, nb, pq, rzp[k & 1], rzp[(k + 1) & 1], x, r, z, p, q, D, stop);
     k_cc_p<T><<<nb, 256, 0, s>>>(n, nb, rzp[k & 1], rzp[(k + 1) & 1], z, p, stop);
     FEM_LAUNCHED();
@@ -793,6 +894,127 @@ void cheb_setup(MgLevel& L, const fem_mg_opts& o) {
   }
 }
 
+// Assemble the order-1 coarsest level into CSR (once, at set-up). Pattern:
+// row i holds the DOFs of the elements containing DOF i, ascending. Each
+// element-matrix entry (e, a, b) contributes to (e2l[e][a], e2l[e][b]); the
+// contributions of an entry are summed in ascending element order, so the
+// values do not depend on the schedule.
+// fn(i0, i1) over [0, n) in contiguous ranges on up to 16 host threads.
+template <typename F>
+void host_parallel(int64_t n, F fn) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), 16, n / 8192 + 1}));
+  if (nt == 1) {
+    fn((int64_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int64_t t = 0; t < nt; ++t) th.emplace_back(fn, n * t / nt, n * (t + 1) / nt);
+  for (auto& x : th) x.join();
+}
+
+fem_status assemble_coarse(MgLevel& C, cudaStream_t s) {
+  const fem_space* sp = C.f->space;
+  const int64_t ne = sp->ne, n = sp->ndof;
+  const std::vector<int32_t>& e2l = sp->e2l;
+  std::vector<int32_t> eoff(n + 1, 0), eslot((size_t)ne * 8);
+  for (int64_t k = 0; k < ne * 8; ++k) eoff[e2l[k] + 1]++;
+  for (int64_t i = 0; i < n; ++i) eoff[i + 1] += eoff[i];
+  {
+    std::vector<int32_t> fill(eoff.begin(), eoff.end() - 1);
+    for (int64_t k = 0; k < ne * 8; ++k) eslot[fill[e2l[k]]++] = (int32_t)k;  // ascending element
+  }
+  for (int64_t i = 0; i < n; ++i)
+    if (eoff[i + 1] - eoff[i] > 64) return FEM_EUNSUPPORTED;  // > 64 elements at a vertex: stay matrix-free
+  // rows: the sorted distinct DOFs of the elements holding DOF i, counted in
+  // parallel, then written at their offsets
+  auto row_cols = [&](int64_t i, int32_t* out) {
+    int32_t tmp[64 * 8];
+    int m = 0;
+    for (int32_t t = eoff[i]; t < eoff[i + 1]; ++t) {
+      const int64_t e = eslot[t] / 8;
+      for (int b = 0; b < 8; ++b) tmp[m++] = e2l[e * 8 + b];
+    }
+    std::sort(tmp, tmp + m);
+    const int u = (int)(std::unique(tmp, tmp + m) - tmp);
+    if (out) std::copy(tmp, tmp + u, out);
+    return u;
+  };
+  std::vector<int32_t> rowptr(n + 1, 0);
+  host_parallel(n, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i) rowptr[i + 1] = row_cols(i, nullptr);
+  });
+  for (int64_t i = 0; i < n; ++i) rowptr[i + 1] += rowptr[i];
+  const int64_t nnz = rowptr[n];
+  std::vector<int32_t> cols(nnz), row_of(nnz);
+  host_parallel(n, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i) {
+      row_cols(i, cols.data() + rowptr[i]);
+      std::fill(row_of.begin() + rowptr[i], row_of.begin() + rowptr[i + 1], (int32_t)i);
+    }
+  });
+  // contributions: the entry of every element-matrix slot (parallel over
+  // elements), then a counting sort that keeps ascending element order
+  std::vector<int32_t> cpos((size_t)ne * 64);
+  host_parallel(ne, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e)
+      for (int a = 0; a < 8; ++a) {
+        const int32_t i = e2l[e * 8 + a];
+        const int32_t* rb = cols.data() + rowptr[i];
+        const int32_t* re = cols.data() + rowptr[i + 1];
+        for (int b = 0; b < 8; ++b)
+          cpos[(size_t)e * 64 + a * 8 + b] = (int32_t)(std::lower_bound(rb, re, e2l[e * 8 + b]) - cols.data());
+      }
+  });
+  std::vector<int32_t> coff(nnz + 1, 0);
+  for (int64_t t = 0; t < ne * 64; ++t) coff[cpos[t] + 1]++;
+  for (int64_t j = 0; j < nnz; ++j) coff[j + 1] += coff[j];
+  std::vector<int32_t> cidx((size_t)ne * 64);
+  {
+    std::vector<int32_t> fill(coff.begin(), coff.end() - 1);
+    for (int64_t t = 0; t < ne * 64; ++t) cidx[fill[cpos[t]]++] = (int32_t)t;
+  }
+  // device: element matrices, then the entries
+  int32_t *d_row_of = nullptr, *d_coff = nullptr, *d_cidx = nullptr;
+  double* d_Ke = nullptr;
+  fem_status st = dev_alloc(&C.rowptr, rowptr.size());
+  if (st == FEM_OK) st = dev_alloc(&C.cols, cols.size());
+  if (st == FEM_OK) st = dev_alloc(&C.vals64, cols.size());
+  if (st == FEM_OK) st = dev_alloc(&C.vals32, cols.size());
+  if (st == FEM_OK) st = dev_alloc(&d_row_of, row_of.size());
+  if (st == FEM_OK) st = dev_alloc(&d_coff, coff.size());
+  if (st == FEM_OK) st = dev_alloc(&d_cidx, cidx.size());
+  if (st == FEM_OK) st = dev_alloc(&d_Ke, (size_t)ne * 64);
+  if (st == FEM_OK &&
+      (cudaMemcpy(C.rowptr, rowptr.data(), sizeof(int32_t) * rowptr.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(C.cols, cols.data(), sizeof(int32_t) * cols.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(d_row_of, row_of.data(), sizeof(int32_t) * row_of.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(d_coff, coff.data(), sizeof(int32_t) * coff.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(d_cidx, cidx.data(), sizeof(int32_t) * cidx.size(), cudaMemcpyHostToDevice) != cudaSuccess))
+    st = fem_fail(FEM_ECUDA, "fem_mg_create: upload of the coarse matrix pattern failed");
+  if (st == FEM_OK) {
+    k_p1_element_matrices<<<grid_for(ne * 64, 256), 256, 0, s>>>(ne, C.f->q1d, C.f->kind, C.f->d_D, C.f->d_B,
+                                                                  C.f->d_G, d_Ke);
+    k_csr_assemble<<<grid_for(nnz, 256), 256, 0, s>>>(nnz, d_row_of, C.cols, d_coff, d_cidx, d_Ke,
+                                                       C.f->d_ess_mask, C.vals64, C.vals32);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+      st = fem_fail(FEM_ECUDA, "fem_mg_create: coarse matrix assembly failed");
+  }
+  dev_free(d_row_of);
+  dev_free(d_coff);
+  dev_free(d_cidx);
+  dev_free(d_Ke);
+  if (st != FEM_OK) {
+    dev_free(C.rowptr);
+    dev_free(C.cols);
+    dev_free(C.vals64);
+    dev_free(C.vals32);
+    return st;
+  }
+  C.nnz = nnz;
+  return FEM_OK;
+}
+
 template <typename T>
 fem_status alloc_vecs(fem_mg* m) {
   size_t maxc = 1;
@@ -824,6 +1046,7 @@ extern "C" void fem_mg_opts_default(fem_mg_opts* o) {
   o->power_its = 20;
   o->coarse_its = 30;
   o->precision = FEM_F64;
+  o->coarse_assembled = 1;
 }
 
 extern "C" void fem_mg_destroy(fem_mg* m) {
@@ -834,6 +1057,10 @@ extern "C" void fem_mg_destroy(fem_mg* m) {
     if (L.vec) cudaFree(L.vec);
     dev_free(L.I);
     dev_free(L.It);
+    dev_free(L.rowptr);
+    dev_free(L.cols);
+    dev_free(L.vals64);
+    dev_free(L.vals32);
     if (L.f_own) fem_form_destroy(L.f_own);
     if (L.sp_own) fem_space_destroy(L.sp_own);
   }
@@ -935,6 +1162,11 @@ extern "C" fem_status fem_mg_create(const fem_form* fine, const fem_mg_opts* opt
     if (st != FEM_OK) return fail(st);
     essf.assign(C.n, 0);
     for (int32_t i : ess) essf[i] = 1;
+  }
+  // the coarsest level as an assembled matrix when it has order 1 (scalar forms)
+  if (o.coarse_assembled && m->lv.back().p == 1 && m->lv.back().vdim == 1 && m->lv.back().f->kind != FEM_ELASTICITY) {
+    st = assemble_coarse(m->lv.back(), s);
+    if (st != FEM_OK && st != FEM_EUNSUPPORTED) return fail(st);  // unsupported: the level stays matrix-free
   }
   // scratch, scalars
   const int64_t n0 = m->lv[0].n;

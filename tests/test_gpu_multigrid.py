@@ -111,6 +111,27 @@ def test_vcycle_parity_fp64(p, N, drop, face_only):
     assert torch.equal(z, z2)
 
 
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("p,N,drop,face_only", [(2, 4, 3, False), (4, 3, 2, True), (6, 2, 1, False),
+                                                (1, 4, 5, False)])
+def test_assembled_coarsest_level(p, N, drop, face_only, precision, tol):
+    """The order-1 coarsest level as an assembled matrix (the default) gives
+    the V-cycle of the matrix-free coarsest level: same operator, other
+    summation order."""
+    import torch
+    M, G, form, fine, ess, keep = _setup(p, N, drop, face_only=face_only, precision=precision)
+    import paper_1911_09220_gb300 as F
+    G0 = F.Multigrid(form, precision=precision, coarse_assembled=False)
+    r = x_uniform(60 + p, fine.ndof)
+    r[ess] = 0.0
+    z = torch.empty(fine.ndof, dtype=torch.float64, device="cuda")
+    z0 = torch.empty_like(z)
+    G.vcycle(cuda(r), z)
+    G0.vcycle(cuda(r), z0)
+    assert relerr(z.cpu().numpy(), z0.cpu().numpy()) <= tol
+    assert relerr(z.cpu().numpy(), M.vcycle(r)) <= (1e-10 if precision == "f64" else 1e-4)
+
+
 @pytest.mark.parametrize("p,N", [(2, 4), (4, 3), (8, 2)])
 def test_vcycle_parity_fp32(p, N):
     import torch
