@@ -51,7 +51,9 @@ def _defines():
     resident 256-thread blocks per SM (its register budget). FEM_F32_TC=1
     runs the x-direction stages of the FP32 diffusion kernel (p >= 4) on the
     tensor cores (split-TF32 mma, k_tc.cuh); FEM_F32_TC=2 with single TF32
-    products."""
+    products. FEM_F32_LANES=0 packs the short stages of the FP32 element
+    kernels like the FP64 ones instead of giving each element whole warps
+    (k_element.cuh, stage_lanes)."""
     t = os.environ.get("FEM_NE_TABLE", "measured")
     out = {"large": ["-DFEM_NE_TABLE=1"], "small": ["-DFEM_NE_TABLE=2"]}.get(t, [])
     mb = os.environ.get("FEM_BATCH_MIN_BLOCKS")
@@ -62,6 +64,8 @@ def _defines():
         out.append(f"-DFEM_BATCH_MIN_BLOCKS64={int(mb64)}")
     if os.environ.get("FEM_F32_TC") in ("1", "2"):
         out.append(f"-DFEM_F32_TC={os.environ['FEM_F32_TC']}")
+    if os.environ.get("FEM_F32_LANES") == "0":
+        out.append("-DFEM_F32_LANES=0")
     return out
 
 

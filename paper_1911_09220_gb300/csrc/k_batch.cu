@@ -1059,8 +1059,13 @@ extern "C" fem_status fem_batch_tune(fem_batch* b, int dtype, const char* cache_
   bool all_cached = true;
   for (auto& pq : pqs) {
     auto it = cache.find(keyof(pq.first, pq.second));
-    if (it != cache.end()) b->h_tiles[pq.first * 2 + (pq.second - pq.first - 1)] = it->second;
-    else all_cached = false;
+    // a cached tile is clamped to the block's whole planes: every element of
+    // a tile needs its plane of q^2 threads among the block's 256
+    if (it != cache.end())
+      b->h_tiles[pq.first * 2 + (pq.second - pq.first - 1)] =
+          std::min(it->second, std::max(1, kBT / (pq.second * pq.second)));
+    else
+      all_cached = false;
   }
   if (!all_cached) {
     // scratch vectors for timing

@@ -18,7 +18,7 @@ namespace {
 // per SM).
 template <typename T, int D1, int Q>
 constexpr int ne_elast() {
-  constexpr int per = 3 * ElemSmem<T, D1, Q>::SE * (int)sizeof(T);
+  constexpr int per = 3 * ElemSmem<T, D1, Q>::SE3 * (int)sizeof(T);
   int ne = 256 / (Q * Q);
   if (ne < 1) ne = 1;
   while (ne > 1 && ne * per > 100 * 1024) --ne;
@@ -35,7 +35,7 @@ constexpr int ne_elast() {
 template <typename T, int D1, int Q, int NE>
 constexpr int elast_min_blocks() {
   if (!std::is_same<T, float>::value || D1 > 6) return 1;
-  constexpr int bytes = NE * 3 * ElemSmem<T, D1, Q>::SE * (int)sizeof(T);
+  constexpr int bytes = NE * 3 * ElemSmem<T, D1, Q>::SE3 * (int)sizeof(T);
   constexpr int fit = (227 * 1024) / (bytes + 1024);
   return fit < 4 ? (fit > 0 ? fit : 1) : 4;
 }
@@ -61,7 +61,7 @@ fem_status launch(const fem_form* f, const T* D, const TX* x, TX* ye, const int*
                   const int32_t* pos) {
   constexpr int D1 = P + 1, NE = ne_elast<T, D1, Q>();
   const int ne = (int)f->space->ne;
-  const size_t bytes = sizeof(T) * (size_t)NE * 3 * ElemSmem<T, D1, Q>::SE;
+  const size_t bytes = sizeof(T) * (size_t)NE * 3 * ElemSmem<T, D1, Q>::SE3;
   auto kern = k_elasticity_apply<T, D1, Q, NE, TX>;
   if (bytes > 48 * 1024)
     FEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));

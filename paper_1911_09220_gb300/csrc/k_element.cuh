@@ -222,18 +222,22 @@ __host__ __device__ constexpr int best_stride(int lo, int n, int A, bool stride_
 }
 
 // The same cost with the readers of NE consecutive elements side by side
-// (reader i belongs to element i / n, whose slab starts SE words after the
-// previous one): the packed stages and the S3 planes put the lines of two
-// elements into one warp whenever n is not a multiple of the bank group.
-__host__ __device__ constexpr int bank_cost_packed(int n, int A, int m_lo, int m_hi, int wbytes, int ne, int se) {
+// (reader i belongs to element i / L, whose slab starts SE words after the
+// previous one; lanes n .. L-1 of an element are idle, L = n when the lines
+// are packed): packed stages and the S3 planes put the lines of two elements
+// into one warp whenever n is not a multiple of the bank group.
+__host__ __device__ constexpr int bank_cost_packed(int n, int A, int m_lo, int m_hi, int wbytes, int ne, int se,
+                                                   int L = 0) {
   const int G = wbytes == 8 ? 16 : 32;
-  const int total = ne * n;
+  if (L < n) L = n;
+  const int total = ne * L;
   int cost = 0;
   for (int g0 = 0; g0 < total; g0 += G) {
     int cnt[32] = {};
     int worst = 0;
     for (int i = g0; i < total && i < g0 + G; ++i) {
-      const int el = i / n, r = i % n;
+      const int el = i / L, r = i % L;
+      if (r >= n) continue;
       const int w = el * se + (r % A) * m_lo + (r / A) * m_hi;
       const int b = w % G;
       cnt[b] += 1;
@@ -244,25 +248,52 @@ __host__ __device__ constexpr int bank_cost_packed(int n, int A, int m_lo, int m
   return cost;
 }
 
+// Lanes one element's lines take in a stage of n lines per element (the
+// stages S1, S5: D1^2 lines; S2, S4: D1 q). FP32 blocks give each element
+// its own half-warp or warp there when 8 < n <= 32 and its plane of QQ
+// threads has that many lanes: then no warp of those stages touches two
+// elements' slabs, whose relative bank offset no single slab stride can
+// suit in all four stages at once (the buffer strides already make one
+// element's lines conflict-free), and the slab stride only has to suit the
+// S3 planes. In a bank model of every stage's accesses this removes the
+// bank-conflict replays of the FP32 block at p = 4, q = 6 (30 % of its
+// shared-memory wavefronts; p = 2, q = 4: 17 %); measured, the FP32 element
+// kernel at p = 4 ran 10 % faster and at p = 2 3 % faster, while elements of
+// two or more warps (p >= 5) gained nothing and keep the packed lines.
+// FP64 and double-float blocks pack the lines of consecutive elements onto
+// the lowest thread ids (L = n): an arithmetic-bound warp pays its issue
+// slot however few lanes are active. (Build option FEM_F32_LANES=0 packs the
+// FP32 stages too.)
+#ifndef FEM_F32_LANES
+#define FEM_F32_LANES 1
+#endif
+template <typename T>
+__host__ __device__ constexpr int stage_lanes(int n, int QQ) {
+  if (FEM_F32_LANES == 0 || !std::is_same<T, float>::value || n <= 8 || n > 32) return n;
+  const int L = n <= 16 ? 16 : 32;
+  return L <= QQ ? L : n;
+}
+
 // Slab stride >= lo (candidates lo .. lo + 31) of least total cost over the
 // shared-memory accesses of all stages, each weighted by the values a line
 // reads or writes (S1: X rows in, BX/GX out; S2: BX/GX in, BB/GB/BG out;
 // S3: BB/GB/BG in, T0-T2 out; S4: T0-T2 in, UA/UB out; S5: UA/UB in),
-// modelled on 8 elements.
+// modelled on 8 elements whose S1/S5 lines take L1 lanes each and S2/S4
+// lines L2 (stage_lanes).
 __host__ __device__ constexpr int best_slab(int lo, int D1, int Q, int XP, int RB, int RC, int RT, int RU,
-                                            int wbytes) {
+                                            int wbytes, int L1 = 0, int L2 = 0) {
   const int N1 = D1 * D1, N2 = D1 * Q, QQ = Q * Q, NEm = 8;
   int best = lo, best_cost = 1 << 30;
   for (int se = lo; se < lo + 32; ++se) {
-    const int c = D1 * bank_cost_packed(N1, N1, XP, 0, wbytes, NEm, se) +
-                  2 * Q * bank_cost_packed(N1, N1, 1, 0, wbytes, NEm, se) +
-                  2 * D1 * bank_cost_packed(N2, Q, RB, D1, wbytes, NEm, se) +
-                  3 * Q * bank_cost_packed(N2, N2, 1, 0, wbytes, NEm, se) +
+    const int c = D1 * bank_cost_packed(N1, N1, XP, 0, wbytes, NEm, se, L1) +
+                  2 * Q * bank_cost_packed(N1, N1, 1, 0, wbytes, NEm, se, L1) +
+                  2 * D1 * bank_cost_packed(N2, Q, RB, D1, wbytes, NEm, se, L2) +
+                  3 * Q * bank_cost_packed(N2, N2, 1, 0, wbytes, NEm, se, L2) +
                   3 * D1 * bank_cost_packed(QQ, Q, 1, RC, wbytes, NEm, se) +
                   3 * D1 * bank_cost_packed(QQ, QQ, 1, 0, wbytes, NEm, se) +
-                  3 * Q * bank_cost_packed(N2, Q, 1, RT, wbytes, NEm, se) +
-                  2 * D1 * bank_cost_packed(N2, N2, 1, 0, wbytes, NEm, se) +
-                  2 * Q * bank_cost_packed(N1, D1, RU, Q, wbytes, NEm, se);
+                  3 * Q * bank_cost_packed(N2, Q, 1, RT, wbytes, NEm, se, L2) +
+                  2 * D1 * bank_cost_packed(N2, N2, 1, 0, wbytes, NEm, se, L2) +
+                  2 * Q * bank_cost_packed(N1, D1, RU, Q, wbytes, NEm, se, L1);
     if (c < best_cost) {
       best_cost = c;
       best = se;
@@ -286,9 +317,16 @@ struct ElemSmem {
   static constexpr int R0 = D1 * D1 * XP > 3 * Q * RC ? D1 * D1 * XP : 3 * Q * RC;
   static constexpr int SA = R0 + 2 * Q * RB;
   static constexpr int SB = 3 * D1 * RT + 2 * D1 * RU;
+  // lanes per element of the S1/S5 and S2/S4 lines (stage_lanes)
+  static constexpr int L1 = stage_lanes<T>(D1 * D1, Q * Q);
+  static constexpr int L2 = stage_lanes<T>(D1 * Q, Q * Q);
   // per element, in T: the larger phase, padded to the slab stride of least
-  // bank conflicts between neighbouring elements' slabs
-  static constexpr int SE = best_slab(SA > SB ? SA : SB, D1, Q, XP, RB, RC, RT, RU, W);
+  // bank conflicts between neighbouring elements' slabs (one slab per
+  // element, the drivers' lane mapping)
+  static constexpr int SE = best_slab(SA > SB ? SA : SB, D1, Q, XP, RB, RC, RT, RU, W, L1, L2);
+  // the same for the elasticity block, whose stages pack the lines of its
+  // (element, component) slabs (three per element) over all its threads
+  static constexpr int SE3 = best_slab(SA > SB ? SA : SB, D1, Q, XP, RB, RC, RT, RU, W);
 };
 
 // ------------------------------------------------------ stage bodies ----
@@ -483,7 +521,7 @@ struct Lines {
     T g[3][3][Q];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      T* sc = s + c * L::SE;
+      T* sc = s + c * L::SE3;
       T rbb[D1], rgb[D1], rbg[D1];
       const T *sbb = BB(sc) + qy * RC + qx, *sgb = GB(sc) + qy * RC + qx, *sbg = BG(sc) + qy * RC + qx;
 #pragma unroll
@@ -603,13 +641,26 @@ struct Lines {
 #include "k_tc.cuh"
 
 // ------------------------------------------------------------- drivers ----
+// Thread tid's line in a stage of N lines per element with L lanes per
+// element (ElemSmem::L1 / L2): element tid / L, line tid % L; lanes N .. L-1
+// of an element and elements >= nel stay idle. L = N packs the lines of
+// consecutive elements onto the lowest thread ids.
+template <int N, int L>
+__device__ __forceinline__ bool stage_line(int tid, int nel, int& el, int& t) {
+  el = tid / L;
+  t = tid - el * L;
+  return el < nel && t < N;
+}
+
 // A block works on elements e0 .. e0 + nel - 1. The gather and stage S3
 // (Q*Q lines per element) keep one plane of Q*Q threads per element, thread
 // tid = el * Q*Q + t (threads of planes el >= nel take part with valid =
 // false; the block needs a slab for every plane it has); the stages with
-// fewer lines (S1, S5: D1^2; S2, S4: D1*Q) pack the lines of the nel
-// elements onto the lowest thread ids, so warps are full and the arithmetic
-// pipe issues no instructions for idle lanes. Element e's DOF list is
+// fewer lines (S1, S5: D1^2; S2, S4: D1*Q) either pack the lines of the
+// nel elements onto the lowest thread ids, so warps are full and the
+// arithmetic pipe issues no instructions for idle lanes (FP64, double-float),
+// or give each element whole warps (FP32 where the plane has the lanes;
+// stage_lanes). Element e's DOF list is
 // e2l + e*D1^3, its D block Dq + e*NC*Q^3 (NC = 6 diffusion, 1 mass), its
 // E-vector slice ye + e*D1^3 (or, with pos, the positions pos[e*D1^3 + k]
 // of the DOF-sorted E-vector ye); its slab sm + el*SE. Every thread of the
@@ -620,34 +671,35 @@ __device__ __forceinline__ void diffusion_block(int tid, int e0, int nel, const 
                                                 TX* __restrict__ ye, const int32_t* __restrict__ pos = nullptr) {
   using Ln = Lines<T, D1, Q>;
   constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
-  constexpr int N1 = D1 * D1, N2 = D1 * Q;
+  constexpr int N1 = D1 * D1, N2 = D1 * Q, L1 = ElemSmem<T, D1, Q>::L1, L2 = ElemSmem<T, D1, Q>::L2;
   const int el = tid / QQ, t = tid % QQ;
   const bool valid = el < nel;
   const size_t ev = valid ? (size_t)(e0 + el) : 0;
+  int se, st;  // element and line of the short stages
   gather_x<T, D1, Q, TX>(t, valid, e2l + ev * ND, x, Ln::X(sm + el * SE), Ln::XP);
   __syncthreads();
   if constexpr (use_tc<T, D1>()) {
     tc_s1<D1, Q>(nel * N1, sm, tid, blockDim.x * blockDim.y * blockDim.z);
   } else {
-    if (tid < nel * N1) Ln::d1(tid % N1, sm + (tid / N1) * SE);
+    if (stage_line<N1, L1>(tid, nel, se, st)) Ln::d1(st, sm + se * SE);
   }
   __syncthreads();
-  if (tid < nel * N2) Ln::d2(tid % N2, sm + (tid / N2) * SE);
+  if (stage_line<N2, L2>(tid, nel, se, st)) Ln::d2(st, sm + se * SE);
   __syncthreads();
   T t0[D1], t1[D1], t2[D1];
   Ln::d3(t, valid, Dq + ev * 6 * NQ, sm + el * SE, t0, t1, t2);
   __syncthreads();
   Ln::d3_store(t, sm + el * SE, t0, t1, t2);
   __syncthreads();
-  if (tid < nel * N2) Ln::d4(tid % N2, sm + (tid / N2) * SE);
+  if (stage_line<N2, L2>(tid, nel, se, st)) Ln::d4(st, sm + se * SE);
   __syncthreads();
   if constexpr (use_tc<T, D1>()) {
     tc_s5<D1, Q, TX>(nel * N1, sm, tid, blockDim.x * blockDim.y * blockDim.z, ye + (pos ? 0 : (size_t)e0 * ND),
                      pos ? pos + (size_t)e0 * ND : nullptr);
-  } else if (tid < nel * N1) {
-    const size_t eo = (size_t)(e0 + tid / N1) * ND;
-    if (pos) Ln::template d5<TX>(tid % N1, sm + (tid / N1) * SE, ye, pos + eo);
-    else Ln::template d5<TX>(tid % N1, sm + (tid / N1) * SE, ye + eo);
+  } else if (stage_line<N1, L1>(tid, nel, se, st)) {
+    const size_t eo = (size_t)(e0 + se) * ND;
+    if (pos) Ln::template d5<TX>(st, sm + se * SE, ye, pos + eo);
+    else Ln::template d5<TX>(st, sm + se * SE, ye + eo);
   }
 }
 
@@ -659,27 +711,28 @@ __device__ __forceinline__ void convection_block(int tid, int e0, int nel, const
                                                  TX* __restrict__ ye, const int32_t* __restrict__ pos = nullptr) {
   using Ln = Lines<T, D1, Q>;
   constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
-  constexpr int N1 = D1 * D1, N2 = D1 * Q;
+  constexpr int N1 = D1 * D1, N2 = D1 * Q, L1 = ElemSmem<T, D1, Q>::L1, L2 = ElemSmem<T, D1, Q>::L2;
   const int el = tid / QQ, t = tid % QQ;
   const bool valid = el < nel;
   const size_t ev = valid ? (size_t)(e0 + el) : 0;
+  int se, st;
   gather_x<T, D1, Q, TX>(t, valid, e2l + ev * ND, x, Ln::X(sm + el * SE), Ln::XP);
   __syncthreads();
-  if (tid < nel * N1) Ln::d1(tid % N1, sm + (tid / N1) * SE);
+  if (stage_line<N1, L1>(tid, nel, se, st)) Ln::d1(st, sm + se * SE);
   __syncthreads();
-  if (tid < nel * N2) Ln::d2(tid % N2, sm + (tid / N2) * SE);
+  if (stage_line<N2, L2>(tid, nel, se, st)) Ln::d2(st, sm + se * SE);
   __syncthreads();
   T t0[D1];
   Ln::c3(t, valid, Dq + ev * 3 * NQ, sm + el * SE, t0);
   __syncthreads();
   Ln::m3_store(t, sm + el * SE, t0);
   __syncthreads();
-  if (tid < nel * N2) Ln::m4(tid % N2, sm + (tid / N2) * SE);
+  if (stage_line<N2, L2>(tid, nel, se, st)) Ln::m4(st, sm + se * SE);
   __syncthreads();
-  if (tid < nel * N1) {
-    const size_t eo = (size_t)(e0 + tid / N1) * ND;
-    if (pos) Ln::template m5<TX>(tid % N1, sm + (tid / N1) * SE, ye, pos + eo);
-    else Ln::template m5<TX>(tid % N1, sm + (tid / N1) * SE, ye + eo);
+  if (stage_line<N1, L1>(tid, nel, se, st)) {
+    const size_t eo = (size_t)(e0 + se) * ND;
+    if (pos) Ln::template m5<TX>(st, sm + se * SE, ye, pos + eo);
+    else Ln::template m5<TX>(st, sm + se * SE, ye + eo);
   }
 }
 
@@ -689,27 +742,28 @@ __device__ __forceinline__ void mass_block(int tid, int e0, int nel, const int32
                                            TX* __restrict__ ye, const int32_t* __restrict__ pos = nullptr) {
   using Ln = Lines<T, D1, Q>;
   constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
-  constexpr int N1 = D1 * D1, N2 = D1 * Q;
+  constexpr int N1 = D1 * D1, N2 = D1 * Q, L1 = ElemSmem<T, D1, Q>::L1, L2 = ElemSmem<T, D1, Q>::L2;
   const int el = tid / QQ, t = tid % QQ;
   const bool valid = el < nel;
   const size_t ev = valid ? (size_t)(e0 + el) : 0;
+  int se, st;
   gather_x<T, D1, Q, TX>(t, valid, e2l + ev * ND, x, Ln::X(sm + el * SE), Ln::XP);
   __syncthreads();
-  if (tid < nel * N1) Ln::m1(tid % N1, sm + (tid / N1) * SE);
+  if (stage_line<N1, L1>(tid, nel, se, st)) Ln::m1(st, sm + se * SE);
   __syncthreads();
-  if (tid < nel * N2) Ln::m2(tid % N2, sm + (tid / N2) * SE);
+  if (stage_line<N2, L2>(tid, nel, se, st)) Ln::m2(st, sm + se * SE);
   __syncthreads();
   T t0[D1];
   Ln::m3(t, valid, Dq + ev * NQ, sm + el * SE, t0);
   __syncthreads();
   Ln::m3_store(t, sm + el * SE, t0);
   __syncthreads();
-  if (tid < nel * N2) Ln::m4(tid % N2, sm + (tid / N2) * SE);
+  if (stage_line<N2, L2>(tid, nel, se, st)) Ln::m4(st, sm + se * SE);
   __syncthreads();
-  if (tid < nel * N1) {
-    const size_t eo = (size_t)(e0 + tid / N1) * ND;
-    if (pos) Ln::template m5<TX>(tid % N1, sm + (tid / N1) * SE, ye, pos + eo);
-    else Ln::template m5<TX>(tid % N1, sm + (tid / N1) * SE, ye + eo);
+  if (stage_line<N1, L1>(tid, nel, se, st)) {
+    const size_t eo = (size_t)(e0 + se) * ND;
+    if (pos) Ln::template m5<TX>(st, sm + se * SE, ye, pos + eo);
+    else Ln::template m5<TX>(st, sm + se * SE, ye + eo);
   }
 }
 
@@ -725,7 +779,7 @@ __device__ __forceinline__ void elasticity_block(int tid, int e0, int nel, int n
                                                  const TX* __restrict__ x, TX* __restrict__ ye,
                                                  const int32_t* __restrict__ pos = nullptr) {
   using Ln = Lines<T, D1, Q>;
-  constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE;
+  constexpr int QQ = Q * Q, ND = D1 * D1 * D1, NQ = Q * Q * Q, SE = ElemSmem<T, D1, Q>::SE3;
   constexpr int N1 = D1 * D1, N2 = D1 * Q, XP = Ln::XP;
   // gather: one map entry, three component values
   for (int i = tid; i < nel * ND; i += NT) {
