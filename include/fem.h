@@ -117,14 +117,15 @@ fem_status fem_mesh_create(const double* coords_host, int64_t nv,
 fem_status fem_mesh2d_create(const double* coords_host, int64_t nv,
                              const int32_t* quad_host, int64_t ne, fem_mesh** out);
 /* High-order (curved) geometry, Sec. 3.1 "nodes": element e is mapped by
- * x(xhat) = sum_i X_{e,i} w_i(xhat) with the (k+1)^3 order-k GLL Lagrange
+ * x(xhat) = sum_i X_{e,i} w_i(xhat) with the (k+1)^dim order-k GLL Lagrange
  * functions w_i (lexicographic, x fastest, in the element's local vertex
- * frame). nodes_host: [ne][(k+1)^3][3] float64, copied; 1 <= k <= 8, or
- * k = 0 to return to the trilinear vertex map. Forms created afterwards use
- * it in their setup (D), load vector and coordinates; an existing form picks
- * it up at its next fem_form_set_coef. The vertex coordinates still define
- * the topology. Errors: FEM_EINVAL (order, non-finite coordinates),
- * FEM_EUNSUPPORTED (2D mesh). */
+ * frame). nodes_host: [ne][(k+1)^3][3] float64 on a hexahedral mesh,
+ * [ne][(k+1)^2][2] on a quadrilateral one, copied; 1 <= k <= 8, or k = 0 to
+ * return to the multilinear vertex map. Forms created afterwards use it in
+ * their setup (D), load vector and coordinates (quadrature points and DOFs);
+ * an existing form picks it up at its next fem_form_set_coef. The vertex
+ * coordinates still define the topology. Errors: FEM_EINVAL (order,
+ * non-finite coordinates). */
 fem_status fem_mesh_set_nodes(fem_mesh* mesh, int k, const double* nodes_host);
 void fem_mesh_destroy(fem_mesh* mesh);
 

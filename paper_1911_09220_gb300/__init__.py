@@ -101,16 +101,18 @@ class Mesh:
         self.geo_nodes, self.geo_order = None, 0
 
     def set_nodes(self, nodes, k):
-        """Curved geometry: element nodal coordinates [ne, (k+1)^3, 3] at the
-        order-k GLL lattice (x fastest, element's local frame); k = 0 returns
-        to the vertex map. Set before creating forms (or call set_coef)."""
+        """Curved geometry: element nodal coordinates [ne, (k+1)^dim, dim] at
+        the order-k GLL lattice (x fastest, element's local frame); k = 0
+        returns to the vertex map. Set before creating forms (or call
+        set_coef)."""
         if k == 0:
             B.check(B.lib().fem_mesh_set_nodes(self._h, 0, None))
             self.geo_nodes, self.geo_order = None, 0
             return
         n = np.ascontiguousarray(nodes, dtype=np.float64)
-        if n.shape != (self.ne, (k + 1) ** 3, 3):
-            raise ValueError(f"nodes must be [{self.ne}, {(k + 1) ** 3}, 3]")
+        d = self.dim
+        if n.shape != (self.ne, (k + 1) ** d, d):
+            raise ValueError(f"nodes must be [{self.ne}, {(k + 1) ** d}, {d}]")
         B.check(B.lib().fem_mesh_set_nodes(self._h, int(k), n.ctypes.data))
         self.geo_nodes, self.geo_order = n, int(k)
 

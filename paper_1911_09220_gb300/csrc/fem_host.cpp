@@ -100,15 +100,16 @@ extern "C" void fem_mesh_destroy(fem_mesh* m) {
 
 extern "C" fem_status fem_mesh_set_nodes(fem_mesh* m, int k, const double* nodes_host) {
   if (!m) return fem_fail(FEM_EINVAL, "fem_mesh_set_nodes: NULL mesh");
-  if (m->dim != 3) return fem_fail(FEM_EUNSUPPORTED, "fem_mesh_set_nodes: hexahedral meshes only");
-  if (k == 0) {  // back to the vertex (trilinear) geometry
+  if (k == 0) {  // back to the vertex (multilinear) geometry
     dev_free(m->d_gnodes);
     m->geo_k = 0;
     return FEM_OK;
   }
   if (k < 1 || k > 8) return fem_fail(FEM_EINVAL, "fem_mesh_set_nodes: order %d not in 1..8", k);
   if (!nodes_host) return fem_fail(FEM_EINVAL, "fem_mesh_set_nodes: NULL nodes");
-  const size_t n = (size_t)m->ne * (k + 1) * (k + 1) * (k + 1) * 3;
+  // [ne][(k+1)^dim][dim]
+  const size_t per = m->dim == 3 ? (size_t)(k + 1) * (k + 1) * (k + 1) * 3 : (size_t)(k + 1) * (k + 1) * 2;
+  const size_t n = (size_t)m->ne * per;
   for (size_t i = 0; i < n; ++i)
     if (!std::isfinite(nodes_host[i])) return fem_fail(FEM_EINVAL, "fem_mesh_set_nodes: non-finite coordinate");
   double* d = nullptr;

@@ -1,7 +1,8 @@
 // Quadrilateral (2D) counterparts of the partial-assembly kernels.
 //
-// Geometry: bilinear map of the 4 vertices on [0,1]^2 (Sec. 3.1), local
-// vertex order (0,0), (1,0), (1,1), (0,1). Quadrature data of the 2D
+// Geometry (Sec. 3.1): the bilinear map of the 4 vertices on [0,1]^2, local
+// vertex order (0,0), (1,0), (1,1), (0,1), or the order-k nodal map of a
+// curved mesh (fem_mesh_set_nodes). Quadrature data of the 2D
 // diffusion setup (Sec. 5.3): D_q = coef w_q adj(J) adj(J)^T / det J, three
 // symmetric components (00, 01, 11) per point, point-major [ne][q1d^2][3];
 // mass D_q = coef w_q det J, [ne][q1d^2].
@@ -24,9 +25,14 @@
 
 namespace {
 
-struct Quad4 {
+// Bilinear map of the 4 vertex coordinates; (qx, qy) index the 1D points
+// pts (Gauss points for quadrature data, GLL nodes for DOF coordinates).
+struct Quad4Geo {
+  const double* coords;
+  const int32_t* quad;
+  const double* pts;
   double X[4][2];
-  __device__ void load(const double* __restrict__ coords, const int32_t* __restrict__ quad, int64_t e) {
+  __device__ void load(int64_t e) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int32_t g = quad[4 * e + v];
@@ -36,7 +42,8 @@ struct Quad4 {
   }
   __device__ static int cx(int v) { return v == 1 || v == 2; }
   __device__ static int cy(int v) { return v >= 2; }
-  __device__ void map(double a, double b, double x[2]) const {
+  __device__ void map(int qx, int qy, double x[2]) const {
+    const double a = pts[qx], b = pts[qy];
     x[0] = x[1] = 0.0;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -46,7 +53,8 @@ struct Quad4 {
     }
   }
   // J[r][c] = d x_r / d xhat_c
-  __device__ void jacobian(double a, double b, double J[2][2]) const {
+  __device__ void jacobian(int qx, int qy, double J[2][2]) const {
+    const double a = pts[qx], b = pts[qy];
     J[0][0] = J[0][1] = J[1][0] = J[1][1] = 0.0;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -61,21 +69,60 @@ struct Quad4 {
   }
 };
 
+// Order-k nodal map of the square: x(xhat) = sum_i X_i w_i(xhat) with the
+// (k+1)^2 GLL Lagrange products w_i (first index fastest, in the element's
+// local vertex frame) and element e's nodal coordinates X [(k+1)^2][2].
+// gB, gG [npts][k+1]: the 1D functions and derivatives at the 1D points that
+// (qx, qy) index.
+struct NodalGeo2 {
+  const double* nodes;  // [ne][(k+1)^2][2]
+  const double* gB;
+  const double* gG;
+  int K;                // k + 1
+  const double* Xe;
+  __device__ void load(int64_t e) { Xe = nodes + e * (int64_t)K * K * 2; }
+  __device__ void jacobian(int qx, int qy, double J[2][2]) const {
+    J[0][0] = J[0][1] = J[1][0] = J[1][1] = 0.0;
+    for (int i2 = 0; i2 < K; ++i2) {
+      const double b2 = gB[qy * K + i2], g2 = gG[qy * K + i2];
+      for (int i1 = 0; i1 < K; ++i1) {
+        const double w0 = gG[qx * K + i1] * b2, w1 = gB[qx * K + i1] * g2;
+        const double* x = Xe + 2 * (i2 * K + i1);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          J[r][0] += x[r] * w0;
+          J[r][1] += x[r] * w1;
+        }
+      }
+    }
+  }
+  __device__ void map(int qx, int qy, double xo[2]) const {
+    xo[0] = xo[1] = 0.0;
+    for (int i2 = 0; i2 < K; ++i2) {
+      const double b2 = gB[qy * K + i2];
+      for (int i1 = 0; i1 < K; ++i1) {
+        const double w = gB[qx * K + i1] * b2;
+        const double* x = Xe + 2 * (i2 * K + i1);
+        xo[0] += x[0] * w;
+        xo[1] += x[1] * w;
+      }
+    }
+  }
+};
+
 // One thread per (element, quadrature point); q = qx + Q qy.
-__global__ void k_setup_2d(int64_t ne, int Q, int kind, const double* __restrict__ coords,
-                           const int32_t* __restrict__ quad, const double* __restrict__ qpts,
-                           const double* __restrict__ qwts, const double* __restrict__ coef,
-                           double* __restrict__ Dout, int* __restrict__ flag) {
+template <typename Geo>
+__global__ void k_setup_2d(int64_t ne, int Q, int kind, Geo h, const double* __restrict__ qwts,
+                           const double* __restrict__ coef, double* __restrict__ Dout, int* __restrict__ flag) {
   const int nq = Q * Q;
   const int64_t total = ne * nq;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = t / nq;
     const int q = (int)(t % nq), qx = q % Q, qy = q / Q;
-    Quad4 h;
-    h.load(coords, quad, e);
+    h.load(e);
     double J[2][2];
-    h.jacobian(qpts[qx], qpts[qy], J);
+    h.jacobian(qx, qy, J);
     const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
     if (!(det > 0.0)) {
       if (atomicExch(&flag[0], 1) == 0) flag[1] = (int)e;
@@ -94,38 +141,36 @@ __global__ void k_setup_2d(int64_t ne, int Q, int kind, const double* __restrict
   }
 }
 
-__global__ void k_qpoint_coords_2d(int64_t ne, int Q, const double* __restrict__ coords,
-                                   const int32_t* __restrict__ quad, const double* __restrict__ qpts,
-                                   double* __restrict__ xq) {
+template <typename Geo>
+__global__ void k_qpoint_coords_2d(int64_t ne, int Q, Geo h, double* __restrict__ xq) {
   const int nq = Q * Q;
   const int64_t total = ne * nq;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = t / nq;
     const int q = (int)(t % nq);
-    Quad4 h;
-    h.load(coords, quad, e);
+    h.load(e);
     double x[2];
-    h.map(qpts[q % Q], qpts[q / Q], x);
+    h.map(q % Q, q / Q, x);
     xq[2 * t] = x[0];
     xq[2 * t + 1] = x[1];
   }
 }
 
-__global__ void k_dof_coords_2d(int64_t ndof, int D1, const double* __restrict__ coords,
-                                const int32_t* __restrict__ quad, const int32_t* __restrict__ off,
-                                const int32_t* __restrict__ idx, const double* __restrict__ nodes,
-                                double* __restrict__ out) {
+// Coordinates of each DOF's GLL node, from the first element holding it
+// (the geometry's 1D points are this space's GLL nodes).
+template <typename Geo>
+__global__ void k_dof_coords_2d(int64_t ndof, int D1, Geo h, const int32_t* __restrict__ off,
+                                const int32_t* __restrict__ idx, double* __restrict__ out) {
   const int nd = D1 * D1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ndof;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t slot = idx[off[i]];
     const int64_t e = slot / nd;
     const int k = slot % nd;
-    Quad4 h;
-    h.load(coords, quad, e);
+    h.load(e);
     double x[2];
-    h.map(nodes[k % D1], nodes[k / D1], x);
+    h.map(k % D1, k / D1, x);
     out[2 * i] = x[0];
     out[2 * i + 1] = x[1];
   }
@@ -178,23 +223,21 @@ __global__ void k_diag_2d(int64_t ne, int D1, int Q, int kind, const double* __r
 
 // Load vector b_e[i] = sum_q w_q det J_q fq[e][q] phi_i(x_q), one thread per
 // (element, local DOF).
-__global__ void k_rhs_2d(int64_t ne, int D1, int Q, const double* __restrict__ coords,
-                         const int32_t* __restrict__ quad, const double* __restrict__ qpts,
-                         const double* __restrict__ qwts, const double* __restrict__ B, const double* __restrict__ fq,
-                         double* __restrict__ ye) {
+template <typename Geo>
+__global__ void k_rhs_2d(int64_t ne, int D1, int Q, Geo h, const double* __restrict__ qwts,
+                         const double* __restrict__ B, const double* __restrict__ fq, double* __restrict__ ye) {
   const int nd = D1 * D1, nq = Q * Q;
   const int64_t total = ne * nd;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = t / nd;
     const int i = (int)(t % nd), ix = i % D1, iy = i / D1;
-    Quad4 h;
-    h.load(coords, quad, e);
+    h.load(e);
     double acc = 0.0;
     for (int qy = 0; qy < Q; ++qy)
       for (int qx = 0; qx < Q; ++qx) {
         double J[2][2];
-        h.jacobian(qpts[qx], qpts[qy], J);
+        h.jacobian(qx, qy, J);
         const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
         acc += qwts[qx] * qwts[qy] * det * fq[e * nq + qx + Q * qy] * B[qx * D1 + ix] * B[qy * D1 + iy];
       }
@@ -238,24 +281,57 @@ fem_status fem_2d_tables_init() { return fem_tables_ensure(); }
 
 fem_status fem_launch_setup_2d(const fem_form* f, cudaStream_t s) {
   const fem_space* sp = f->space;
-  k_setup_2d<<<grid_for(sp->ne * f->nq, 256), 256, 0, s>>>(sp->ne, f->q1d, f->kind, sp->mesh->d_coords,
-                                                           sp->mesh->d_hex, f->d_qpts, f->d_qwts, f->d_coef,
-                                                           f->d_D, f->d_flag);
+  const fem_mesh* m = sp->mesh;
+  const int grid = grid_for(sp->ne * f->nq, 256);
+  if (m->geo_k > 0) {
+    FEM_TRY(fem_form_geo_tables(f));
+    const NodalGeo2 g{m->d_gnodes, f->d_gB, f->d_gG, m->geo_k + 1, nullptr};
+    k_setup_2d<NodalGeo2><<<grid, 256, 0, s>>>(sp->ne, f->q1d, f->kind, g, f->d_qwts, f->d_coef, f->d_D, f->d_flag);
+  } else {
+    const Quad4Geo g{m->d_coords, m->d_hex, f->d_qpts, {}};
+    k_setup_2d<Quad4Geo><<<grid, 256, 0, s>>>(sp->ne, f->q1d, f->kind, g, f->d_qwts, f->d_coef, f->d_D, f->d_flag);
+  }
   FEM_LAUNCHED();
   return FEM_OK;
 }
 
 fem_status fem_launch_qpoint_coords_2d(const fem_form* f, double* xq, cudaStream_t s) {
   const fem_space* sp = f->space;
-  k_qpoint_coords_2d<<<grid_for(sp->ne * f->nq, 256), 256, 0, s>>>(sp->ne, f->q1d, sp->mesh->d_coords,
-                                                                   sp->mesh->d_hex, f->d_qpts, xq);
+  const fem_mesh* m = sp->mesh;
+  const int grid = grid_for(sp->ne * f->nq, 256);
+  if (m->geo_k > 0) {
+    FEM_TRY(fem_form_geo_tables(f));
+    const NodalGeo2 g{m->d_gnodes, f->d_gB, f->d_gG, m->geo_k + 1, nullptr};
+    k_qpoint_coords_2d<NodalGeo2><<<grid, 256, 0, s>>>(sp->ne, f->q1d, g, xq);
+  } else {
+    const Quad4Geo g{m->d_coords, m->d_hex, f->d_qpts, {}};
+    k_qpoint_coords_2d<Quad4Geo><<<grid, 256, 0, s>>>(sp->ne, f->q1d, g, xq);
+  }
   FEM_LAUNCHED();
   return FEM_OK;
 }
 
 fem_status fem_launch_dof_coords_2d(const fem_space* sp, double* out, cudaStream_t s) {
-  k_dof_coords_2d<<<grid_for(sp->ndof, 256), 256, 0, s>>>(sp->ndof, sp->D1, sp->mesh->d_coords, sp->mesh->d_hex,
-                                                          sp->d_l2e_off, sp->d_l2e_idx, sp->d_nodes, out);
+  const fem_mesh* m = sp->mesh;
+  const int grid = grid_for(sp->ndof, 256);
+  if (m->geo_k > 0) {
+    // order-k geometry functions at this space's GLL nodes, [D1][k+1]
+    fem_space* spm = const_cast<fem_space*>(sp);
+    if (spm->gBn_k != m->geo_k) {
+      std::vector<double> nk, B, G;
+      fem_gll_nodes(m->geo_k, nk);
+      fem_lagrange_tables(nk, sp->nodes, B, G);
+      dev_free(spm->d_gBn);
+      FEM_TRY(dev_alloc(&spm->d_gBn, B.size()));
+      FEM_CUDA(cudaMemcpy(spm->d_gBn, B.data(), sizeof(double) * B.size(), cudaMemcpyHostToDevice));
+      spm->gBn_k = m->geo_k;
+    }
+    const NodalGeo2 g{m->d_gnodes, sp->d_gBn, sp->d_gBn, m->geo_k + 1, nullptr};
+    k_dof_coords_2d<NodalGeo2><<<grid, 256, 0, s>>>(sp->ndof, sp->D1, g, sp->d_l2e_off, sp->d_l2e_idx, out);
+  } else {
+    const Quad4Geo g{m->d_coords, m->d_hex, sp->d_nodes, {}};
+    k_dof_coords_2d<Quad4Geo><<<grid, 256, 0, s>>>(sp->ndof, sp->D1, g, sp->d_l2e_off, sp->d_l2e_idx, out);
+  }
   FEM_LAUNCHED();
   return FEM_OK;
 }
@@ -297,8 +373,16 @@ fem_status fem_launch_diag_element_2d(const fem_form* f, double* ye, cudaStream_
 
 fem_status fem_launch_rhs_element_2d(const fem_form* f, const double* fq, double* ye, cudaStream_t s) {
   const fem_space* sp = f->space;
-  k_rhs_2d<<<grid_for(sp->ne * sp->nd, 256), 256, 0, s>>>(sp->ne, sp->D1, f->q1d, sp->mesh->d_coords,
-                                                          sp->mesh->d_hex, f->d_qpts, f->d_qwts, f->d_B, fq, ye);
+  const fem_mesh* m = sp->mesh;
+  const int grid = grid_for(sp->ne * sp->nd, 256);
+  if (m->geo_k > 0) {
+    FEM_TRY(fem_form_geo_tables(f));
+    const NodalGeo2 g{m->d_gnodes, f->d_gB, f->d_gG, m->geo_k + 1, nullptr};
+    k_rhs_2d<NodalGeo2><<<grid, 256, 0, s>>>(sp->ne, sp->D1, f->q1d, g, f->d_qwts, f->d_B, fq, ye);
+  } else {
+    const Quad4Geo g{m->d_coords, m->d_hex, f->d_qpts, {}};
+    k_rhs_2d<Quad4Geo><<<grid, 256, 0, s>>>(sp->ne, sp->D1, f->q1d, g, f->d_qwts, f->d_B, fq, ye);
+  }
   FEM_LAUNCHED();
   return FEM_OK;
 }

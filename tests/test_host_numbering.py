@@ -227,7 +227,14 @@ def test_set_nodes_validation(hostlib):
     assert np.array_equal(e2l, numbering.build(h, 2, nv=c.shape[0])["e2l"])
     L.fem_space_destroy(s)
     L.fem_mesh_destroy(m)
+    # quadrilateral meshes take [ne][(k+1)^2][2] nodes: exactly that many
+    # values are read and checked (a non-finite last value is caught)
     cq, q = quad_lattice(2, 0.0, seed=1)
     m2 = _mesh(L, cq, q, 2)
-    assert f(m2, 2, good.ctypes.data) == 7                # hexahedral meshes only
+    E2 = q.shape[0]
+    g2 = np.zeros((E2, 9, 2))
+    assert f(m2, 2, g2.ctypes.data) == 0
+    g2[-1, -1, -1] = np.nan
+    assert f(m2, 2, g2.ctypes.data) == 1
+    assert f(m2, 0, None) == 0
     L.fem_mesh_destroy(m2)

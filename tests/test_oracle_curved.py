@@ -86,3 +86,78 @@ def test_invariance_under_renumbering():
     perm = np.empty(P0.ndof, dtype=np.int64)
     perm[o0] = o1
     np.testing.assert_allclose(P1.K.toarray()[np.ix_(perm, perm)], P0.K.toarray(), atol=1e-11)
+
+
+# ---------------------------------------------------------------- 2D ----
+from fem_inputs import quad_lattice
+from oracle import twod
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_bilinear_as_nodes_2d(k, p):
+    c, q = quad_lattice(3, 0.2, seed=13, shuffle=True)
+    kap = lognormal(14, q.shape[0])
+    bil = twod.Problem2(c, q, p, p + 2, kappa=kap, rho=kap)
+    Xn = curved.nodes_from_corners2(c[q.astype(np.int64)], k)
+    if k == 1:  # the order-1 lattice (x fastest) visits the corners 0, 1, 3, 2
+        np.testing.assert_array_equal(Xn, c[q.astype(np.int64)][:, [0, 1, 3, 2]])
+    cp = curved.CurvedProblem2(q, Xn, k, p, p + 2, kappa=kap, rho=kap, nv=c.shape[0])
+    for kind in ("diffusion", "mass"):
+        A, B = cp.matrix(kind).toarray(), bil.matrix(kind).toarray()
+        assert np.abs(A - B).max() <= 1e-13 * np.abs(B).max()
+    np.testing.assert_allclose(cp.dof_coords(), bil.dof_coords(), atol=1e-14)
+    np.testing.assert_allclose(cp.qpoint_coords(), bil.qpoint_coords(), atol=1e-14)
+
+
+def test_area_of_polynomial_map_2d():
+    """Single element, Phi(x, y) = (x (1 + a y^2), y (1 + b x^2)): degree
+    <= 2 per variable, so order-2 GLL nodes reproduce it exactly and the mass
+    matrix's total equals int det(grad Phi) over the unit square (the right
+    and top edges are curved, so the area is not 1)."""
+    a, b = 0.35, -0.3
+    xs, ys = sy.symbols("x y")
+    Phi = sy.Matrix([xs * (1 + a * ys ** 2), ys * (1 + b * xs ** 2)])
+    area = float(sy.integrate(Phi.jacobian([xs, ys]).det(), (xs, 0, 1), (ys, 0, 1)))
+    xi = curved.lattice_nodes2(2)
+    f = sy.lambdify((xs, ys), Phi, "numpy")
+    Xn = np.stack([np.asarray(f(*pt), dtype=np.float64).ravel() for pt in xi])[None]
+    cp = curved.CurvedProblem2(np.arange(4)[None], Xn, 2, 2, 5)
+    one = np.ones(cp.ndof)
+    assert one @ (cp.M @ one) == pytest.approx(area, abs=1e-14)
+    assert abs(area - 1.0) > 1e-3          # the map is not area preserving
+    # and the stiffness matrix annihilates constants
+    assert np.abs(cp.K @ one).max() <= 1e-13 * abs(cp.K).max()
+
+
+@pytest.mark.parametrize("k,p", [(2, 2), (2, 3), (3, 3), (4, 5)])
+def test_isoparametric_patch_test_2d(k, p):
+    c, q = quad_lattice(4, 0.1, seed=15)
+    Xg = curved_nodes(c, q, k, amp=0.06)
+    cp = curved.CurvedProblem2(q, Xg, k, p, p + 2, nv=c.shape[0])
+    X = cp.dof_coords()
+    bnd = cp.num["boundary_mask"]
+    Kd = cp.K
+    for g in (np.array([1.0, 0.0]), np.array([0.3, -1.1])):
+        r = Kd @ (X @ g + 0.25)
+        assert np.abs(r[~bnd]).max() <= 1e-11 * abs(Kd).max()
+    one = np.ones(cp.ndof)
+    assert np.abs(Kd @ one).max() <= 1e-12 * abs(Kd).max()
+    assert one @ (cp.M @ one) == pytest.approx(1.0, abs=1e-12)   # the boundary stays on the unit square
+    bil = twod.Problem2(c, q, p, p + 2)
+    assert np.abs(cp.M.toarray() - bil.M.toarray()).max() > 1e-6
+
+
+def test_invariance_under_renumbering_2d():
+    k, p = 3, 2
+    c0, q0 = quad_lattice(3, 0.1, seed=17)
+    c1, q1 = quad_lattice(3, 0.1, seed=17, shuffle=True, shuffle_seed=19)
+    P0 = curved.CurvedProblem2(q0, curved_nodes(c0, q0, k), k, p, p + 2, nv=c0.shape[0])
+    P1 = curved.CurvedProblem2(q1, curved_nodes(c1, q1, k), k, p, p + 2, nv=c1.shape[0])
+    X0, X1 = P0.dof_coords(), P1.dof_coords()
+    key = lambda X: np.lexsort(np.round(X, 11).T[::-1])
+    o0, o1 = key(X0), key(X1)
+    np.testing.assert_allclose(X0[o0], X1[o1], atol=1e-12)
+    perm = np.empty(P0.ndof, dtype=np.int64)
+    perm[o0] = o1
+    np.testing.assert_allclose(P1.K.toarray()[np.ix_(perm, perm)], P0.K.toarray(), atol=1e-11)
