@@ -299,8 +299,12 @@ typedef struct {
   double rtol;          /* relative tolerance, e.g. 1e-10 */
   int maxit;            /* cap on (inner, for mixed) CG iterations */
   int precision;        /* FEM_SOLVE_F64 or FEM_SOLVE_MIXED */
-  double inner_rtol;    /* mixed: inner relative tolerance (e.g. 1e-4); reliable
-                           updates: residual drop between updates (e.g. 1e-2) */
+  double inner_rtol;    /* mixed: inner relative tolerance; reliable updates:
+                           residual drop between updates; <= 0 (the default)
+                           takes the measured default of the call and mode:
+                           fem_solve 1e-3 (FEM_SOLVE_MIXED), 0.1
+                           (FEM_SOLVE_MIXED_RU); fem_mg_solve 3e-4;
+                           fem_batch_solve 1e-4 */
   int max_outer;        /* mixed: cap on refinement steps */
   int check_every;      /* iterations per CUDA-graph launch between host polls */
   int use_graph;        /* capture check_every iterations in a CUDA graph */

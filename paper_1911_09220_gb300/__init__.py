@@ -334,15 +334,14 @@ class Form:
               check_every=16, use_graph=True, stream=None, raise_on_error=True, precond="jacobi"):
         """Jacobi-PCG on the constrained operator. precision: "f64", "df64"
         (FP64 CG, double-float operator), "mixed" (FP32 inner CG restarted in
-        FP64 refinement; inner_rtol default 1e-4) or "mixed_ru" (FP32 CG with
+        FP64 refinement; inner_rtol default 1e-3) or "mixed_ru" (FP32 CG with
         FP64 reliable updates; inner_rtol = residual drop between updates,
-        default 1e-2). precond: "jacobi" or "none" (plain CG)."""
+        default 0.1). None takes the library's measured default.
+        precond: "jacobi" or "none" (plain CG)."""
         import torch
         o = B.SolveOpts()
         B.lib().fem_solve_opts_default(C.byref(o))
-        if inner_rtol is None:
-            inner_rtol = 1e-2 if precision == "mixed_ru" else 1e-4
-        o.rtol, o.maxit, o.inner_rtol, o.max_outer = rtol, maxit, inner_rtol, max_outer
+        o.rtol, o.maxit, o.inner_rtol, o.max_outer = rtol, maxit, inner_rtol or 0.0, max_outer
         o.precision = {"f64": FEM_SOLVE_F64, "mixed": FEM_SOLVE_MIXED, "df64": FEM_SOLVE_DF64,
                        "mixed_ru": FEM_SOLVE_MIXED_RU}[precision]
         o.check_every, o.use_graph = check_every, int(bool(use_graph))
@@ -408,12 +407,12 @@ class Batch:
                                         int(bool(constrained)), _stream(stream)))
         return Y
 
-    def solve(self, Bv, X, rtol=1e-10, maxit=20000, precision="f64", inner_rtol=1e-4, max_outer=30,
+    def solve(self, Bv, X, rtol=1e-10, maxit=20000, precision="f64", inner_rtol=None, max_outer=30,
               check_every=16, use_graph=True, stream=None, raise_on_error=True):
         import torch
         o = B.SolveOpts()
         B.lib().fem_solve_opts_default(C.byref(o))
-        o.rtol, o.maxit, o.inner_rtol, o.max_outer = rtol, maxit, inner_rtol, max_outer
+        o.rtol, o.maxit, o.inner_rtol, o.max_outer = rtol, maxit, inner_rtol or 0.0, max_outer
         o.precision = FEM_SOLVE_MIXED if precision == "mixed" else FEM_SOLVE_F64
         o.check_every, o.use_graph = check_every, int(bool(use_graph))
         iters = np.zeros(self.nsys, dtype=np.int32)
@@ -500,7 +499,7 @@ class Multigrid:
         return z
 
     def solve(self, b, x, rtol=1e-10, maxit=500, max_outer=30, check_every=4, use_graph=True, stream=None,
-              raise_on_error=True, arith="f64", inner_rtol=1e-4):
+              raise_on_error=True, arith="f64", inner_rtol=None):
         """Flexible CG with one V-cycle per iteration. arith, the outer
         operator apply: "f64", "df64" (double-float), or "f32" (FP32 operator
         inside FP64 iterative refinement: each pass reduces the residual by
@@ -512,7 +511,7 @@ class Multigrid:
         if arith not in ("f64", "df64", "f32"):
             raise ValueError(f"arith must be 'f64', 'df64' or 'f32', not {arith!r}")
         o.precision = {"f64": FEM_SOLVE_F64, "df64": FEM_SOLVE_DF64, "f32": FEM_SOLVE_MIXED}[arith]
-        o.inner_rtol = inner_rtol
+        o.inner_rtol = inner_rtol or 0.0
         o.check_every, o.use_graph = check_every, int(bool(use_graph))
         info = B.SolveInfo()
         st = B.lib().fem_mg_solve(self._h, _ptr(b, torch.float64, "b"), _ptr(x, torch.float64, "x"), C.byref(o),

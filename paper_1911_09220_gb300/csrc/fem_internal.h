@@ -160,6 +160,9 @@ struct fem_shard {
 
 // Length of the form's vectors: vdim * ndof (component-major).// Length of the form's vectors: vdim * ndof (component-major).
 inline int64_t fem_form_len(const fem_form* f) { return (int64_t)f->vdim * f->space->ndof; }
+// opts.inner_rtol, or, when it is <= 0, the default of fem_solve (which 0;
+// by precision), fem_mg_solve (1) or fem_batch_solve (2); k_solve.cu.
+double fem_inner_rtol(const fem_solve_opts& o, int which);
 
 // ---------------------------------------------------------------- basis -----
 // 1D tables on [0,1]: GLL nodes (D1 = p+1), Gauss-Legendre points/weights (q),

@@ -896,6 +896,7 @@ extern "C" fem_status fem_batch_solve(fem_batch* b, const double* Bv, double* Xv
   if (opts) o = *opts;
   if (!(o.rtol > 0) || o.maxit <= 0) return fem_fail(FEM_EINVAL, "fem_batch_solve: rtol > 0 and maxit > 0 required");
   if (o.precond != FEM_PC_JACOBI) return fem_fail(FEM_EUNSUPPORTED, "fem_batch_solve: Jacobi preconditioner only");
+  o.inner_rtol = fem_inner_rtol(o, 2);
   const bool mixed = o.precision == FEM_SOLVE_MIXED;
   cudaStream_t s = (cudaStream_t)stream;
   for (int i = 0; i < b->nprob; ++i)

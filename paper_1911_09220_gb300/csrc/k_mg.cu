@@ -1330,8 +1330,9 @@ extern "C" fem_status fem_mg_solve(fem_mg* m, const double* b, double* xio, cons
   if (o.precision != FEM_SOLVE_F64 && o.precision != FEM_SOLVE_DF64 && o.precision != FEM_SOLVE_MIXED)
     return fem_fail(FEM_EINVAL, "fem_mg_solve: precision must be FEM_SOLVE_F64, FEM_SOLVE_DF64 or FEM_SOLVE_MIXED");
   const bool mixed = o.precision == FEM_SOLVE_MIXED;
-  if (mixed && !(o.inner_rtol > 0.0 && o.inner_rtol < 1.0))
-    return fem_fail(FEM_EINVAL, "fem_mg_solve: FEM_SOLVE_MIXED needs 0 < inner_rtol < 1");
+  o.inner_rtol = fem_inner_rtol(o, 1);
+  if (mixed && !(o.inner_rtol < 1.0))
+    return fem_fail(FEM_EINVAL, "fem_mg_solve: FEM_SOLVE_MIXED needs inner_rtol < 1");
   const int dtype = o.precision == FEM_SOLVE_DF64 ? FEM_DF64 : mixed ? FEM_F32 : FEM_F64;
   cudaStream_t s = (cudaStream_t)stream;
   const MgLevel& L = m->lv[0];

@@ -536,12 +536,27 @@ extern "C" fem_status fem_compliance(const fem_form* fc, const double* b, const 
   return FEM_OK;
 }
 
+// inner_rtol <= 0 selects the default of the mode, measured on the
+// ~2e7-DOF p = 4 and p = 6 diffusion problems (lognormal kappa, perturbed
+// hexes): restarted FP32 inner CG 1e-3 (1e-4: p = 4 1.77 -> 1.68 s, p = 6
+// 1.76 -> 1.43 s), reliable updates 0.1 (1e-2: 2.30 -> 1.44 s, 2.78 ->
+// 1.35 s), the multigrid FP32 outer operator 3e-4, the batched mixed solve
+// 1e-4 (1e-3 was slower there).
+double fem_inner_rtol(const fem_solve_opts& o, int which) {
+  if (o.inner_rtol > 0) return o.inner_rtol;
+  switch (which) {
+    case 1: return 3e-4;   // fem_mg_solve, FP32 outer operator
+    case 2: return 1e-4;   // fem_batch_solve
+    default: return o.precision == FEM_SOLVE_MIXED_RU ? 0.1 : 1e-3;
+  }
+}
+
 extern "C" void fem_solve_opts_default(fem_solve_opts* o) {
   if (!o) return;
   o->rtol = 1e-10;
   o->maxit = 20000;
   o->precision = FEM_SOLVE_F64;
-  o->inner_rtol = 1e-4;
+  o->inner_rtol = 0.0;  // the mode's measured default (fem_inner_rtol)
   o->max_outer = 30;
   o->check_every = 16;
   o->use_graph = 1;
@@ -557,6 +572,7 @@ extern "C" fem_status fem_solve(const fem_form* fc, const double* b, double* xio
   fem_solve_opts_default(&o);
   if (opts) o = *opts;
   if (!(o.rtol > 0) || o.maxit <= 0) return fem_fail(FEM_EINVAL, "fem_solve: rtol > 0 and maxit > 0 required");
+  o.inner_rtol = fem_inner_rtol(o, 0);
   if (o.precision != FEM_SOLVE_F64 && o.precision != FEM_SOLVE_MIXED && o.precision != FEM_SOLVE_DF64 &&
       o.precision != FEM_SOLVE_MIXED_RU)
     return fem_fail(FEM_EINVAL, "fem_solve: unknown precision %d", o.precision);
