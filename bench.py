@@ -1211,11 +1211,20 @@ def main():
     t32e = time_events(lambda: form.apply_element(x32, ye32), args.steps, 2)
     t32 = time_events(lambda: form.apply(x32, y32), args.steps, 2)
     _, bytes32 = alg_counts(p, q, E, n, fp=4)
+    # bytes the atomic-free design moves on top of the algorithmic ones: the
+    # inverse map (one int32 slot position per element slot and one offset
+    # per DOF) and the E-vector written by the element kernel and read by the
+    # scatter (counted separately, as implementation overheads)
+    nd = (p + 1) ** 3
+    impl32 = bytes32 + 4 * nd * E + 4 * (n + 1) + 2 * 4 * nd * E
+    hbm = peaks().get("hbm_gbs", 6800.0)
     fp32 = {"gdofs": n / (t32 * 1e-3) / 1e9, "ms_per_apply": t32, "element_kernel_ms": t32e,
             "element_kernel_hbm_gbs": (bytes32 - 8 * n + 4 * n) / (t32e * 1e-3) / 1e9,
             "apply_alg_gbs": bytes32 / (t32 * 1e-3) / 1e9,
-            "apply_frac_of_hbm": bytes32 / (t32 * 1e-3) / 1e9 / peaks().get("hbm_gbs", 6800.0),
-            "alg_bytes_per_apply": bytes32}
+            "apply_frac_of_hbm": bytes32 / (t32 * 1e-3) / 1e9 / hbm,
+            "alg_bytes_per_apply": bytes32,
+            "impl_bytes_per_apply": impl32,
+            "apply_frac_of_hbm_impl_bytes": impl32 / (t32 * 1e-3) / 1e9 / hbm}
     del x32, y32, ye32
     # double-float element arithmetic (FP64 vectors, FP32 pipe)
     form.apply(x, y, arith="df64")
