@@ -292,7 +292,8 @@ fem_status fem_qpoint_coords(const fem_form* form, double* xq, void* stream);
  * true residual (recomputed in FP64 at exit; the iteration restarts from x if
  * the recursive residual drifted). precision FEM_SOLVE_MIXED runs FP32 inner
  * Jacobi-PCG to inner_rtol on FP32 copies of D, inside FP64 iterative
- * refinement (FP64 outer residual, norms and updates).
+ * refinement (FP64 outer residual, norms and updates; a pass that needs less
+ * than inner_rtol to reach the tolerance stops at half of it).
  * precond FEM_PC_NONE replaces the Jacobi diagonal by ones.
  * Synchronises `stream`. Errors: FEM_ENOCONV, FEM_EBREAKDOWN. */
 typedef struct {
@@ -302,7 +303,7 @@ typedef struct {
   double inner_rtol;    /* mixed: inner relative tolerance; reliable updates:
                            residual drop between updates; <= 0 (the default)
                            takes the measured default of the call and mode:
-                           fem_solve 1e-3 (FEM_SOLVE_MIXED), 0.1
+                           fem_solve 1e-4 (FEM_SOLVE_MIXED), 0.1
                            (FEM_SOLVE_MIXED_RU); fem_mg_solve 3e-4;
                            fem_batch_solve 1e-4 */
   int max_outer;        /* mixed: cap on refinement steps */

@@ -334,7 +334,7 @@ class Form:
               check_every=16, use_graph=True, stream=None, raise_on_error=True, precond="jacobi"):
         """Jacobi-PCG on the constrained operator. precision: "f64", "df64"
         (FP64 CG, double-float operator), "mixed" (FP32 inner CG restarted in
-        FP64 refinement; inner_rtol default 1e-3) or "mixed_ru" (FP32 CG with
+        FP64 refinement; inner_rtol default 1e-4) or "mixed_ru" (FP32 CG with
         FP64 reliable updates; inner_rtol = residual drop between updates,
         default 0.1). None takes the library's measured default.
         precond: "jacobi" or "none" (plain CG)."""

@@ -17,6 +17,7 @@
 // graph of `check_every` iterations can be replayed and the host only polls
 // between replays. Reductions are block partials summed in a fixed order:
 // results are bitwise reproducible.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -541,16 +542,17 @@ extern "C" fem_status fem_compliance(const fem_form* fc, const double* b, const 
 
 // inner_rtol <= 0 selects the default of the mode, measured on the
 // ~2e7-DOF p = 4 and p = 6 diffusion problems (lognormal kappa, perturbed
-// hexes): restarted FP32 inner CG 1e-3 (1e-4: p = 4 1.77 -> 1.68 s, p = 6
-// 1.76 -> 1.43 s), reliable updates 0.1 (1e-2: 2.30 -> 1.44 s, 2.78 ->
-// 1.35 s), the multigrid FP32 outer operator 3e-4, the batched mixed solve
-// 1e-4 (1e-3 was slower there).
+// hexes) and the p = 2, 8 ones of ~4e6 DOFs: restarted FP32 inner CG 1e-4
+// (with the last pass stopping at half the tolerance; p = 4 1.53 s against
+// 1.67 s at 1e-3), reliable updates 0.1 (1e-2: 2.30 -> 1.44 s at p = 4,
+// 2.78 -> 1.35 s at p = 6), the multigrid FP32 outer operator 3e-4, the
+// batched mixed solve 1e-4 (1e-3 was slower there).
 double fem_inner_rtol(const fem_solve_opts& o, int which) {
   if (o.inner_rtol > 0) return o.inner_rtol;
   switch (which) {
     case 1: return 3e-4;   // fem_mg_solve, FP32 outer operator
     case 2: return 1e-4;   // fem_batch_solve
-    default: return o.precision == FEM_SOLVE_MIXED_RU ? 0.1 : 1e-3;
+    default: return o.precision == FEM_SOLVE_MIXED_RU ? 0.1 : 1e-4;
   }
 }
 
@@ -718,11 +720,14 @@ extern "C" fem_status fem_solve(const fem_form* fc, const double* b, double* xio
       FEM_LAUNCHED();
       FEM_TRY(cg_loop<double>(f, w, op64, w.x, w.r, w.z, w.p, w.q, w.diag, oi, s, &st_in, &it_in));
     } else {
-      // inner FP32 solve of A d = r / ||r|| to inner_rtol, then x += ||r|| d
+      // inner FP32 solve of A d = r / ||r|| to inner_rtol, then x += ||r|| d;
+      // a pass that needs less than that to reach the tolerance stops at half
+      // of the tolerance (rtol ||b|| / 2) instead of a full inner_rtol drop
+      const double inner = std::max(o.inner_rtol, 0.5 * std::sqrt(tol2 / rr));
       k_cast_f32<<<w.nb, 256, 0, s>>>(n, w.diag, w.diag32);
       k_scale_to_f32<<<w.nb, 256, 0, s>>>(n, w.r, rr_dev, w.r32, w.x32);
       k_cg_init<float><<<w.nb, 256, 0, s>>>(n, w.r32, w.diag32, w.z32, w.p32, nullptr, w.part);
-      k_cg_init_scalars<<<1, kRedThreads, 0, s>>>(w.sc, w.part, w.nb, o.inner_rtol, 1.0, oi.maxit);
+      k_cg_init_scalars<<<1, kRedThreads, 0, s>>>(w.sc, w.part, w.nb, inner, 1.0, oi.maxit);
       FEM_LAUNCHED();
       FEM_TRY(cg_loop<float>(f, w, FEM_F32, w.x32, w.r32, w.z32, w.p32, w.q32, w.diag32, oi, s, &st_in, &it_in));
       k_axpy_scaled<<<w.nb, 256, 0, s>>>(n, rr_dev, w.x32, w.x);
