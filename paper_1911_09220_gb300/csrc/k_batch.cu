@@ -995,6 +995,14 @@ extern "C" fem_status fem_batch_solve(fem_batch* b, const double* Bv, double* Xv
       k_bcg_init_scalars<<<(int)ns, 128, 0, s>>>(b->d_probs, b->nrhs, b->sc, b->d_part, b->pstride, o.inner_rtol, 1.0,
                                                  maxit_in);
       FEM_LAUNCHED();
+      // a system whose pass needs less than inner_rtol to reach the tolerance
+      // stops at half of it (tolerances of the normalised inner systems)
+      std::vector<double> tol2(ns);
+      for (int64_t k = 0; k < ns; ++k) {
+        const double need = hrr[k] > 0 ? 0.25 * o.rtol * o.rtol * hbb[k] / hrr[k] : 0.0;
+        tol2[k] = std::max(o.inner_rtol * o.inner_rtol, need);
+      }
+      FEM_CUDA(cudaMemcpyAsync(b->sc.tol2, tol2.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, s));
       FEM_TRY(bcg_loop<float>(b, x32, r32, z32, p32, q32, xz32, o, maxit_in, s));
       FEM_CUDA(cudaMemcpyAsync(b->sc.done, frozen.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
       k_b_axpy<<<b->grid_vec, kBT, 0, s>>>(b->d_probs, b->d_vitems, b->nvitems, b->nrhs, b->sc.scale, b->sc.done, x32,
