@@ -53,7 +53,7 @@ struct BProb {
   const float* B32;
   const float* G32;
   const uint8_t* mask;
-  const double* diag64;
+  const double* diag64;   // reciprocal Jacobi diagonals (FP64, FP32 copy)
   const float* diag32;
 };
 struct BItem {
@@ -253,7 +253,7 @@ __device__ double sys_sum(const double* part, int n, double* red) {
   return block_sum(v, red);
 }
 
-// z = r / diag, p = z; partials r.z, r.r, b.b (b may be null)
+// z = r dinv, p = z; partials r.z, r.r, b.b (b may be null)
 template <typename T>
 __global__ void __launch_bounds__(kBT)
 k_bcg_init(const BProb* __restrict__ probs, const VItem* __restrict__ items, int nitems, int nrhs,
@@ -263,7 +263,7 @@ k_bcg_init(const BProb* __restrict__ probs, const VItem* __restrict__ items, int
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const VItem v = items[it];
     const BProb& P = probs[v.prob];
-    const T* diag = diag_of<T>(P);
+    const T* dinv = diag_of<T>(P);
     const int64_t i0 = (int64_t)v.chunk * kCH, i1 = min(i0 + kCH, P.ndof);
     for (int r = 0; r < nrhs; ++r) {
       if (done && done[P.sys0 + r]) continue;
@@ -273,7 +273,7 @@ k_bcg_init(const BProb* __restrict__ probs, const VItem* __restrict__ items, int
       double bb = 0;
       for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const T ri = R[xo + i];
-        const T zi = ri / diag[i];
+        const T zi = ri * dinv[i];
         Z[xo + i] = zi;
         Pv[xo + i] = zi;
         rz += (A)ri * (A)zi;
@@ -348,7 +348,7 @@ k_bcg_update(const BProb* __restrict__ probs, const VItem* __restrict__ items, i
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const VItem v = items[it];
     const BProb& P = probs[v.prob];
-    const T* diag = diag_of<T>(P);
+    const T* dinv = diag_of<T>(P);
     const int64_t i0 = (int64_t)v.chunk * kCH, i1 = min(i0 + kCH, P.ndof);
     for (int r = 0; r < nrhs; ++r) {
       const int s = P.sys0 + r;
@@ -361,7 +361,7 @@ k_bcg_update(const BProb* __restrict__ probs, const VItem* __restrict__ items, i
         X[xo + i] += a * Pv[xo + i];
         const T ri = R[xo + i] - a * Qv[xo + i];
         R[xo + i] = ri;
-        const T zi = ri / diag[i];
+        const T zi = ri * dinv[i];
         Z[xo + i] = zi;
         rz += (A)ri * (A)zi;
         rr += (A)ri * (A)ri;
@@ -493,6 +493,11 @@ k_b_axpy(const BProb* __restrict__ probs, const VItem* __restrict__ items, int n
       for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) X[xo + i] += sc * (double)D32[xo + i];
     }
   }
+}
+
+__global__ void k_recip_vec(int64_t n, double* __restrict__ a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = 1.0 / a[i];
 }
 
 __global__ void k_cast_vec(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
@@ -912,6 +917,10 @@ extern "C" fem_status fem_batch_solve(fem_batch* b, const double* Bv, double* Xv
     b->hprobs[i].diag32 = mixed ? b->d_diag32 + b->off[i] : nullptr;
     b->hprobs[i].mask = b->forms[i]->d_ess_mask;
   }
+  // the reciprocal diagonals (every iteration multiplies; FP64 divisions per
+  // entry bound the FP64 vector updates on GB300's FP64 pipe)
+  k_recip_vec<<<grid_for(b->off.back(), 256), 256, 0, s>>>(b->off.back(), b->d_diag);
+  FEM_LAUNCHED();
   if (mixed) {
     k_cast_vec<<<grid_for(b->off.back(), 256), 256, 0, s>>>(b->off.back(), b->d_diag, b->d_diag32);
     FEM_LAUNCHED();

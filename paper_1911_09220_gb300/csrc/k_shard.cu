@@ -126,11 +126,11 @@ __global__ void k_sh_ess_rows(int64_t n, const uint8_t* __restrict__ mask, const
 // Scalars (device): S[0] = p.q, S[1] = r.z (new), S[2] = r.r, S[3 + (it & 1)]
 // = r.z of iteration it; all-reduced sums where they are global.
 __global__ void k_sh_cg_start(int64_t n, const double* __restrict__ b, const double* __restrict__ q,
-                              const double* __restrict__ diag, double* __restrict__ r, double* __restrict__ z,
+                              const double* __restrict__ dinv, double* __restrict__ r, double* __restrict__ z,
                               double* __restrict__ p) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double ri = b[i] - q[i];
-    const double zi = ri / diag[i];
+    const double zi = ri * dinv[i];
     r[i] = ri;
     z[i] = zi;
     p[i] = zi;
@@ -139,16 +139,21 @@ __global__ void k_sh_cg_start(int64_t n, const double* __restrict__ b, const dou
 
 __global__ void k_sh_copy_scalar(double* __restrict__ dst, const double* __restrict__ src) { *dst = *src; }
 
-// x += a p, r -= a q, z = r / diag with a = S[3 + par] / S[0].
+__global__ void k_sh_recip(int64_t n, double* __restrict__ a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = 1.0 / a[i];
+}
+
+// x += a p, r -= a q, z = r dinv with a = S[3 + par] / S[0].
 __global__ void k_sh_cg_update(int64_t n, const double* __restrict__ S, int par, double* __restrict__ x,
                                double* __restrict__ r, double* __restrict__ z, const double* __restrict__ p,
-                               const double* __restrict__ q, const double* __restrict__ diag) {
+                               const double* __restrict__ q, const double* __restrict__ dinv) {
   const double a = S[3 + par] / S[0];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] += a * p[i];
     const double ri = r[i] - a * q[i];
     r[i] = ri;
-    z[i] = ri / diag[i];
+    z[i] = ri * dinv[i];
   }
 }
 
@@ -371,6 +376,9 @@ extern "C" fem_status fem_shard_solve(const fem_shard* sh, const fem_form* f, co
     FEM_LAUNCHED();
   } else {
     FEM_TRY(fem_shard_diagonal(sh, f, diag, 1, comm, s));
+    // the reciprocal diagonal: every iteration multiplies instead of dividing
+    k_sh_recip<<<grid_for(n, kT), kT, 0, s>>>(n, diag);
+    FEM_LAUNCHED();
   }
   fem_solve_info inf;
   std::memset(&inf, 0, sizeof inf);

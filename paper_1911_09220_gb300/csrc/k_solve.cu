@@ -6,7 +6,7 @@
 // One iteration is four launches on the solver stream:
 //   element kernel (p -> E-vector), scatter (q = A_c p, partials of p.q),
 //   update (every block sums the p.q partials to alpha; x += a p, r -= a q,
-//   z = r / diag, partials of r.z and r.r), direction (every block sums the
+//   z = r dinv, partials of r.z and r.r), direction (every block sums the
 //   r.z and r.r partials: convergence test, beta; p = z + beta p).
 // The scalar steps run redundantly in every block from the same partials in
 // the same order, so every block takes the same decision and no single-block
@@ -64,14 +64,14 @@ struct Vec16<double> {
 };
 
 template <typename T>
-__global__ void k_cg_init(int64_t n, const T* __restrict__ r, const T* __restrict__ diag, T* __restrict__ z,
+__global__ void k_cg_init(int64_t n, const T* __restrict__ r, const T* __restrict__ dinv, T* __restrict__ z,
                           T* __restrict__ p, const T* __restrict__ b, double* __restrict__ part) {
   __shared__ double red[32];
   using A = typename DotAcc<T>::type;
   A rz = 0, rr = 0, bb = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const T ri = r[i];
-    const T zi = ri / diag[i];
+    const T zi = ri * dinv[i];
     z[i] = zi;
     p[i] = zi;
     rz += (A)ri * (A)zi;
@@ -118,14 +118,14 @@ __global__ void k_cg_init_scalars(CgScalars* sc, const double* __restrict__ part
   }
 }
 
-// x += a p, r -= a q, z = r / diag with a = (r.z) / (p.q), the p.q partials
+// x += a p, r -= a q, z = r dinv with a = (r.z) / (p.q), the p.q partials
 // (pq_part, written by the scatter) summed by every block; partials of r.z
 // and r.r to part_out[0, nb) and part_out[nb, 2 nb). A non-positive or
 // non-finite p.q stops the solve (breakdown) in every block alike.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
 k_cg_update(int64_t n, CgScalars* __restrict__ sc, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
-            const T* __restrict__ p, const T* __restrict__ q, const T* __restrict__ diag,
+            const T* __restrict__ p, const T* __restrict__ q, const T* __restrict__ dinv,
             const double* __restrict__ pq_part, double* __restrict__ part_out, int nb) {
   __shared__ double red[32];
   __shared__ double s_alpha;
@@ -158,7 +158,7 @@ k_cg_update(int64_t n, CgScalars* __restrict__ sc, T* __restrict__ x, T* __restr
   for (int64_t j = tid; j < nv; j += stride) {
     V xv = reinterpret_cast<const V*>(x)[j], rv = reinterpret_cast<const V*>(r)[j];
     const V pv = reinterpret_cast<const V*>(p)[j], qv = reinterpret_cast<const V*>(q)[j];
-    const V dv = reinterpret_cast<const V*>(diag)[j];
+    const V dv = reinterpret_cast<const V*>(dinv)[j];
     V zv;
     T* xs = reinterpret_cast<T*>(&xv);
     T* rs = reinterpret_cast<T*>(&rv);
@@ -171,7 +171,7 @@ k_cg_update(int64_t n, CgScalars* __restrict__ sc, T* __restrict__ x, T* __restr
       xs[u] += a * ps[u];
       const T ri = rs[u] - a * qs[u];
       rs[u] = ri;
-      const T zi = ri / ds[u];
+      const T zi = ri * ds[u];
       zs[u] = zi;
       rz += (A)ri * (A)zi;
       rr += (A)ri * (A)ri;
@@ -184,7 +184,7 @@ k_cg_update(int64_t n, CgScalars* __restrict__ sc, T* __restrict__ x, T* __restr
     x[i] += a * p[i];
     const T ri = r[i] - a * q[i];
     r[i] = ri;
-    const T zi = ri / diag[i];
+    const T zi = ri * dinv[i];
     z[i] = zi;
     rz += (A)ri * (A)zi;
     rr += (A)ri * (A)ri;
@@ -256,16 +256,16 @@ k_cg_direction(int64_t n, CgScalars* __restrict__ sc, const T* __restrict__ z, T
   for (int64_t i = nv * W + tid; i < n; i += stride) p[i] = z[i] + b * p[i];
 }
 
-// After a reliable update replaced r: z = r / diag and partials of r.z.
+// After a reliable update replaced r: z = r dinv and partials of r.z.
 template <typename T>
-__global__ void k_cg_rz(int64_t n, const T* __restrict__ r, const T* __restrict__ diag, T* __restrict__ z,
+__global__ void k_cg_rz(int64_t n, const T* __restrict__ r, const T* __restrict__ dinv, T* __restrict__ z,
                         double* __restrict__ part) {
   __shared__ double red[32];
   using A = typename DotAcc<T>::type;
   A rz = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const T ri = r[i];
-    const T zi = ri / diag[i];
+    const T zi = ri * dinv[i];
     z[i] = zi;
     rz += (A)ri * (A)zi;
   }
@@ -365,6 +365,15 @@ __global__ void k_axpy_scaled(int64_t n, const double* __restrict__ rr, const fl
     x[i] += s * (double)d[i];
 }
 
+// a = 1 / a in place (the Jacobi preconditioner's reciprocal diagonal, once
+// per solve, so that every iteration multiplies: an FP64 division is a
+// multi-instruction sequence on GB300's FP64 pipe, and the FP64 vector
+// update was bound by it rather than by HBM).
+__global__ void k_recip(int64_t n, double* __restrict__ a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = 1.0 / a[i];
+}
+
 __global__ void k_fill(int64_t n, double v, double* __restrict__ a) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     a[i] = v;
@@ -379,7 +388,7 @@ __global__ void k_cast_f32(int64_t n, const double* __restrict__ a, float* __res
 struct Work {
   int64_t n;
   int nb;                         // blocks of the vector kernels (and partials)
-  double *x, *r, *z, *p, *q, *diag, *t;  // FP64 vectors
+  double *x, *r, *z, *p, *q, *diag, *t;  // FP64 vectors (diag: the reciprocal Jacobi diagonal)
   float *x32, *r32, *z32, *p32, *q32, *diag32;
   double* part;                   // 3 * nb partials
   double* scal;                   // misc scalars (rr of refinement)
@@ -426,13 +435,13 @@ fem_status get_work(fem_form* f, bool mixed, Work& w) {
 // One CG iteration on vectors of type T.
 // dtype: element-kernel type (FEM_F64, FEM_F32 or FEM_DF64); the vectors are T.
 template <typename T>
-fem_status cg_iteration(const fem_form* f, const Work& w, int dtype, T* x, T* r, T* z, T* p, T* q, const T* diag,
+fem_status cg_iteration(const fem_form* f, const Work& w, int dtype, T* x, T* r, T* z, T* p, T* q, const T* dinv,
                         cudaStream_t s) {
   const int* skip = &w.sc->done;
   const int vt = std::is_same<T, float>::value ? FEM_F32 : FEM_F64;
   FEM_TRY(fem_launch_apply_element(f, dtype, p, f->d_ye, s, skip, true));
   FEM_TRY(fem_launch_scatter(f, vt, f->d_ye, q, f->d_ess_mask, p, w.part, w.nb, s, skip, true));
-  k_cg_update<T><<<w.nb, kRedThreads, 0, s>>>(w.n, w.sc, x, r, z, p, q, diag, w.part, w.part + w.nb, w.nb);
+  k_cg_update<T><<<w.nb, kRedThreads, 0, s>>>(w.n, w.sc, x, r, z, p, q, dinv, w.part, w.part + w.nb, w.nb);
   k_cg_direction<T><<<w.nb, kRedThreads, 0, s>>>(w.n, w.sc, z, p, w.part + w.nb, w.nb);
   FEM_LAUNCHED();
   return FEM_OK;
@@ -442,7 +451,7 @@ fem_status cg_iteration(const fem_form* f, const Work& w, int dtype, T* x, T* r,
 // check_every iterations are captured once into a graph on a private stream
 // and replayed on `s`.
 template <typename T>
-fem_status cg_loop(fem_form* f, const Work& w, int dtype, T* x, T* r, T* z, T* p, T* q, const T* diag,
+fem_status cg_loop(fem_form* f, const Work& w, int dtype, T* x, T* r, T* z, T* p, T* q, const T* dinv,
                    const fem_solve_opts& o, cudaStream_t s, int* status_out, int* it_out) {
   const int k = o.check_every > 0 ? o.check_every : 16;
   cudaGraphExec_t exec = nullptr;
@@ -454,7 +463,7 @@ fem_status cg_loop(fem_form* f, const Work& w, int dtype, T* x, T* r, T* z, T* p
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       st = fem_fail(FEM_ECUDA, "solve: stream capture failed to begin");
     } else {
-      for (int i = 0; i < k && st == FEM_OK; ++i) st = cg_iteration<T>(f, w, dtype, x, r, z, p, q, diag, cs);
+      for (int i = 0; i < k && st == FEM_OK; ++i) st = cg_iteration<T>(f, w, dtype, x, r, z, p, q, dinv, cs);
       cudaError_t e = cudaStreamEndCapture(cs, &g);
       if (st == FEM_OK && e != cudaSuccess) st = fem_fail(FEM_ECUDA, "solve: end capture: %s", cudaGetErrorString(e));
     }
@@ -477,7 +486,7 @@ fem_status cg_loop(fem_form* f, const Work& w, int dtype, T* x, T* r, T* z, T* p
         break;
       }
     } else {
-      for (int i = 0; i < k && st == FEM_OK; ++i) st = cg_iteration<T>(f, w, dtype, x, r, z, p, q, diag, s);
+      for (int i = 0; i < k && st == FEM_OK; ++i) st = cg_iteration<T>(f, w, dtype, x, r, z, p, q, dinv, s);
       if (st != FEM_OK) break;
     }
     if (cudaMemcpyAsync(h, &w.sc->it, 4 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -599,6 +608,8 @@ extern "C" fem_status fem_solve(const fem_form* fc, const double* b, double* xio
     FEM_LAUNCHED();
   } else {
     FEM_TRY(fem_assemble_diagonal(f, w.diag, 1, s));
+    k_recip<<<w.nb, 256, 0, s>>>(n, w.diag);  // w.diag holds the reciprocal from here on
+    FEM_LAUNCHED();
   }
   fem_solve_info inf;
   std::memset(&inf, 0, sizeof inf);
