@@ -60,3 +60,21 @@ def test_error_path_without_gpu(libpath):
     st = P.lib().fem_mesh_create(None, 0, None, 0, C.byref(h))
     assert st == B.FEM_EINVAL
     assert "empty mesh" in P.lib().fem_last_error().decode()
+
+
+def test_solve_option_defaults(libpath):
+    """fem_solve_opts_default leaves inner_rtol at 0: every solver then takes
+    its mode's measured default (documented in include/fem.h); the other
+    fields have their documented values."""
+    import ctypes as C
+    import paper_1911_09220_gb300 as P
+    from paper_1911_09220_gb300 import _binding as B
+    o = B.SolveOpts()
+    P.lib().fem_solve_opts_default(C.byref(o))
+    assert o.inner_rtol == 0.0
+    assert o.rtol == 1e-10 and o.maxit == 20000 and o.max_outer == 30
+    assert o.check_every == 16 and o.use_graph == 1 and o.precond == 0
+    hdr = open(os.path.join(ROOT, "include", "fem.h")).read()
+    for phrase in ("fem_solve 1e-4 (FEM_SOLVE_MIXED)", "(FEM_SOLVE_MIXED_RU); fem_mg_solve 3e-4",
+                   "fem_batch_solve 1e-4"):
+        assert phrase in " ".join(hdr.split()), phrase
