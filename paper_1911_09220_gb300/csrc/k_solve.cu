@@ -33,8 +33,9 @@ struct CgScalars {
   double upd2;      // reliable updates: stop for an FP64 update once r.r <= upd2
   double rz_new;    // r.z of the iteration that stopped for an update
   int it, done, status, maxit;  // read by the host as four ints
-  int it1;          // it + 1, written by the update kernel for the direction kernel
+  int it1;          // it + 1, written by the update kernel for its last block
   int ru;           // 1: reliable-update mode
+  unsigned ticket;  // blocks of the update kernel that have finished (0 between launches)
 };
 enum { ST_RUN = 0, ST_CONV = 1, ST_NOCONV = 2, ST_BREAK = 3, ST_UPDATE = 4 };
 
@@ -43,6 +44,14 @@ constexpr int kRedThreads = 256;
 __device__ double sum_partials(const double* part, int n, double* red) {
   double v = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
+  return block_sum(v, red);
+}
+
+// The same sum of partials that other blocks of the running kernel wrote
+// (loads that bypass L1).
+__device__ double sum_partials_cg(const double* part, int n, double* red) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(part + i);
   return block_sum(v, red);
 }
 
@@ -107,6 +116,7 @@ __global__ void k_cg_init_scalars(CgScalars* sc, const double* __restrict__ part
     sc->done = 0;
     sc->ru = 0;
     sc->upd2 = 0.0;
+    sc->ticket = 0;
     if (rr <= sc->tol2) {
       sc->done = 1;
       sc->status = ST_CONV;
@@ -121,7 +131,11 @@ __global__ void k_cg_init_scalars(CgScalars* sc, const double* __restrict__ part
 // x += a p, r -= a q, z = r dinv with a = (r.z) / (p.q), the p.q partials
 // (pq_part, written by the scatter) summed by every block; partials of r.z
 // and r.r to part_out[0, nb) and part_out[nb, 2 nb). A non-positive or
-// non-finite p.q stops the solve (breakdown) in every block alike.
+// non-finite p.q stops the solve (breakdown) in every block alike. The last
+// block to finish (an atomic ticket: no block waits for another) sums the
+// r.z and r.r partials in the fixed order and takes the iteration's
+// decisions (convergence test, beta, the next r.z slot) for the direction
+// kernel.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
 k_cg_update(int64_t n, CgScalars* __restrict__ sc, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
@@ -193,53 +207,50 @@ k_cg_update(int64_t n, CgScalars* __restrict__ sc, T* __restrict__ x, T* __restr
   if (threadIdx.x == 0) part_out[blockIdx.x] = s;
   s = block_sum((double)rr, red);
   if (threadIdx.x == 0) part_out[gridDim.x + blockIdx.x] = s;
-}
-
-// Convergence test and the next search direction: r.z and r.r summed by every
-// block from part[0, nb) and part[nb, 2 nb); unless the solve stops,
-// beta = (r.z)_new / (r.z)_old and p = z + beta p.
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads)
-k_cg_direction(int64_t n, CgScalars* __restrict__ sc, const T* __restrict__ z, T* __restrict__ p,
-               const double* __restrict__ part, int nb) {
-  __shared__ double red[32];
-  __shared__ double s_beta;
-  __shared__ int s_go;
-  if (sc->done) return;
-  const double rz = sum_partials(part, nb, red);
-  const double rr = sum_partials(part + nb, nb, red);
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&sc->ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const double rzt = sum_partials_cg(part_out, gridDim.x, red);
+  const double rrt = sum_partials_cg(part_out + gridDim.x, gridDim.x, red);
   if (threadIdx.x == 0) {
+    sc->ticket = 0;
     const int it = sc->it1;
     int status = ST_RUN;
-    if (!isfinite(rz) || !isfinite(rr)) {
+    if (!isfinite(rzt) || !isfinite(rrt)) {
       status = ST_BREAK;
-    } else if (sc->ru && (rr <= sc->upd2 || rr <= sc->tol2)) {
+    } else if (sc->ru && (rrt <= sc->upd2 || rrt <= sc->tol2)) {
       // reliable-update mode: hand over to the host for an FP64 update (the
       // true residual decides convergence); beta waits for the new residual
       status = ST_UPDATE;
-    } else if (rr <= sc->tol2) {
+    } else if (rrt <= sc->tol2) {
       status = ST_CONV;
     } else if (it >= sc->maxit) {
       status = ST_NOCONV;
     }
-    s_go = status == ST_RUN;
-    s_beta = rz / sc->rzb[(it - 1) & 1];
-    if (blockIdx.x == 0) {
-      sc->it = it;
-      sc->rr = rr;
-      if (status == ST_RUN) {
-        sc->rzb[it & 1] = rz;
-        sc->beta = s_beta;
-      } else {
-        sc->status = status;
-        sc->done = 1;
-        if (status == ST_UPDATE) sc->rz_new = rz;
-      }
+    sc->it = it;
+    sc->rr = rrt;
+    if (status == ST_RUN) {
+      sc->beta = rzt / sc->rzb[(it - 1) & 1];
+      sc->rzb[it & 1] = rzt;
+    } else {
+      sc->status = status;
+      sc->done = 1;
+      if (status == ST_UPDATE) sc->rz_new = rzt;
     }
   }
-  __syncthreads();
-  if (!s_go) return;
-  const T b = (T)s_beta;
+}
+
+// The next search direction p = z + beta p, with beta and the decision to go
+// on taken by the update kernel's last block.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+k_cg_direction(int64_t n, const CgScalars* __restrict__ sc, const T* __restrict__ z, T* __restrict__ p) {
+  if (sc->done) return;
+  const T b = (T)sc->beta;
   using V = typename Vec16<T>::V;
   constexpr int W = Vec16<T>::W;
   const int64_t nv = n / W, stride = (int64_t)gridDim.x * blockDim.x;
@@ -286,6 +297,7 @@ __global__ void k_cg_resume(CgScalars* sc, const double* __restrict__ part, int 
     sc->upd2 = upd2;
     sc->status = ST_RUN;
     sc->done = 0;
+    sc->ticket = 0;
     if (!isfinite(rz) || !(rz > 0.0)) {
       sc->done = 1;
       sc->status = ST_BREAK;
@@ -442,7 +454,7 @@ fem_status cg_iteration(const fem_form* f, const Work& w, int dtype, T* x, T* r,
   FEM_TRY(fem_launch_apply_element(f, dtype, p, f->d_ye, s, skip, true));
   FEM_TRY(fem_launch_scatter(f, vt, f->d_ye, q, f->d_ess_mask, p, w.part, w.nb, s, skip, true));
   k_cg_update<T><<<w.nb, kRedThreads, 0, s>>>(w.n, w.sc, x, r, z, p, q, dinv, w.part, w.part + w.nb, w.nb);
-  k_cg_direction<T><<<w.nb, kRedThreads, 0, s>>>(w.n, w.sc, z, p, w.part + w.nb, w.nb);
+  k_cg_direction<T><<<w.nb, kRedThreads, 0, s>>>(w.n, w.sc, z, p);
   FEM_LAUNCHED();
   return FEM_OK;
 }
